@@ -1,0 +1,208 @@
+/*
+ * matgraph: batched periodic cutoff and k-nearest-neighbour multigraphs of crystal
+ * structures on one GB300 GPU (sm_103a), with edge vectors and their gradients.
+ *
+ * Method: Klipfel, Fregier, Sayede, Bouraoui, "Optimized Crystallographic Graph
+ * Generation for Material Science" (IJCAI 2023 workshop; arXiv 2307.05380).
+ *
+ * Conventions (Sec. 2.1, Def. 1 and Def. 3)
+ *   A structure s is a lattice L_s (3x3 float, ROW r = lattice vector r, Angstrom; the
+ *   paper's rho is L^T) and fractional coordinates x (float [n][3], any finite value;
+ *   never wrapped).  A batch concatenates structures: atom rows
+ *   atom_ptr[s] .. atom_ptr[s+1]-1 belong to structure s.
+ *   An edge is (src i, dst j, t), i and j GLOBAL atom rows of one structure, t an
+ *   integer cell offset, with edge vector v = (x_j - x_i + t) L and length |v|.
+ *   Cutoff graph (Def. 3, constant c per structure): every (i, j, t) with |v| < c,
+ *   strictly, except (i, i, 0).  Images of an atom itself, (i, i, t != 0), are edges.
+ *   KNN graph (Sec. 2.1, the special case after Def. 3; Alg. 1 and 2): exactly k edges
+ *   per atom, the k smallest by (d2, j, t) lexicographically, t signed.
+ *   Membership and ranking use the canonical FP64 distance: with inputs promoted to
+ *   double and every operation rounded to nearest without fused multiply-add,
+ *     df_c = (x_j[c] - x_i[c]) + t_c;  v_c = (df_0 L_0c + df_1 L_1c) + df_2 L_2c;
+ *     d2 = (v_0^2 + v_1^2) + v_2^2;    edge iff d2 < (double)c * (double)c.
+ *   Output order is canonical: (src, dst, tx, ty, tz) ascending; structures in order.
+ *
+ * Memory and streams
+ *   Every pointer named "device" is device memory owned by the caller.  The library
+ *   never allocates device memory: scratch comes from a caller workspace sized by
+ *   mg_workspace_size.  All calls are ordered on the caller's stream (a cudaStream_t
+ *   passed as void*; NULL = legacy default stream) and none synchronises the host,
+ *   except mg_autotune.  The host-side mg_context_t owns only host state (device
+ *   properties, tuned schedules, captured CUDA graphs).
+ *
+ * Errors
+ *   Arguments the host can check (null pointers, k <= 0, cutoff <= 0, too small a
+ *   workspace) make a call return an error code before anything is launched.
+ *   Problems found on the device (non-finite input, singular lattice, too small an
+ *   edge capacity, an offset that does not fit a sort key, a bounded wait that ran
+ *   out) are written to the graph's device status word; read it after synchronising
+ *   the stream.  A CUDA launch error returns MG_ERR_CUDA.
+ */
+#ifndef MATGRAPH_H
+#define MATGRAPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_context *mg_context_t;
+
+typedef enum {
+    MG_OK = 0,
+    MG_ERR_INVALID_ARGUMENT = 1,
+    MG_ERR_NONFINITE_INPUT = 2,
+    MG_ERR_SINGULAR_LATTICE = 3,
+    MG_ERR_CAPACITY = 4,     /* more edges than graph capacity; nothing past it written */
+    MG_ERR_OFFSET_RANGE = 5, /* an offset component outside [-511, 511] where a packed
+                                sort key needs it, or a KNN radius that could not grow */
+    MG_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up */
+    MG_ERR_CUDA = 7,
+    MG_ERR_WORKSPACE = 8,    /* workspace pointer NULL or smaller than required */
+    MG_ERR_NOT_BUILT = 9,    /* mg_update_graph on a graph no build call has filled */
+    MG_ERR_INTERNAL = 10     /* an internal consistency check failed (a library bug) */
+} mg_status_t;
+
+/* Device status word, written by the kernels of a build. */
+typedef struct {
+    int32_t code;                /* mg_status_t of the first device-side problem, else 0 */
+    int32_t first_bad_structure; /* structure index for input errors, else -1 */
+    int64_t num_edges;           /* edges in the graph (also edge_ptr[B]) */
+    int64_t required_capacity;   /* edges needed; equals num_edges on success */
+    int64_t rechecked;           /* FP32 candidates re-tested in FP64 (opts.collect_stats) */
+    int64_t candidates;          /* FP32 candidates evaluated (opts.collect_stats) */
+} mg_device_status_t;
+
+/* A batch of structures.  Counts are host values (no synchronisation needed). */
+typedef struct {
+    int32_t num_structures;   /* B >= 1 */
+    int32_t total_atoms;      /* N = atom_ptr[B] */
+    int32_t max_atoms;        /* max atoms in one structure, 0 if unknown (picks schedule) */
+    const float *lattice;     /* device [B][3][3], row r = lattice vector r, Angstrom */
+    const float *frac;        /* device [N][3] fractional coordinates */
+    const int32_t *atom_ptr;  /* device [B+1], atom_ptr[0] = 0, non-decreasing */
+} mg_batch_t;
+
+/* Graph buffers, all device memory owned by the caller. */
+typedef struct {
+    int64_t capacity;          /* edges the arrays below can hold */
+    int32_t *src;              /* [capacity] global atom row i */
+    int32_t *dst;              /* [capacity] global atom row j */
+    int32_t *offset;           /* [capacity][3] cell offset t */
+    float *vec;                /* [capacity][3] (x_j - x_i + t) L, or NULL */
+    float *len;                /* [capacity] |vec|, or NULL */
+    int64_t *edge_ptr;         /* [B+1] edges of structure s: edge_ptr[s] .. edge_ptr[s+1]-1 */
+    int64_t *src_ptr;          /* [N+1] CSR by source atom (needed by fwd/bwd), or NULL */
+    int32_t *perm_dst;         /* [capacity] edge ids ordered by (dst, src, t), or NULL */
+    int64_t *dst_ptr;          /* [N+1] CSR of perm_dst by destination atom; with perm_dst */
+    mg_device_status_t *status;/* device status word */
+} mg_graph_t;
+
+/* Options; pass NULL for the defaults shown. */
+typedef struct {
+    float band_rel;        /* 1e-5: FP64 re-test band, relative to the cutoff distance
+                              (candidates within band_rel*c of c are re-tested in FP64,
+                              widened further to the FP32 error bound when that is larger) */
+    int32_t knn_keep_ties; /* 0: exactly k.  Other values are reserved (invalid argument) */
+    int32_t schedule;      /* 0 auto (tuned), 1 flat grid, 2 persistent work queue */
+    int32_t collect_stats; /* 1: count FP32 candidates and FP64 re-tests into status */
+} mg_opts_t;
+
+#define MG_KIND_CUTOFF 1
+#define MG_KIND_KNN 2
+
+/* Create a context bound to CUDA device `device`.  Reads device properties. */
+mg_status_t mg_create(mg_context_t *ctx, int device);
+mg_status_t mg_destroy(mg_context_t ctx);
+const char *mg_status_string(mg_status_t status);
+
+/* Workspace bytes that suffice for every call on batches with this many structures
+ * and atoms (any values) and graphs of up to max_edges edges. */
+mg_status_t mg_workspace_size(mg_context_t ctx, const mg_batch_t *batch, int64_t max_edges,
+                              size_t *bytes);
+
+/* Cutoff multigraph (Def. 3 with a constant cutoff per structure).
+ * cutoff: radius for every structure, or cutoff_per_structure (device [B]) if not NULL.
+ * Writes src, dst, offset, vec/len (if not NULL), edge_ptr, src_ptr (if not NULL), and
+ * perm_dst/dst_ptr (if not NULL).  If the edge count exceeds capacity, the status word
+ * reports MG_ERR_CAPACITY with required_capacity; edge arrays are then not written.
+ * Canonical order holds whichever schedule runs. */
+mg_status_t mg_cutoff_graph(mg_context_t ctx, const mg_batch_t *batch, float cutoff,
+                            const float *cutoff_per_structure, const mg_opts_t *opts,
+                            mg_graph_t *graph, void *workspace, size_t workspace_bytes,
+                            void *stream);
+
+/* KNN multigraph (Alg. 1 output): exactly k edges per atom, k * N in total, so the
+ * capacity needed is known up front.  Search radii start from the number density and
+ * grow until the k-th distance is covered (Alg. 1's loop).  Same outputs as above. */
+mg_status_t mg_knn_graph(mg_context_t ctx, const mg_batch_t *batch, int32_t k,
+                         const mg_opts_t *opts, mg_graph_t *graph, void *workspace,
+                         size_t workspace_bytes, void *stream);
+
+/* Rebuild `graph` for new coordinates/lattices held in the same device buffers, with
+ * the kind, parameters, shapes and pointers of the last build of this graph (Sec. 1:
+ * the graph follows the geometry inside a generative model's forward pass).  The
+ * first call captures the build into a CUDA graph; later calls replay it.
+ * Returns MG_ERR_NOT_BUILT if no build call has filled this graph. */
+mg_status_t mg_update_graph(mg_context_t ctx, const mg_batch_t *batch, mg_graph_t *graph,
+                            void *workspace, size_t workspace_bytes, void *stream);
+
+/* The plain comparison build: the same kernels, launched once per structure (one launch
+ * sequence per structure, device-chained offsets, no host synchronisation).
+ * atom_ptr_host: host copy of batch->atom_ptr.  kind: MG_KIND_CUTOFF or MG_KIND_KNN
+ * (cutoff or k used accordingly).  Output identical to the batched build. */
+mg_status_t mg_build_per_structure(mg_context_t ctx, const mg_batch_t *batch, int32_t kind,
+                                   float cutoff, int32_t k, const int32_t *atom_ptr_host,
+                                   const mg_opts_t *opts, mg_graph_t *graph, void *workspace,
+                                   size_t workspace_bytes, void *stream);
+
+/* Edge vectors for a fixed edge set (Def. 3's rho (x_j - x_i + t)): vec [E][3] and
+ * len [E] from the current batch coordinates.  Needs graph->src_ptr and edge_ptr; the
+ * edge count is read on the device (edge_ptr[B]).  Either output may be NULL. */
+mg_status_t mg_edge_vectors_fwd(mg_context_t ctx, const mg_batch_t *batch, const mg_graph_t *graph,
+                                float *vec, float *len, void *stream);
+
+/* Backward of mg_edge_vectors_fwd with the edge set held fixed:
+ *   g_e = grad_vec_e + grad_len_e * vec_e / len_e   (len_e > 0)
+ *   grad_frac[j] = sum_{e: dst=j} g_e L^T - sum_{e: src=j} g_e L^T
+ *   grad_lattice[s] = sum_{e in s} (x_j - x_i + t)^T g_e          (3x3)
+ * Deterministic: segmented sums in canonical order (src segments, then dst segments
+ * through perm_dst), no floating-point atomics.  grad_vec or grad_len may be NULL (zero);
+ * vec/len are the forward outputs.  Needs src_ptr, perm_dst and dst_ptr.  Outputs
+ * (device float [N][3] and [B][3][3]) are overwritten. */
+mg_status_t mg_edge_vectors_bwd(mg_context_t ctx, const mg_batch_t *batch, const mg_graph_t *graph,
+                                const float *grad_vec, const float *grad_len, const float *vec,
+                                const float *len, float *grad_frac, float *grad_lattice,
+                                void *workspace, size_t workspace_bytes, void *stream);
+
+/* Time the available schedules for this batch shape on the caller's buffers and keep
+ * the fastest per size class in the context (synchronises; results are identical for
+ * every schedule).  kind/cutoff/k as in mg_build_per_structure. */
+mg_status_t mg_autotune(mg_context_t ctx, const mg_batch_t *batch, int32_t kind, float cutoff,
+                        int32_t k, mg_graph_t *graph, void *workspace, size_t workspace_bytes,
+                        void *stream);
+
+/* Number of kernel launches the last build/fwd/bwd call on this context issued
+ * (graph replays count their kernel nodes). */
+int64_t mg_last_launch_count(mg_context_t ctx);
+
+/* Measurement support (not needed for results).  When on, the batched builds and the
+ * edge-vector calls of this context record CUDA events on the caller's stream between
+ * their kernel stages; plans captured while on contain the event records too.
+ * mg_stage_times waits for the events of the last call of kind `which`
+ * (MG_PROF_CUTOFF, MG_PROF_KNN, MG_PROF_FWD, MG_PROF_BWD), then writes up to max_stages
+ * stage names (static strings) and durations in milliseconds.  Returns the number of
+ * stages, or -1 if that kind has not run with profiling on. */
+#define MG_PROF_CUTOFF 0
+#define MG_PROF_KNN 1
+#define MG_PROF_FWD 2
+#define MG_PROF_BWD 3
+mg_status_t mg_profile_enable(mg_context_t ctx, int32_t on);
+int32_t mg_stage_times(mg_context_t ctx, int32_t which, int32_t max_stages, const char **names, float *ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MATGRAPH_H */

@@ -1,0 +1,678 @@
+// C-ABI host layer of matgraph (include/matgraph.h): argument checks, workspace
+// carving, launch sequences, CUDA-graph plans for mg_update_graph, the per-structure
+// comparison build and the schedule autotuner.  It allocates no device memory.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "matgraph.h"
+#include "mg_device.cuh"
+#include "mg_launch.h"
+
+namespace mg {
+
+static int g_num_sms = 0;
+int num_sms() { return g_num_sms > 0 ? g_num_sms : 152; }
+
+}  // namespace mg
+
+using namespace mg;
+
+// A recorded build: everything a rebuild of the same graph needs.
+struct Plan {
+    int kind = 0;
+    float cutoff = 0.f;
+    const float *cutoff_ps = nullptr;
+    int k = 0;
+    mg_opts_t opts{};
+    mg_batch_t batch{};
+    mg_graph_t graph{};
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;
+};
+
+// Stage events of one call kind (measurement support).
+struct Prof {
+    static constexpr int MAX = 16;
+    cudaEvent_t ev[MAX] = {};
+    const char *name[MAX] = {};
+    int n = 0;
+    bool valid = false;
+};
+
+struct mg_context {
+    int device = 0;
+    int sms = 152;
+    bool prof_on = false;
+    Prof prof[4];
+    std::mutex mu;
+    std::map<const void *, Plan> plans;      // keyed by graph->src
+    int tuned[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};  // [kind-1][size class] -> schedule
+    int64_t last_launches = 0;
+};
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+// Stage marks: with profiling on, record the next event of set `which` on the stream.
+struct Marker {
+    mg_context *ctx;
+    int which;
+    cudaStream_t st;
+    Marker(mg_context *c, int w, cudaStream_t s) : ctx(c), which(w), st(s) {
+        if (on()) {
+            ctx->prof[which].n = 0;
+            ctx->prof[which].valid = false;
+            mark("start");
+        }
+    }
+    bool on() const { return ctx && which >= 0 && ctx->prof_on; }
+    void mark(const char *name) {
+        if (!on()) return;
+        Prof &p = ctx->prof[which];
+        if (p.n >= Prof::MAX) return;
+        if (!p.ev[p.n]) return;
+        cudaEventRecord(p.ev[p.n], st);
+        p.name[p.n] = name;
+        ++p.n;
+        p.valid = true;
+    }
+};
+
+size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Layout {
+    size_t recs, pos, atom_struct, cnt, cursor, tile_sum, src_ptr, gpart, lpart, sort_tmp, queue, total;
+};
+
+Layout layout(int B, int N, int64_t max_edges) {
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off += align_up(bytes > 0 ? bytes : 1);
+        return at;
+    };
+    const size_t n = (size_t)(N > 0 ? N : 1);
+    const size_t tiles = (size_t)((N + 1 + SCAN_TILE - 1) / SCAN_TILE + 2);
+    L.recs = take(sizeof(StructRec) * (size_t)(B > 0 ? B : 1));
+    L.pos = take(sizeof(float4) * n);
+    L.atom_struct = take(sizeof(int32_t) * n);
+    L.cnt = take(sizeof(int32_t) * n);
+    L.cursor = take(sizeof(int32_t) * n);
+    L.tile_sum = take(sizeof(long long) * tiles);
+    L.src_ptr = take(sizeof(int64_t) * (n + 1));
+    L.gpart = take(sizeof(double) * 3 * n);
+    L.lpart = take(sizeof(double) * 9 * n);
+    L.sort_tmp = take(sizeof(int32_t) * (size_t)(max_edges > 0 ? max_edges : 1));
+    L.queue = take(16 * sizeof(unsigned int));
+    L.total = off;
+    return L;
+}
+
+Work carve(void *ws, int B, int N, int64_t max_edges) {
+    const Layout L = layout(B, N, max_edges);
+    char *b = static_cast<char *>(ws);
+    Work w;
+    w.recs = reinterpret_cast<StructRec *>(b + L.recs);
+    w.pos = reinterpret_cast<float4 *>(b + L.pos);
+    w.atom_struct = reinterpret_cast<int32_t *>(b + L.atom_struct);
+    w.cnt = reinterpret_cast<int32_t *>(b + L.cnt);
+    w.cursor = reinterpret_cast<int32_t *>(b + L.cursor);
+    w.tile_sum = reinterpret_cast<long long *>(b + L.tile_sum);
+    w.src_ptr = reinterpret_cast<int64_t *>(b + L.src_ptr);
+    w.gpart = reinterpret_cast<double *>(b + L.gpart);
+    w.lpart = reinterpret_cast<double *>(b + L.lpart);
+    w.sort_tmp = reinterpret_cast<int32_t *>(b + L.sort_tmp);
+    w.queue = reinterpret_cast<unsigned int *>(b + L.queue);
+    w.max_edges = max_edges;
+    return w;
+}
+
+// Largest edge count a workspace of ws_bytes supports for this batch.
+int64_t ws_max_edges(int B, int N, size_t ws_bytes) {
+    const Layout L0 = layout(B, N, 0);
+    if (ws_bytes < L0.total) return -1;
+    return (int64_t)((ws_bytes - L0.total) / sizeof(int32_t));
+}
+
+mg_opts_t defaults(const mg_opts_t *o) {
+    mg_opts_t d;
+    d.band_rel = 1e-5f;
+    d.knn_keep_ties = 0;
+    d.schedule = 0;
+    d.collect_stats = 0;
+    if (o) d = *o;
+    return d;
+}
+
+mg_status_t check_batch(const mg_batch_t *b) {
+    if (!b || b->num_structures < 1 || b->total_atoms < 0 || !b->lattice || !b->atom_ptr ||
+        (b->total_atoms > 0 && !b->frac))
+        return MG_ERR_INVALID_ARGUMENT;
+    return MG_OK;
+}
+
+mg_status_t check_graph(const mg_graph_t *g, const mg_batch_t *b) {
+    if (!g || !g->status || !g->edge_ptr || g->capacity < 0) return MG_ERR_INVALID_ARGUMENT;
+    if (g->capacity > 0 && (!g->src || !g->dst || !g->offset)) return MG_ERR_INVALID_ARGUMENT;
+    if (g->perm_dst && !g->dst_ptr) return MG_ERR_INVALID_ARGUMENT;
+    if (g->perm_dst && g->capacity > (int64_t)INT_MAX) return MG_ERR_INVALID_ARGUMENT;
+    (void)b;
+    return MG_OK;
+}
+
+int size_class(const mg_batch_t *b) {
+    const int m = b->max_atoms;
+    if (m <= 0) return 1;
+    if (m <= 32) return 0;
+    if (m <= 128) return 1;
+    if (m <= 512) return 2;
+    return 3;
+}
+
+int pick_schedule(mg_context *ctx, int kind, const mg_batch_t *b, const mg_opts_t &o) {
+    if (o.schedule == 1 || o.schedule == 2) return o.schedule;
+    const int t = ctx->tuned[kind - 1][size_class(b)];
+    return t ? t : 1;
+}
+
+__global__ void status_init_kernel(mg_device_status_t *st) {
+    st->code = 0;
+    st->first_bad_structure = INT_MAX;
+    st->num_edges = 0;
+    st->required_capacity = 0;
+    st->rechecked = 0;
+    st->candidates = 0;
+}
+
+// The batched build's launch sequence (no host synchronisation).
+mg_status_t enqueue_build(mg_context *ctx, int kind, const mg_batch_t *b, float cutoff, const float *cutoff_ps,
+                          int k, const mg_opts_t &o, const mg_graph_t *g, void *ws, size_t ws_bytes,
+                          cudaStream_t st, int *launches) {
+    const int B = b->num_structures, N = b->total_atoms;
+    const int64_t me = ws_max_edges(B, N, ws_bytes);
+    if (!ws || me < 0) return MG_ERR_WORKSPACE;
+    const Work w = carve(ws, B, N, me);
+    int n = 0;
+    Marker mk(ctx, kind == MG_KIND_CUTOFF ? MG_PROF_CUTOFF : MG_PROF_KNN, st);
+    status_init_kernel<<<1, 1, 0, st>>>(g->status);
+    ++n;
+    PrepArgs pa{B, N, b->lattice, b->frac, b->atom_ptr, cutoff, cutoff_ps, kind == MG_KIND_KNN ? k : 0,
+                o.band_rel, g->status};
+    if (launch_prep(pa, w, st)) return MG_ERR_CUDA;
+    ++n;
+    mk.mark("prep");
+    BuildArgs ba;
+    ba.B = B;
+    ba.N = N;
+    ba.frac = b->frac;
+    ba.atom_ptr = b->atom_ptr;
+    ba.schedule = pick_schedule(ctx, kind, b, o);
+    ba.collect_stats = o.collect_stats;
+    ba.g = *g;
+    ba.src_ptr = g->src_ptr ? g->src_ptr : w.src_ptr;
+    ba.knn_k = k;
+    ba.band_rel = o.band_rel;
+    ba.atom_lo = 0;
+    ba.atom_hi = N;
+    if (kind == MG_KIND_CUTOFF) {
+        if (launch_cutoff_count(ba, w, st)) return MG_ERR_CUDA;
+        n += 1 + (ba.schedule == 2);
+        mk.mark("count");
+        ScanArgs sa{N, w.cnt, ba.src_ptr};
+        if (launch_scan(sa, w, st)) return MG_ERR_CUDA;
+        n += 3;
+        mk.mark("scan");
+        if (launch_cutoff_finalize(ba, w, st)) return MG_ERR_CUDA;
+        ++n;
+        mk.mark("finalize");
+        if (launch_cutoff_write(ba, w, st)) return MG_ERR_CUDA;
+        n += 1 + (ba.schedule == 2);
+        mk.mark("write");
+    } else {
+        if (launch_knn_pointers(ba, w, st)) return MG_ERR_CUDA;
+        ++n;
+        mk.mark("pointers");
+        if (launch_knn(ba, w, st)) return MG_ERR_CUDA;
+        n += 1 + (ba.schedule == 2);
+        mk.mark("knn");
+    }
+    if (g->perm_dst) {
+        if (launch_dst_sort(ba, w, st, &n)) return MG_ERR_CUDA;
+        mk.mark("dst_sort");
+    }
+    if (launches) *launches = n;
+    return MG_OK;
+}
+
+bool same_batch(const mg_batch_t &a, const mg_batch_t &b) {
+    return a.num_structures == b.num_structures && a.total_atoms == b.total_atoms && a.max_atoms == b.max_atoms &&
+           a.lattice == b.lattice && a.frac == b.frac && a.atom_ptr == b.atom_ptr;
+}
+
+bool same_graph(const mg_graph_t &a, const mg_graph_t &b) {
+    return a.capacity == b.capacity && a.src == b.src && a.dst == b.dst && a.offset == b.offset && a.vec == b.vec &&
+           a.len == b.len && a.edge_ptr == b.edge_ptr && a.src_ptr == b.src_ptr && a.perm_dst == b.perm_dst &&
+           a.dst_ptr == b.dst_ptr && a.status == b.status;
+}
+
+bool same_opts(const mg_opts_t &a, const mg_opts_t &b) {
+    return a.band_rel == b.band_rel && a.knn_keep_ties == b.knn_keep_ties && a.schedule == b.schedule &&
+           a.collect_stats == b.collect_stats;
+}
+
+mg_status_t check_build_args(mg_context *ctx, const mg_batch_t *b, const mg_opts_t &o, const mg_graph_t *g) {
+    if (!ctx) return MG_ERR_INVALID_ARGUMENT;
+    mg_status_t r = check_batch(b);
+    if (r) return r;
+    r = check_graph(g, b);
+    if (r) return r;
+    if (o.knn_keep_ties != 0 || !(o.band_rel >= 0.f) || o.schedule < 0 || o.schedule > 2)
+        return MG_ERR_INVALID_ARGUMENT;
+    return MG_OK;
+}
+
+mg_status_t build_and_record(mg_context *ctx, int kind, const mg_batch_t *b, float cutoff, const float *cutoff_ps,
+                             int k, const mg_opts_t *opts, mg_graph_t *g, void *ws, size_t ws_bytes, void *stream) {
+    const mg_opts_t o = defaults(opts);
+    mg_status_t r = check_build_args(ctx, b, o, g);
+    if (r) return r;
+    if (kind == MG_KIND_CUTOFF && !cutoff_ps && !(cutoff > 0.f)) return MG_ERR_INVALID_ARGUMENT;
+    if (kind == MG_KIND_KNN) {
+        if (k <= 0 || k > KNN_MAX_K) return MG_ERR_INVALID_ARGUMENT;
+        if ((int64_t)k * b->total_atoms > g->capacity) return MG_ERR_CAPACITY;
+    }
+    int launches = 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    r = enqueue_build(ctx, kind, b, cutoff, cutoff_ps, k, o, g, ws, ws_bytes, st, &launches);
+    if (r) return r;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->last_launches = launches;
+    Plan &p = ctx->plans[(const void *)g->src];
+    const bool same = p.kind == kind && p.cutoff == cutoff && p.cutoff_ps == cutoff_ps && p.k == k &&
+                      same_opts(p.opts, o) && same_batch(p.batch, *b) && same_graph(p.graph, *g) && p.ws == ws &&
+                      p.ws_bytes == ws_bytes;
+    if (!same) {
+        if (p.exec) cudaGraphExecDestroy(p.exec);
+        p = Plan();
+        p.kind = kind;
+        p.cutoff = cutoff;
+        p.cutoff_ps = cutoff_ps;
+        p.k = k;
+        p.opts = o;
+        p.batch = *b;
+        p.graph = *g;
+        p.ws = ws;
+        p.ws_bytes = ws_bytes;
+        p.launches = launches;
+    }
+    return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mg_status_t mg_create(mg_context_t *ctx, int device) {
+    if (!ctx) return MG_ERR_INVALID_ARGUMENT;
+    *ctx = nullptr;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return MG_ERR_CUDA;
+    mg_context *c = new (std::nothrow) mg_context();
+    if (!c) return MG_ERR_INVALID_ARGUMENT;
+    c->device = device;
+    c->sms = prop.multiProcessorCount;
+    g_num_sms = prop.multiProcessorCount;
+    *ctx = c;
+    return MG_OK;
+}
+
+mg_status_t mg_destroy(mg_context_t ctx) {
+    if (!ctx) return MG_ERR_INVALID_ARGUMENT;
+    for (auto &kv : ctx->plans)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    for (auto &p : ctx->prof)
+        for (auto &e : p.ev)
+            if (e) cudaEventDestroy(e);
+    delete ctx;
+    return MG_OK;
+}
+
+const char *mg_status_string(mg_status_t s) {
+    switch (s) {
+    case MG_OK: return "MG_OK";
+    case MG_ERR_INVALID_ARGUMENT: return "MG_ERR_INVALID_ARGUMENT: invalid argument";
+    case MG_ERR_NONFINITE_INPUT: return "MG_ERR_NONFINITE_INPUT: non-finite lattice or coordinate";
+    case MG_ERR_SINGULAR_LATTICE: return "MG_ERR_SINGULAR_LATTICE: singular lattice";
+    case MG_ERR_CAPACITY: return "MG_ERR_CAPACITY: edge capacity too small";
+    case MG_ERR_OFFSET_RANGE: return "MG_ERR_OFFSET_RANGE: cell offset outside the packed-key range";
+    case MG_ERR_TIMEOUT: return "MG_ERR_TIMEOUT: a bounded device wait gave up";
+    case MG_ERR_CUDA: return "MG_ERR_CUDA: CUDA error";
+    case MG_ERR_WORKSPACE: return "MG_ERR_WORKSPACE: workspace missing or too small";
+    case MG_ERR_NOT_BUILT: return "MG_ERR_NOT_BUILT: graph was never built";
+    case MG_ERR_INTERNAL: return "MG_ERR_INTERNAL: internal consistency check failed";
+    }
+    return "unknown matgraph status";
+}
+
+mg_status_t mg_workspace_size(mg_context_t ctx, const mg_batch_t *batch, int64_t max_edges, size_t *bytes) {
+    if (!ctx || !batch || !bytes || max_edges < 0 || batch->num_structures < 1 || batch->total_atoms < 0)
+        return MG_ERR_INVALID_ARGUMENT;
+    *bytes = layout(batch->num_structures, batch->total_atoms, max_edges).total;
+    return MG_OK;
+}
+
+mg_status_t mg_cutoff_graph(mg_context_t ctx, const mg_batch_t *batch, float cutoff, const float *cutoff_ps,
+                            const mg_opts_t *opts, mg_graph_t *graph, void *ws, size_t ws_bytes, void *stream) {
+    return build_and_record(ctx, MG_KIND_CUTOFF, batch, cutoff, cutoff_ps, 0, opts, graph, ws, ws_bytes, stream);
+}
+
+mg_status_t mg_knn_graph(mg_context_t ctx, const mg_batch_t *batch, int32_t k, const mg_opts_t *opts,
+                         mg_graph_t *graph, void *ws, size_t ws_bytes, void *stream) {
+    return build_and_record(ctx, MG_KIND_KNN, batch, 0.f, nullptr, k, opts, graph, ws, ws_bytes, stream);
+}
+
+mg_status_t mg_update_graph(mg_context_t ctx, const mg_batch_t *batch, mg_graph_t *graph, void *ws, size_t ws_bytes,
+                            void *stream) {
+    if (!ctx || !graph) return MG_ERR_INVALID_ARGUMENT;
+    mg_status_t r = check_batch(batch);
+    if (r) return r;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->plans.find((const void *)graph->src);
+    if (it == ctx->plans.end()) return MG_ERR_NOT_BUILT;
+    Plan &p = it->second;
+    if (!same_batch(p.batch, *batch) || !same_graph(p.graph, *graph) || p.ws != ws || p.ws_bytes != ws_bytes)
+        return MG_ERR_INVALID_ARGUMENT;  // shapes, pointers or workspace differ from the recorded build
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (st != nullptr && cudaStreamIsCapturing(st, &cap) != cudaSuccess) return MG_ERR_CUDA;
+    if (st == nullptr || cap != cudaStreamCaptureStatusNone) {
+        // legacy stream or a capture already in progress: enqueue the launches directly
+        int n = 0;
+        r = enqueue_build(ctx, p.kind, batch, p.cutoff, p.cutoff_ps, p.k, p.opts, graph, ws, ws_bytes, st, &n);
+        ctx->last_launches = n;
+        return r;
+    }
+    if (!p.exec) {
+        cudaGraph_t cg = nullptr;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MG_ERR_CUDA;
+        int n = 0;
+        r = enqueue_build(ctx, p.kind, batch, p.cutoff, p.cutoff_ps, p.k, p.opts, graph, ws, ws_bytes, st, &n);
+        const cudaError_t ce = cudaStreamEndCapture(st, &cg);
+        if (r) {
+            if (cg) cudaGraphDestroy(cg);
+            return r;
+        }
+        if (ce != cudaSuccess || !cg) return MG_ERR_CUDA;
+        const cudaError_t ie = cudaGraphInstantiate(&p.exec, cg, 0);
+        cudaGraphDestroy(cg);
+        if (ie != cudaSuccess) {
+            p.exec = nullptr;
+            return MG_ERR_CUDA;
+        }
+        p.launches = n;
+    }
+    if (cudaGraphLaunch(p.exec, st) != cudaSuccess) return MG_ERR_CUDA;
+    ctx->last_launches = p.launches;
+    return MG_OK;
+}
+
+__global__ void per_structure_final_kernel(int B, int N, const int64_t *__restrict__ edge_ptr, int64_t capacity,
+                                           mg_device_status_t *status) {
+    Status *st = reinterpret_cast<Status *>(status);
+    const long long tot = edge_ptr[B];
+    st->num_edges = (unsigned long long)tot;
+    st->required_capacity = (unsigned long long)tot;
+    if (tot > capacity) set_error(status, MG_ERR_CAPACITY, -1);
+    (void)N;
+}
+
+__global__ void edge_ptr_link_kernel(int64_t *__restrict__ edge_ptr, int s, const int64_t *__restrict__ src_ptr,
+                                     int hi) {
+    edge_ptr[s + 1] = src_ptr[hi];
+}
+
+__global__ void add_base_kernel2(int64_t *__restrict__ out, int n, const int64_t *__restrict__ base) {
+    const int64_t b = *base;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q <= n; q += (int64_t)gridDim.x * blockDim.x)
+        out[q] += b;
+}
+
+mg_status_t mg_build_per_structure(mg_context_t ctx, const mg_batch_t *b, int32_t kind, float cutoff, int32_t k,
+                                   const int32_t *atom_ptr_host, const mg_opts_t *opts, mg_graph_t *g, void *ws,
+                                   size_t ws_bytes, void *stream) {
+    const mg_opts_t o = defaults(opts);
+    mg_status_t r = check_build_args(ctx, b, o, g);
+    if (r) return r;
+    if (!atom_ptr_host || (kind != MG_KIND_CUTOFF && kind != MG_KIND_KNN)) return MG_ERR_INVALID_ARGUMENT;
+    if (kind == MG_KIND_CUTOFF && !(cutoff > 0.f)) return MG_ERR_INVALID_ARGUMENT;
+    if (kind == MG_KIND_KNN && (k <= 0 || k > KNN_MAX_K)) return MG_ERR_INVALID_ARGUMENT;
+    if (kind == MG_KIND_KNN && (int64_t)k * b->total_atoms > g->capacity) return MG_ERR_CAPACITY;
+    const int B = b->num_structures, N = b->total_atoms;
+    const int64_t me = ws_max_edges(B, N, ws_bytes);
+    if (!ws || me < 0) return MG_ERR_WORKSPACE;
+    const Work w0 = carve(ws, B, N, me);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int n = 0;
+    status_init_kernel<<<1, 1, 0, st>>>(g->status);
+    ++n;
+    int64_t *src_ptr = g->src_ptr ? g->src_ptr : w0.src_ptr;
+    cudaMemsetAsync(g->edge_ptr, 0, sizeof(int64_t), st);
+    for (int s = 0; s < B; ++s) {
+        const int lo = atom_ptr_host[s], hi = atom_ptr_host[s + 1];
+        Work w = w0;
+        w.recs = w0.recs + s;  // the structure's record sits at local index 0
+        PrepArgs pa{1, hi - lo, b->lattice + 9 * (size_t)s, b->frac, b->atom_ptr + s, cutoff, nullptr,
+                    kind == MG_KIND_KNN ? k : 0, o.band_rel, g->status};
+        if (launch_prep(pa, w, st)) return MG_ERR_CUDA;
+        ++n;
+        BuildArgs ba;
+        ba.B = B;
+        ba.N = N;
+        ba.frac = b->frac;
+        ba.atom_ptr = b->atom_ptr;
+        ba.schedule = 1;
+        ba.collect_stats = o.collect_stats;
+        ba.g = *g;
+        ba.src_ptr = src_ptr;
+        ba.knn_k = k;
+        ba.band_rel = o.band_rel;
+        ba.atom_lo = lo;
+        ba.atom_hi = hi;
+        if (hi == lo) {
+            if (kind == MG_KIND_CUTOFF) {
+                edge_ptr_link_kernel<<<1, 1, 0, st>>>(g->edge_ptr, s, g->edge_ptr, s);  // edge_ptr[s+1] = edge_ptr[s]
+                ++n;
+            }
+            continue;
+        }
+        if (kind == MG_KIND_CUTOFF) {
+            if (launch_cutoff_count(ba, w, st)) return MG_ERR_CUDA;
+            ScanArgs sa{hi - lo, w.cnt + lo, src_ptr + lo};
+            if (launch_scan(sa, w, st)) return MG_ERR_CUDA;
+            add_base_kernel2<<<1, 256, 0, st>>>(src_ptr + lo, hi - lo, g->edge_ptr + s);
+            edge_ptr_link_kernel<<<1, 1, 0, st>>>(g->edge_ptr, s, src_ptr, hi);
+            if (launch_cutoff_write(ba, w, st)) return MG_ERR_CUDA;
+            n += 7;
+        } else {
+            if (launch_knn(ba, w, st)) return MG_ERR_CUDA;
+            n += 1;
+        }
+    }
+    BuildArgs fa;
+    fa.B = B;
+    fa.N = N;
+    fa.frac = b->frac;
+    fa.atom_ptr = b->atom_ptr;
+    fa.schedule = 1;
+    fa.collect_stats = 0;
+    fa.g = *g;
+    fa.src_ptr = src_ptr;
+    fa.knn_k = k;
+    fa.band_rel = o.band_rel;
+    fa.atom_lo = 0;
+    fa.atom_hi = N;
+    if (kind == MG_KIND_KNN) {
+        if (launch_knn_pointers(fa, w0, st)) return MG_ERR_CUDA;
+        ++n;
+    }
+    per_structure_final_kernel<<<1, 1, 0, st>>>(B, N, g->edge_ptr, g->capacity, g->status);
+    ++n;
+    if (g->perm_dst) {
+        if (launch_dst_sort(fa, w0, st, &n)) return MG_ERR_CUDA;
+    }
+    if (cudaGetLastError() != cudaSuccess) return MG_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->last_launches = n;
+    return MG_OK;
+}
+
+mg_status_t mg_edge_vectors_fwd(mg_context_t ctx, const mg_batch_t *b, const mg_graph_t *g, float *vec, float *len,
+                                void *stream) {
+    if (!ctx) return MG_ERR_INVALID_ARGUMENT;
+    mg_status_t r = check_batch(b);
+    if (r) return r;
+    if (!g || !g->src_ptr || !g->edge_ptr || !g->dst || !g->offset) return MG_ERR_INVALID_ARGUMENT;
+    EdgeVecArgs a{};
+    a.B = b->num_structures;
+    a.N = b->total_atoms;
+    a.lattice = b->lattice;
+    a.frac = b->frac;
+    a.atom_ptr = b->atom_ptr;
+    a.g = *g;
+    a.out_vec = vec;
+    a.out_len = len;
+    Marker mk(ctx, MG_PROF_FWD, static_cast<cudaStream_t>(stream));
+    if (launch_edgevec_fwd(a, static_cast<cudaStream_t>(stream))) return MG_ERR_CUDA;
+    mk.mark("fwd");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->last_launches = 1;
+    return MG_OK;
+}
+
+mg_status_t mg_edge_vectors_bwd(mg_context_t ctx, const mg_batch_t *b, const mg_graph_t *g, const float *grad_vec,
+                                const float *grad_len, const float *vec, const float *len, float *grad_frac,
+                                float *grad_lattice, void *ws, size_t ws_bytes, void *stream) {
+    if (!ctx) return MG_ERR_INVALID_ARGUMENT;
+    mg_status_t r = check_batch(b);
+    if (r) return r;
+    if (!g || !g->src_ptr || !g->edge_ptr || !g->dst || !g->offset || !g->perm_dst || !g->dst_ptr || !grad_frac ||
+        !grad_lattice)
+        return MG_ERR_INVALID_ARGUMENT;
+    if (grad_len && (!vec || !len)) return MG_ERR_INVALID_ARGUMENT;
+    const int B = b->num_structures, N = b->total_atoms;
+    const int64_t me = ws_max_edges(B, N, ws_bytes);
+    if (!ws || me < 0) return MG_ERR_WORKSPACE;
+    const Work w = carve(ws, B, N, me);
+    EdgeVecArgs a{};
+    a.B = B;
+    a.N = N;
+    a.lattice = b->lattice;
+    a.frac = b->frac;
+    a.atom_ptr = b->atom_ptr;
+    a.g = *g;
+    a.grad_vec = grad_vec;
+    a.grad_len = grad_len;
+    a.vec = vec;
+    a.len = len;
+    a.grad_frac = grad_frac;
+    a.grad_lattice = grad_lattice;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Marker mk(ctx, MG_PROF_BWD, st);
+    if (launch_bwd_src(a, w, st)) return MG_ERR_CUDA;
+    mk.mark("bwd_src");
+    if (launch_bwd_dst(a, w, st)) return MG_ERR_CUDA;
+    mk.mark("bwd_dst");
+    if (launch_bwd_lat(a, w, st)) return MG_ERR_CUDA;
+    mk.mark("bwd_lat");
+    const int n = 3;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->last_launches = n;
+    return MG_OK;
+}
+
+mg_status_t mg_autotune(mg_context_t ctx, const mg_batch_t *b, int32_t kind, float cutoff, int32_t k, mg_graph_t *g,
+                        void *ws, size_t ws_bytes, void *stream) {
+    if (!ctx || (kind != MG_KIND_CUTOFF && kind != MG_KIND_KNN)) return MG_ERR_INVALID_ARGUMENT;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) return MG_ERR_CUDA;
+    float best = 1e30f;
+    int best_s = 1;
+    for (int sched = 1; sched <= 2; ++sched) {
+        mg_opts_t o = defaults(nullptr);
+        o.schedule = sched;
+        float tot = 0.f;
+        for (int rep = 0; rep < 4; ++rep) {
+            mg_status_t r;
+            cudaEventRecord(e0, st);
+            if (kind == MG_KIND_CUTOFF)
+                r = mg_cutoff_graph(ctx, b, cutoff, nullptr, &o, g, ws, ws_bytes, stream);
+            else
+                r = mg_knn_graph(ctx, b, k, &o, g, ws, ws_bytes, stream);
+            cudaEventRecord(e1, st);
+            if (r) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return r;
+            }
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tot += ms;  // first repetition warms up
+        }
+        if (tot < best) {
+            best = tot;
+            best_s = sched;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->tuned[kind - 1][size_class(b)] = best_s;
+    return MG_OK;
+}
+
+mg_status_t mg_profile_enable(mg_context_t ctx, int32_t on) {
+    if (!ctx) return MG_ERR_INVALID_ARGUMENT;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (on)  // create every event up front: nothing is created while a plan is captured
+        for (auto &p : ctx->prof)
+            for (auto &e : p.ev)
+                if (!e && cudaEventCreate(&e) != cudaSuccess) return MG_ERR_CUDA;
+    ctx->prof_on = on != 0;
+    return MG_OK;
+}
+
+int32_t mg_stage_times(mg_context_t ctx, int32_t which, int32_t max_stages, const char **names, float *ms) {
+    if (!ctx || which < 0 || which > 3) return -1;
+    Prof &p = ctx->prof[which];
+    if (!p.valid || p.n < 2) return -1;
+    if (cudaEventSynchronize(p.ev[p.n - 1]) != cudaSuccess) return -1;
+    const int stages = p.n - 1;
+    for (int q = 0; q < stages && q < max_stages; ++q) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, p.ev[q], p.ev[q + 1]);
+        if (names) names[q] = p.name[q + 1];
+        if (ms) ms[q] = t;
+    }
+    return stages;
+}
+
+int64_t mg_last_launch_count(mg_context_t ctx) {
+    if (!ctx) return -1;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return ctx->last_launches;
+}
+
+}  // extern "C"

@@ -1,0 +1,201 @@
+// Edge vectors and their backward pass for a fixed edge set (Sec. 1 and Sec. 4: the
+// graph is rebuilt from the geometry inside a generative model's forward pass, and the
+// loss is differentiated through v = (x_j - x_i + t) L and |v|).
+//
+//   fwd       one warp per source atom over its CSR segment: vec (compensated
+//             float-float evaluation, rounded once) and len.
+//   bwd_src   one warp per atom over its out-edges: g_e = dvec_e + dlen_e vec_e / len_e,
+//             the sum of g over out-edges and the per-atom lattice partial
+//             sum_e (x_j - x_i + t)^T g_e (FP32 lane sums, FP64 warp reduction).
+//   bwd_dst   one warp per atom over its in-edges in (dst, src, t) order (perm_dst):
+//             grad_frac[j] = (sum_in g - sum_out g) L^T.
+//   bwd_lat   one warp per structure: grad_lattice = sum of the atoms' partials in
+//             atom order.
+// Every sum runs in a fixed order, so the result does not depend on scheduling.
+#include "mg_device.cuh"
+#include "mg_launch.h"
+
+namespace mg {
+
+// Structure of global atom row `row` (binary search over atom_ptr), same in all lanes.
+__device__ __forceinline__ int structure_of(const int32_t *__restrict__ atom_ptr, int B, int row) {
+    int lo = 0, hi = B;  // atom_ptr[lo] <= row < atom_ptr[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (atom_ptr[mid] <= row) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) edgevec_fwd_kernel(EdgeVecArgs a) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = lane_id();
+    if (i >= a.N) return;
+    const int64_t E = a.g.edge_ptr[a.B];
+    if (E > a.g.capacity) return;
+    const int64_t lo = a.g.src_ptr[i], hi = a.g.src_ptr[i + 1];
+    if (hi <= lo) return;
+    const int s = structure_of(a.atom_ptr, a.B, i);
+    float L[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) L[q] = a.lattice[9 * (int64_t)s + q];
+    const float xi0 = a.frac[3 * (int64_t)i], xi1 = a.frac[3 * (int64_t)i + 1], xi2 = a.frac[3 * (int64_t)i + 2];
+    for (int64_t e = lo + lane; e < hi; e += 32) {
+        const int64_t j = a.g.dst[e];
+        const int t0 = a.g.offset[3 * e], t1 = a.g.offset[3 * e + 1], t2 = a.g.offset[3 * e + 2];
+        const float3 v = edge_vec_ff(L, xi0, xi1, xi2, a.frac[3 * j], a.frac[3 * j + 1], a.frac[3 * j + 2], t0, t1, t2);
+        if (a.out_vec) {
+            a.out_vec[3 * e] = v.x;
+            a.out_vec[3 * e + 1] = v.y;
+            a.out_vec[3 * e + 2] = v.z;
+        }
+        if (a.out_len) a.out_len[e] = vec_len(v);
+    }
+}
+
+cudaError_t launch_edgevec_fwd(const EdgeVecArgs &a, cudaStream_t s) {
+    if (a.N <= 0) return cudaSuccess;
+    edgevec_fwd_kernel<<<(a.N + 7) / 8, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// g_e from the upstream gradients.
+__device__ __forceinline__ float3 edge_g(const EdgeVecArgs &a, int64_t e) {
+    float3 g = make_float3(0.f, 0.f, 0.f);
+    if (a.grad_vec) g = make_float3(a.grad_vec[3 * e], a.grad_vec[3 * e + 1], a.grad_vec[3 * e + 2]);
+    if (a.grad_len) {
+        const float l = a.len[e];
+        if (l > 0.f) {
+            const float f = __fdiv_rn(a.grad_len[e], l);
+            g.x = __fmaf_rn(f, a.vec[3 * e], g.x);
+            g.y = __fmaf_rn(f, a.vec[3 * e + 1], g.y);
+            g.z = __fmaf_rn(f, a.vec[3 * e + 2], g.z);
+        }
+    }
+    return g;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(256) bwd_src_kernel(EdgeVecArgs a, double *__restrict__ gpart,
+                                                      double *__restrict__ lpart) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = lane_id();
+    if (i >= a.N) return;
+    const int64_t E = a.g.edge_ptr[a.B];
+    const int64_t lo = a.g.src_ptr[i], hi = (E > a.g.capacity) ? lo : a.g.src_ptr[i + 1];
+    const float xi0 = a.frac[3 * (int64_t)i], xi1 = a.frac[3 * (int64_t)i + 1], xi2 = a.frac[3 * (int64_t)i + 2];
+    float gs[3] = {0.f, 0.f, 0.f};
+    float M[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) M[q] = 0.f;
+    for (int64_t e = lo + lane; e < hi; e += 32) {
+        const float3 g = edge_g(a, e);
+        const int64_t j = a.g.dst[e];
+        const int t[3] = {a.g.offset[3 * e], a.g.offset[3 * e + 1], a.g.offset[3 * e + 2]};
+        const float xj[3] = {a.frac[3 * j], a.frac[3 * j + 1], a.frac[3 * j + 2]};
+        const float xi[3] = {xi0, xi1, xi2};
+        gs[0] += g.x;
+        gs[1] += g.y;
+        gs[2] += g.z;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            // df_k = x_j - x_i + t, carried exactly then rounded once
+            float s1, e1, s2, e2;
+            two_sum(xj[k], -xi[k], s1, e1);
+            two_sum(s1, (float)t[k], s2, e2);
+            const float df = __fadd_rn(s2, __fadd_rn(e2, e1));
+            M[3 * k + 0] = __fmaf_rn(df, g.x, M[3 * k + 0]);
+            M[3 * k + 1] = __fmaf_rn(df, g.y, M[3 * k + 1]);
+            M[3 * k + 2] = __fmaf_rn(df, g.z, M[3 * k + 2]);
+        }
+    }
+    double r[12];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) r[q] = warp_sum_d((double)gs[q]);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) r[3 + q] = warp_sum_d((double)M[q]);
+    if (lane == 0) {
+        gpart[3 * (int64_t)i + 0] = r[0];
+        gpart[3 * (int64_t)i + 1] = r[1];
+        gpart[3 * (int64_t)i + 2] = r[2];
+    }
+    if (lane < 9) {
+        double v = r[3];
+#pragma unroll
+        for (int q = 1; q < 9; ++q)
+            if (lane == q) v = r[3 + q];
+        lpart[9 * (int64_t)i + lane] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) bwd_dst_kernel(EdgeVecArgs a, const double *__restrict__ gpart) {
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = lane_id();
+    if (j >= a.N) return;
+    const int64_t E = a.g.edge_ptr[a.B];
+    const int64_t lo = a.g.dst_ptr[j], hi = (E > a.g.capacity) ? lo : a.g.dst_ptr[j + 1];
+    float gs[3] = {0.f, 0.f, 0.f};
+    for (int64_t p = lo + lane; p < hi; p += 32) {
+        const int64_t e = a.g.perm_dst[p];
+        const float3 g = edge_g(a, e);
+        gs[0] += g.x;
+        gs[1] += g.y;
+        gs[2] += g.z;
+    }
+    double tot[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) tot[q] = warp_sum_d((double)gs[q]) - gpart[3 * (int64_t)j + q];
+    if (lane < 3) {
+        const int s = structure_of(a.atom_ptr, a.B, j);
+        const float *L = a.lattice + 9 * (int64_t)s;
+        // (g L^T)_k = sum_c g_c L[k][c]
+        const double h = tot[0] * (double)L[3 * lane + 0] + tot[1] * (double)L[3 * lane + 1] +
+                         tot[2] * (double)L[3 * lane + 2];
+        a.grad_frac[3 * (int64_t)j + lane] = (float)h;
+    }
+}
+
+__global__ void __launch_bounds__(256) bwd_lat_kernel(EdgeVecArgs a, const double *__restrict__ lpart) {
+    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = lane_id();
+    if (s >= a.B) return;
+    const int lo = a.atom_ptr[s], hi = a.atom_ptr[s + 1];
+    double acc[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q] = 0.0;
+    for (int r = lo + lane; r < hi; r += 32)
+#pragma unroll
+        for (int q = 0; q < 9; ++q) acc[q] += lpart[9 * (int64_t)r + q];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q] = warp_sum_d(acc[q]);
+    if (lane < 9) {
+        double v = acc[0];
+#pragma unroll
+        for (int q = 1; q < 9; ++q)
+            if (lane == q) v = acc[q];
+        a.grad_lattice[9 * (int64_t)s + lane] = (float)v;
+    }
+}
+
+cudaError_t launch_bwd_src(const EdgeVecArgs &a, const Work &w, cudaStream_t s) {
+    if (a.N > 0) bwd_src_kernel<<<(a.N + 7) / 8, 256, 0, s>>>(a, w.gpart, w.lpart);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_dst(const EdgeVecArgs &a, const Work &w, cudaStream_t s) {
+    if (a.N > 0) bwd_dst_kernel<<<(a.N + 7) / 8, 256, 0, s>>>(a, w.gpart);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_lat(const EdgeVecArgs &a, const Work &w, cudaStream_t s) {
+    if (a.B > 0) bwd_lat_kernel<<<(a.B + 7) / 8, 256, 0, s>>>(a, w.lpart);
+    return cudaGetLastError();
+}
+
+}  // namespace mg

@@ -1,0 +1,548 @@
+// Batched cutoff-graph construction (Def. 3, Sec. 2.1) on sm_103a:
+//   prep      one warp per structure: FP64 lattice inverse, interplanar spacings,
+//             FP32 Cartesian positions, FP32 error bound and re-test band;
+//   count     one warp per source atom: FP32 scan of the periodic images inside the
+//             interplanar box (Sec. 2.2's evaluated area), FP64 re-test in the band;
+//   scan      exclusive prefix of the counts (tile reduce, top scan, tile apply);
+//   finalize  per-structure edge pointers, edge count, capacity check;
+//   write     the same scan again, emitting (src, dst, t, vec, len) in canonical order;
+//   dst sort  edge ids ordered by (dst, src, t) for the deterministic backward pass.
+#include <cstdio>
+
+#include "mg_device.cuh"
+#include "mg_enum.cuh"
+#include "mg_launch.h"
+
+namespace mg {
+
+// ============================================================================ prep
+
+__global__ void __launch_bounds__(128) prep_kernel(PrepArgs a, StructRec *__restrict__ recs,
+                                                    float4 *__restrict__ pos,
+                                                    int32_t *__restrict__ atom_struct) {
+    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = lane_id();
+    if (s >= a.B) return;
+    const int begin = a.atom_ptr[s], end = a.atom_ptr[s + 1];
+    float Lf[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Lf[q] = a.lattice[9 * (int64_t)s + q];
+    float xm0 = 0.f, xm1 = 0.f, xm2 = 0.f;
+    int nonfinite = 0;
+    for (int r = begin + lane; r < end; r += 32) {
+        const float x0 = a.frac[3 * (int64_t)r], x1 = a.frac[3 * (int64_t)r + 1], x2 = a.frac[3 * (int64_t)r + 2];
+        if (!isfinite(x0) || !isfinite(x1) || !isfinite(x2)) nonfinite = 1;
+        const float3 p = cart(Lf, x0, x1, x2);
+        pos[r] = make_float4(p.x, p.y, p.z, 0.f);
+        atom_struct[r] = s;
+        xm0 = fmaxf(xm0, fabsf(x0));
+        xm1 = fmaxf(xm1, fabsf(x1));
+        xm2 = fmaxf(xm2, fabsf(x2));
+    }
+    xm0 = warp_max(xm0);
+    xm1 = warp_max(xm1);
+    xm2 = warp_max(xm2);
+    nonfinite = __any_sync(FULL, nonfinite);
+    if (lane != 0) return;
+
+    StructRec R;
+    double L[9];
+    int bad = 0;
+    for (int q = 0; q < 9; ++q) {
+        R.L[q] = Lf[q];
+        L[q] = (double)Lf[q];
+        if (!isfinite(Lf[q])) bad = MG_ERR_NONFINITE_INPUT;
+    }
+    if (nonfinite) bad = MG_ERR_NONFINITE_INPUT;
+    // FP64 inverse by cofactors (row-vector convention: f = v L^-1)
+    const double c00 = L[4] * L[8] - L[5] * L[7], c01 = L[5] * L[6] - L[3] * L[8], c02 = L[3] * L[7] - L[4] * L[6];
+    const double c10 = L[2] * L[7] - L[1] * L[8], c11 = L[0] * L[8] - L[2] * L[6], c12 = L[1] * L[6] - L[0] * L[7];
+    const double c20 = L[1] * L[5] - L[2] * L[4], c21 = L[2] * L[3] - L[0] * L[5], c22 = L[0] * L[4] - L[1] * L[3];
+    const double det = L[0] * c00 + L[1] * c01 + L[2] * c02;
+    const double la = sqrt(L[0] * L[0] + L[1] * L[1] + L[2] * L[2]);
+    const double lb = sqrt(L[3] * L[3] + L[4] * L[4] + L[5] * L[5]);
+    const double lc = sqrt(L[6] * L[6] + L[7] * L[7] + L[8] * L[8]);
+    if (!bad && (!(fabs(det) > 1e-9 * la * lb * lc) || !isfinite(det))) bad = MG_ERR_SINGULAR_LATTICE;
+    // Linv[c][k] = cofactor[k][c] / det ; column k of Linv = (c_k0, c_k1, c_k2) / det
+    const double cof[3][3] = {{c00, c01, c02}, {c10, c11, c12}, {c20, c21, c22}};
+    const double xm[3] = {(double)xm0, (double)xm1, (double)xm2};
+    double invd[3];
+    for (int k = 0; k < 3; ++k) {
+        const double n2 = cof[k][0] * cof[k][0] + cof[k][1] * cof[k][1] + cof[k][2] * cof[k][2];
+        invd[k] = bad ? 1.0 : sqrt(n2) / fabs(det);
+        R.invd[k] = __double2float_ru(invd[k] * (1.0 + 1e-6));
+    }
+    double c;
+    const int n = end - begin;
+    if (a.knn_k > 0) {
+        const double V = fabs(det);
+        c = 1.1 * cbrt(3.0 * (a.knn_k + 1) * V / (4.0 * 3.14159265358979 * (n > 0 ? n : 1)));
+        if (!(c > 0.0) || !isfinite(c)) c = 1.0;
+    } else {
+        c = a.cutoff_ps ? (double)a.cutoff_ps[s] : (double)a.cutoff;
+        if (!bad && (!(c > 0.0) || !isfinite(c))) bad = MG_ERR_INVALID_ARGUMENT;
+    }
+    R.cut = (float)c;
+    for (int cc = 0; cc < 3; ++cc) {
+        double P = 0.0, Lt = 0.0, C = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            const double al = fabs(L[3 * k + cc]);
+            P += xm[k] * al;
+            Lt += (double)R.invd[k] * al;
+            C += (2.0 * xm[k] + 1.0) * al;
+        }
+        R.errP[cc] = __double2float_ru(P * (1.0 + 1e-6));
+        R.errL[cc] = __double2float_ru(Lt * (1.0 + 1e-6));
+        R.errC[cc] = __double2float_ru(C * (1.0 + 1e-6));
+    }
+    R.L2norm2 = Lf[6] * Lf[6] + Lf[7] * Lf[7] + Lf[8] * Lf[8];
+    R.L2norm = sqrtf(R.L2norm2);
+    const double cr = (double)R.cut;
+    R.rr = cr * cr;
+    // re-test band around the cutoff: FP32 error bound, widened to the requested band
+    {
+        const double u8 = 8.0 * 5.9604644775390625e-8;
+        double en2 = 0.0;
+        for (int cc = 0; cc < 3; ++cc) {
+            const double e = u8 * (2.0 * R.errP[cc] + cr * R.errL[cc] + R.errC[cc]);
+            en2 += e * e;
+        }
+        const double en = sqrt(en2) * 1.01;
+        const double dv = cr * 1.01 + en;
+        const double fp = 2.0 * (3.1 * 5.9604644775390625e-8 * dv * dv + 2.0 * dv * en + en * en);
+        const double band = fmax(fp, 2.0 * (double)a.band_rel * R.rr);
+        R.thr_lo = __double2float_rd(R.rr - band);
+        R.thr_hi = __double2float_ru(R.rr + band);
+    }
+    R.atom_begin = begin;
+    R.n_atoms = n;
+    R.bad = bad;
+    R.pad = 0;
+    recs[s] = R;
+    if (bad) set_error(a.status, bad, s);
+}
+
+cudaError_t launch_prep(const PrepArgs &a, const Work &w, cudaStream_t s) {
+    if (a.B <= 0) return cudaSuccess;
+    const int threads = 128;
+    const int blocks = (a.B * 32 + threads - 1) / threads;
+    prep_kernel<<<blocks, threads, 0, s>>>(a, w.recs, w.pos, w.atom_struct);
+    return cudaGetLastError();
+}
+
+// ============================================================================ scan
+
+__device__ __forceinline__ long long block_excl_scan_ll(long long v, long long *sm, long long &total) {
+    // 256 threads: warp scans, then a scan of the 8 warp totals
+    const int lane = lane_id(), wid = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sm[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        long long t = (lane < (int)(blockDim.x >> 5)) ? sm[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(FULL, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < 32) sm[lane + 32] = t;
+    }
+    __syncthreads();
+    const long long warp_prefix = wid ? sm[32 + wid - 1] : 0;
+    total = sm[32 + (blockDim.x >> 5) - 1];
+    __syncthreads();
+    return warp_prefix + x - v;
+}
+
+__global__ void __launch_bounds__(256) scan_reduce_kernel(const int32_t *__restrict__ cnt, int n,
+                                                          long long *__restrict__ tile_sum) {
+    __shared__ long long sm[64];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    long long v = 0;
+    for (int q = threadIdx.x; q < SCAN_TILE; q += 256)
+        if (base + q < n) v += cnt[base + q];
+    long long tot;
+    block_excl_scan_ll(v, sm, tot);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(256) scan_top_kernel(long long *__restrict__ tile_sum, int ntiles) {
+    __shared__ long long sm[64];
+    long long carry = 0;
+    for (int b0 = 0; b0 < ntiles; b0 += 256) {
+        const int q = b0 + threadIdx.x;
+        const long long v = q < ntiles ? tile_sum[q] : 0;
+        long long tot;
+        const long long ex = block_excl_scan_ll(v, sm, tot);
+        if (q < ntiles) tile_sum[q] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) tile_sum[ntiles] = carry;
+}
+
+// Each thread scans 16 consecutive counts of the tile.
+__global__ void __launch_bounds__(256) scan_apply_kernel(const int32_t *__restrict__ cnt, int n,
+                                                         const long long *__restrict__ tile_off,
+                                                         int ntiles, int64_t *__restrict__ out) {
+    __shared__ long long sm[64];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + 16 * threadIdx.x;
+    int vals[16];
+    long long mysum = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        vals[q] = (base + q < n) ? cnt[base + q] : 0;
+        mysum += vals[q];
+    }
+    long long tot;
+    long long run = block_excl_scan_ll(mysum, sm, tot) + tile_off[blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        if (base + q < n) out[base + q] = run;
+        run += vals[q];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = tile_off[ntiles];
+}
+
+__global__ void add_base_kernel(int64_t *__restrict__ out, int n, const int64_t *__restrict__ base) {
+    const int64_t b = *base;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q <= n; q += (int64_t)gridDim.x * blockDim.x)
+        out[q] += b;
+}
+
+cudaError_t launch_scan(const ScanArgs &a, const Work &w, cudaStream_t s) {
+    const int ntiles = (a.n + SCAN_TILE - 1) / SCAN_TILE;
+    if (ntiles == 0) {
+        cudaMemsetAsync(a.out_ptr, 0, sizeof(int64_t), s);
+        return cudaGetLastError();
+    }
+    scan_reduce_kernel<<<ntiles, 256, 0, s>>>(a.cnt, a.n, w.tile_sum);
+    scan_top_kernel<<<1, 256, 0, s>>>(w.tile_sum, ntiles);
+    scan_apply_kernel<<<ntiles, 256, 0, s>>>(a.cnt, a.n, w.tile_sum, ntiles, a.out_ptr);
+    return cudaGetLastError();
+}
+
+// ============================================================================ schedule
+
+// Work distribution over source atoms [lo, hi): flat (one warp per atom) or a persistent
+// grid whose warps pull atoms from a counter (w.queue[0]) until the range is exhausted.
+template <int SCHED>
+struct AtomLoop {
+    int lo, hi;
+    unsigned int *queue;
+    __device__ __forceinline__ int first() {
+        if (SCHED == 1) {
+            const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+            return lo + gw;
+        }
+        return next();
+    }
+    __device__ __forceinline__ int next() {
+        if (SCHED == 1) return hi;
+        unsigned int v = 0;
+        if (lane_id() == 0) v = atomicAdd(queue, 1u);
+        v = __shfl_sync(FULL, v, 0);
+        return lo + (int)v;
+    }
+};
+
+// ============================================================================ cutoff count
+
+template <int SCHED>
+__global__ void __launch_bounds__(256) cutoff_count_kernel(BuildArgs a, Work w) {
+    AtomLoop<SCHED> loop{a.atom_lo, a.atom_hi, w.queue};
+    unsigned long long nre = 0, ncand = 0;
+    for (int i = loop.first(); i < a.atom_hi; i = loop.next()) {
+        const int s = w.atom_struct[i];
+        const StructRec &R = w.recs[s];
+        if (R.bad) {
+            if (lane_id() == 0) w.cnt[i] = 0;
+            continue;
+        }
+        Source S;
+        load_source(S, w.recs, s, a.frac, w.pos, i);
+        const float thr_lo = R.thr_lo, thr_hi = R.thr_hi;
+        const double rr = R.rr;
+        int count = 0;
+        for_each_candidate(S, a.frac, w.pos, R.cut, [&](bool vc, float d2, bool self, int ow, int t2,
+                                                         const RowRegs &rw) {
+            const bool cand = vc && !self;
+            bool in = cand && d2 < thr_lo;
+            const bool band = cand && !in && d2 <= thr_hi;
+            if (__any_sync(FULL, band)) {
+                const int jj = __shfl_sync(FULL, rw.j, ow);
+                const int t0 = __shfl_sync(FULL, rw.t0, ow);
+                const int t1 = __shfl_sync(FULL, rw.t1, ow);
+                if (band) {
+                    const int64_t jr = (int64_t)S.begin + jj;
+                    const double d = canon_d2(S.L, S.xi0, S.xi1, S.xi2, a.frac[3 * jr], a.frac[3 * jr + 1],
+                                              a.frac[3 * jr + 2], t0, t1, t2);
+                    in = d < rr;
+                }
+                nre += __popc(__ballot_sync(FULL, band));
+            }
+            count += __popc(__ballot_sync(FULL, in));
+            ncand += __popc(__ballot_sync(FULL, cand));
+        });
+        if (lane_id() == 0) w.cnt[i] = count;
+    }
+    if (a.collect_stats && lane_id() == 0 && ncand) {
+        Status *st = reinterpret_cast<Status *>(a.g.status);
+        atomicAdd(&st->rechecked, nre);
+        atomicAdd(&st->candidates, ncand);
+    }
+}
+
+static int blocks_for(int atoms, int threads) {
+    const int warps = threads / 32;
+    return (atoms + warps - 1) / warps;
+}
+
+static int persistent_blocks(const void *kernel, int threads) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+    if (per_sm < 1) per_sm = 1;
+    return per_sm * num_sms();
+}
+
+cudaError_t launch_reset_queue(const Work &w, cudaStream_t s) {
+    return cudaMemsetAsync(w.queue, 0, 4 * sizeof(unsigned int), s);
+}
+
+cudaError_t launch_cutoff_count(const BuildArgs &a, const Work &w, cudaStream_t s) {
+    const int atoms = a.atom_hi - a.atom_lo;
+    if (atoms <= 0) return cudaSuccess;
+    const int threads = 256;
+    if (a.schedule == 2) {
+        cudaError_t e = launch_reset_queue(w, s);
+        if (e) return e;
+        int blocks = persistent_blocks((const void *)cutoff_count_kernel<2>, threads);
+        blocks = min(blocks, blocks_for(atoms, threads));
+        cutoff_count_kernel<2><<<blocks, threads, 0, s>>>(a, w);
+    } else {
+        cutoff_count_kernel<1><<<blocks_for(atoms, threads), threads, 0, s>>>(a, w);
+    }
+    return cudaGetLastError();
+}
+
+// ============================================================================ finalize
+
+// After the scan of per-atom counts: edge_ptr[s] = src_ptr[atom_ptr[s]], edge count and
+// capacity check.  For a per-structure build (B == 1 slice) the same holds with the
+// pointers offset by the caller.
+__global__ void cutoff_finalize_kernel(int B, const int32_t *__restrict__ atom_ptr, int N,
+                                       const int64_t *__restrict__ src_ptr, int64_t *__restrict__ edge_ptr,
+                                       int64_t capacity, mg_device_status_t *status) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s <= B; s += gridDim.x * blockDim.x) {
+        const int a = (s == B) ? N : atom_ptr[s];
+        edge_ptr[s] = src_ptr[a];
+        if (s == B) {
+            const long long tot = src_ptr[N];
+            Status *st = reinterpret_cast<Status *>(status);
+            st->num_edges = (unsigned long long)tot;
+            st->required_capacity = (unsigned long long)tot;
+            if (tot > capacity) set_error(status, MG_ERR_CAPACITY, -1);
+        }
+    }
+}
+
+cudaError_t launch_cutoff_finalize(const BuildArgs &a, const Work &w, cudaStream_t s) {
+    const int threads = 256;
+    const int blocks = min(1024, (a.B + 1 + threads - 1) / threads);
+    cutoff_finalize_kernel<<<blocks, threads, 0, s>>>(a.B, a.atom_ptr, a.N, a.src_ptr, a.g.edge_ptr,
+                                                      a.g.capacity, a.g.status);
+    return cudaGetLastError();
+}
+
+// ============================================================================ cutoff write
+
+template <int SCHED>
+__global__ void __launch_bounds__(256) cutoff_write_kernel(BuildArgs a, Work w) {
+    AtomLoop<SCHED> loop{a.atom_lo, a.atom_hi, w.queue};
+    const mg_graph_t g = a.g;
+    for (int i = loop.first(); i < a.atom_hi; i = loop.next()) {
+        const int64_t base = a.src_ptr[i];
+        const int64_t endp = a.src_ptr[i + 1];
+        if (endp > g.capacity || endp == base) continue;  // capacity error already reported
+        const int s = w.atom_struct[i];
+        const StructRec &R = w.recs[s];
+        if (R.bad) continue;
+        Source S;
+        load_source(S, w.recs, s, a.frac, w.pos, i);
+        const float thr_lo = R.thr_lo, thr_hi = R.thr_hi;
+        const double rr = R.rr;
+        int64_t out = base;
+        const unsigned lt = (1u << lane_id()) - 1u;
+        for_each_candidate(S, a.frac, w.pos, R.cut, [&](bool vc, float d2, bool self, int ow, int t2,
+                                                         const RowRegs &rw) {
+            const bool cand = vc && !self;
+            bool in = cand && d2 < thr_lo;
+            const bool band = cand && !in && d2 <= thr_hi;
+            if (__any_sync(FULL, in || band)) {
+                const int jj = __shfl_sync(FULL, rw.j, ow);
+                const int t0 = __shfl_sync(FULL, rw.t0, ow);
+                const int t1 = __shfl_sync(FULL, rw.t1, ow);
+                const int64_t jr = (int64_t)S.begin + jj;
+                float xj0 = 0.f, xj1 = 0.f, xj2 = 0.f;
+                if (in || band) {
+                    xj0 = a.frac[3 * jr];
+                    xj1 = a.frac[3 * jr + 1];
+                    xj2 = a.frac[3 * jr + 2];
+                }
+                if (band) in = canon_d2(S.L, S.xi0, S.xi1, S.xi2, xj0, xj1, xj2, t0, t1, t2) < rr;
+                const unsigned bal = __ballot_sync(FULL, in);
+                if (in) {
+                    const int64_t e = out + __popc(bal & lt);
+                    if (e < endp) {
+                        g.src[e] = i;
+                        g.dst[e] = (int32_t)jr;
+                        g.offset[3 * e + 0] = t0;
+                        g.offset[3 * e + 1] = t1;
+                        g.offset[3 * e + 2] = t2;
+                        if (g.vec || g.len) {
+                            const float3 v = edge_vec_ff(S.L, S.xi0, S.xi1, S.xi2, xj0, xj1, xj2, t0, t1, t2);
+                            if (g.vec) {
+                                g.vec[3 * e + 0] = v.x;
+                                g.vec[3 * e + 1] = v.y;
+                                g.vec[3 * e + 2] = v.z;
+                            }
+                            if (g.len) g.len[e] = vec_len(v);
+                        }
+                    }
+                }
+                out += __popc(bal);
+            }
+        });
+        if (lane_id() == 0 && out != endp) set_error(g.status, MG_ERR_INTERNAL, s);  // count/write mismatch
+    }
+}
+
+cudaError_t launch_cutoff_write(const BuildArgs &a, const Work &w, cudaStream_t s) {
+    const int atoms = a.atom_hi - a.atom_lo;
+    if (atoms <= 0) return cudaSuccess;
+    const int threads = 256;
+    if (a.schedule == 2) {
+        cudaError_t e = launch_reset_queue(w, s);
+        if (e) return e;
+        int blocks = persistent_blocks((const void *)cutoff_write_kernel<2>, threads);
+        blocks = min(blocks, blocks_for(atoms, threads));
+        cutoff_write_kernel<2><<<blocks, threads, 0, s>>>(a, w);
+    } else {
+        cutoff_write_kernel<1><<<blocks_for(atoms, threads), threads, 0, s>>>(a, w);
+    }
+    return cudaGetLastError();
+}
+
+// ============================================================================ dst sort
+
+__global__ void dst_hist_kernel(const int32_t *__restrict__ dst, const int64_t *__restrict__ E_dev,
+                                int64_t capacity, int32_t *__restrict__ deg) {
+    const int64_t E = *E_dev;
+    if (E > capacity) return;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&deg[dst[e]], 1);
+}
+
+__global__ void dst_scatter_kernel(const int32_t *__restrict__ dst, const int64_t *__restrict__ E_dev,
+                                   int64_t capacity, const int64_t *__restrict__ dst_ptr,
+                                   int32_t *__restrict__ cursor, int32_t *__restrict__ perm) {
+    const int64_t E = *E_dev;
+    if (E > capacity) return;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        const int d = dst[e];
+        perm[dst_ptr[d] + atomicAdd(&cursor[d], 1)] = (int32_t)e;
+    }
+}
+
+constexpr int SEG_SMEM = 2048;  // per-warp shared-memory sort capacity (edge ids)
+
+__device__ __forceinline__ int warp_sort32_int(int x) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+        const bool desc = (lane & size) != 0;
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const int y = __shfl_xor_sync(FULL, x, stride);
+            const bool lower = (lane & stride) == 0;
+            x = (lower != desc) ? min(x, y) : max(x, y);
+        }
+    }
+    return x;
+}
+
+// Warp per destination atom: sort its segment of perm_dst ascending (edge ids are in
+// canonical (src, dst, t) order, so this yields (dst, src, t) order).
+__global__ void __launch_bounds__(128) dst_segsort_kernel(int N, const int64_t *__restrict__ dst_ptr,
+                                                          const int64_t *__restrict__ E_dev, int64_t capacity,
+                                                          int32_t *__restrict__ perm, int32_t *__restrict__ tmp) {
+    __shared__ int32_t sm[4][SEG_SMEM];
+    if (*E_dev > capacity) return;
+    const int wid = threadIdx.x >> 5, lane = lane_id();
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= N) return;
+    const int64_t lo = dst_ptr[j], hi = dst_ptr[j + 1];
+    const int n = (int)(hi - lo);
+    if (n <= 1) return;
+    if (n <= 32) {
+        int v = lane < n ? perm[lo + lane] : 0x7fffffff;
+        v = warp_sort32_int(v);
+        if (lane < n) perm[lo + lane] = v;
+        return;
+    }
+    if (n <= SEG_SMEM) {
+        int P = 64;
+        while (P < n) P <<= 1;
+        int32_t *b = sm[wid];
+        for (int q = lane; q < P; q += 32) b[q] = q < n ? perm[lo + q] : 0x7fffffff;
+        __syncwarp();
+        for (int size = 2; size <= P; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int q = lane; q < P / 2; q += 32) {
+                    const int x = 2 * stride * (q / stride) + (q % stride);
+                    const int y = x + stride;
+                    const bool asc = (x & size) == 0;
+                    const int vx = b[x], vy = b[y];
+                    if ((vx > vy) == asc) {
+                        b[x] = vy;
+                        b[y] = vx;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        for (int q = lane; q < n; q += 32) perm[lo + q] = b[q];
+        return;
+    }
+    // long segment: rank sort through scratch (ids are distinct)
+    for (int64_t q = lo + lane; q < hi; q += 32) tmp[q] = perm[q];
+    __syncwarp();
+    for (int64_t q = lo + lane; q < hi; q += 32) {
+        const int v = tmp[q];
+        int64_t rank = 0;
+        for (int64_t r = lo; r < hi; ++r) rank += tmp[r] < v;
+        perm[lo + rank] = v;
+    }
+}
+
+cudaError_t launch_dst_sort(const BuildArgs &a, const Work &w, cudaStream_t s, int *launches) {
+    const mg_graph_t &g = a.g;
+    const int64_t *E_dev = g.edge_ptr + a.B;
+    const int grid = 4 * num_sms();
+    cudaMemsetAsync(w.cnt, 0, sizeof(int32_t) * (size_t)(a.N > 0 ? a.N : 1), s);
+    dst_hist_kernel<<<grid, 256, 0, s>>>(g.dst, E_dev, g.capacity, w.cnt);
+    ScanArgs sa{a.N, w.cnt, g.dst_ptr};
+    cudaError_t e = launch_scan(sa, w, s);
+    if (e) return e;
+    cudaMemsetAsync(w.cursor, 0, sizeof(int32_t) * (size_t)(a.N > 0 ? a.N : 1), s);
+    dst_scatter_kernel<<<grid, 256, 0, s>>>(g.dst, E_dev, g.capacity, g.dst_ptr, w.cursor, g.perm_dst);
+    if (a.N > 0) dst_segsort_kernel<<<(a.N + 3) / 4, 128, 0, s>>>(a.N, g.dst_ptr, E_dev, g.capacity, g.perm_dst, w.sort_tmp);
+    if (launches) *launches += 6;
+    return cudaGetLastError();
+}
+
+}  // namespace mg

@@ -1,0 +1,373 @@
+// KNN multigraph construction (Sec. 2.1 after Def. 3; Alg. 1 and Alg. 2) on sm_103a.
+//
+// One warp per source atom.  Alg. 1 grows the evaluated area until the k-th distance
+// d^max_i is covered; Alg. 2 keeps the k closest in an "ordered stack".  Here:
+//   pass 1  scan every image within radius rho (interplanar box, mg_enum.cuh) and keep
+//           the k smallest FP32 squared distances in registers: a sorted 32*S-entry
+//           array spread over the lanes, updated by warp-shuffle bitonic merges.  If
+//           fewer than k images lie within rho, or the k-th distance tau is not covered
+//           by rho with the error band to spare, rho grows and the pass repeats (the
+//           covered-radius test plays the role of closest_distance(border, rho)).
+//   pass 2  the same scan again: images with FP32 d2 < tau - 2 delta are certainly
+//           among the k nearest; images within tau +- 2 delta are re-ranked by the
+//           canonical FP64 distance with the (d2, j, t) tie-break in a second register
+//           top-k; the k winners are sorted by (j, t) and written in canonical order.
+// delta bounds the FP32 error (fp32_d2_error) plus the requested band.
+#include "mg_device.cuh"
+#include "mg_enum.cuh"
+#include "mg_launch.h"
+
+namespace mg {
+
+// ------------------------------------------------------------------ key types
+
+struct FKey {
+    float v;
+};
+__device__ __forceinline__ FKey kshfl(FKey k, int src) { return FKey{__shfl_sync(FULL, k.v, src)}; }
+__device__ __forceinline__ FKey kxor(FKey k, int m) { return FKey{__shfl_xor_sync(FULL, k.v, m)}; }
+__device__ __forceinline__ bool kless(FKey a, FKey b) { return a.v < b.v; }
+__device__ __forceinline__ FKey kinf(FKey) { return FKey{F_INF}; }
+
+// Exact key: canonical FP64 d2 (non-negative, so its bit pattern orders like the value),
+// then (local j << 32 | packed t).
+struct XKey {
+    unsigned long long d, jt;
+};
+__device__ __forceinline__ XKey kshfl(XKey k, int src) {
+    return XKey{__shfl_sync(FULL, k.d, src), __shfl_sync(FULL, k.jt, src)};
+}
+__device__ __forceinline__ XKey kxor(XKey k, int m) {
+    return XKey{__shfl_xor_sync(FULL, k.d, m), __shfl_xor_sync(FULL, k.jt, m)};
+}
+__device__ __forceinline__ bool kless(XKey a, XKey b) { return a.d < b.d || (a.d == b.d && a.jt < b.jt); }
+__device__ __forceinline__ XKey kinf(XKey) { return XKey{~0ull, ~0ull}; }
+
+template <class K>
+__device__ __forceinline__ K kmin(K a, K b) { return kless(b, a) ? b : a; }
+template <class K>
+__device__ __forceinline__ K kmax(K a, K b) { return kless(b, a) ? a : b; }
+
+// Bitonic sort of one key per lane, ascending by lane.
+template <class K>
+__device__ __forceinline__ K warp_bitonic_sort(K x) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+        const bool desc = (lane & size) != 0;
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const K y = kxor(x, stride);
+            const bool lower = (lane & stride) == 0;
+            x = (lower != desc) ? kmin(x, y) : kmax(x, y);
+        }
+    }
+    return x;
+}
+
+// A bitonic sequence across the lanes, sorted ascending.
+template <class K>
+__device__ __forceinline__ K warp_bitonic_merge(K x) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int stride = 16; stride > 0; stride >>= 1) {
+        const K y = kxor(x, stride);
+        x = ((lane & stride) == 0) ? kmin(x, y) : kmax(x, y);
+    }
+    return x;
+}
+
+// The 32*S smallest keys seen so far, sorted: slot s of lane l holds rank 32 s + l.
+template <class K, int S>
+struct TopK {
+    K a[S];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int s = 0; s < S; ++s) a[s] = kinf(K{});
+    }
+    // Merge one key per lane (kinf for none).
+    __device__ __forceinline__ void insert(K b) {
+        const int lane = lane_id();
+        b = warp_bitonic_sort(b);
+        // the 32 smallest of the top block and b (a bitonic split), sorted
+        K m = kmin(a[S - 1], kshfl(b, 31 - lane));
+        m = warp_bitonic_merge(m);
+        // ripple m down through the sorted blocks
+#pragma unroll
+        for (int s = 0; s < S - 1; ++s) {
+            const K rm = kshfl(m, 31 - lane);
+            const K lo = kmin(a[s], rm), hi = kmax(a[s], rm);
+            a[s] = warp_bitonic_merge(lo);
+            m = warp_bitonic_merge(hi);
+        }
+        a[S - 1] = m;
+    }
+    // The r-th smallest (1-based, r <= 32 S), the same in every lane.
+    __device__ __forceinline__ K kth(int r) const {
+        const int idx = r - 1, blk = idx >> 5, l = idx & 31;
+        K v = a[0];
+#pragma unroll
+        for (int s = 1; s < S; ++s)
+            if (s == blk) v = a[s];
+        return kshfl(v, l);
+    }
+};
+
+// Sort n (<= P, P a power of two >= 64) 64-bit keys in shared memory with one warp.
+__device__ __forceinline__ void warp_smem_sort_u64(unsigned long long *b, int n, int P) {
+    const int lane = lane_id();
+    for (int q = n + lane; q < P; q += 32) b[q] = ~0ull;
+    __syncwarp();
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int q = lane; q < P / 2; q += 32) {
+                const int x = 2 * stride * (q / stride) + (q % stride);
+                const int y = x + stride;
+                const bool asc = (x & size) == 0;
+                const unsigned long long vx = b[x], vy = b[y];
+                if ((vx > vy) == asc) {
+                    b[x] = vy;
+                    b[y] = vx;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Work distribution over source atoms (same scheme as the cutoff kernels).
+template <int SCHED>
+struct KnnLoop {
+    int lo, hi;
+    unsigned int *queue;
+    __device__ __forceinline__ int first() {
+        if (SCHED == 1) return lo + (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+        return next();
+    }
+    __device__ __forceinline__ int next() {
+        if (SCHED == 1) return hi;
+        unsigned int v = 0;
+        if (lane_id() == 0) v = atomicAdd(queue + 1, 1u);
+        v = __shfl_sync(FULL, v, 0);
+        return lo + (int)v;
+    }
+};
+
+constexpr int KNN_WARPS = 4;
+
+template <int S, int SCHED>
+__global__ void __launch_bounds__(KNN_WARPS * 32) knn_kernel(BuildArgs a, Work w) {
+    __shared__ unsigned long long sel_all[KNN_WARPS][S * 32 > 64 ? S * 32 : 64];
+    const int wid = threadIdx.x >> 5, lane = lane_id();
+    unsigned long long *sel = sel_all[wid];
+    const int k = a.knn_k;
+    const unsigned lt = (1u << lane) - 1u;
+    const mg_graph_t g = a.g;
+    KnnLoop<SCHED> loop{a.atom_lo, a.atom_hi, w.queue};
+    unsigned long long nre = 0, ncand = 0;
+
+    for (int i = loop.first(); i < a.atom_hi; i = loop.next()) {
+        const int s = w.atom_struct[i];
+        const StructRec &R = w.recs[s];
+        if (R.bad) continue;
+        Source Src;
+        load_source(Src, w.recs, s, a.frac, w.pos, i);
+
+        // ---------------- pass 1: grow rho until the k-th FP32 distance is covered
+        float rho = R.cut, tau = F_INF, delta = 0.f;
+        bool ok = false;
+        for (int iter = 0; iter < 64 && !ok; ++iter) {
+            TopK<FKey, S> tk;
+            tk.init();
+            float thr = F_INF;
+            int found = 0;
+            const float rho2 = rho * rho;
+            for_each_candidate(Src, a.frac, w.pos, rho, [&](bool vc, float d2, bool self, int, int,
+                                                              const RowRegs &) {
+                const bool c = vc && !self && d2 < rho2;
+                found += __popc(__ballot_sync(FULL, c));
+                const float v = c ? d2 : F_INF;
+                if (__any_sync(FULL, v < thr)) {
+                    tk.insert(FKey{v < thr ? v : F_INF});
+                    thr = tk.kth(k).v;
+                }
+                if (a.collect_stats) ncand += __popc(__ballot_sync(FULL, vc && !self));
+            });
+            delta = fp32_d2_error(R, rho, rho2) + 2.0f * a.band_rel * rho2;
+            if (found >= k && thr + 3.0f * delta < rho2) {
+                tau = thr;
+                ok = true;
+            } else if (found >= k) {
+                rho = sqrtf(thr + 3.0f * delta) * 1.0005f + 1e-6f;
+            } else {
+                rho *= 1.5f;
+            }
+            if (!(rho < 1e6f)) break;
+        }
+        if (!ok) {
+            if (lane == 0) set_error(g.status, MG_ERR_OFFSET_RANGE, s);
+            continue;
+        }
+
+        // ---------------- pass 2: certain members, FP64 re-rank of the band
+        const float lo_thr = tau - 2.0f * delta, hi_thr = tau + 2.0f * delta;
+        int m = 0;
+        bool range_bad = false;
+        TopK<XKey, S> ek;
+        ek.init();
+        XKey ethr = kinf(XKey{});
+        for_each_candidate(Src, a.frac, w.pos, rho, [&](bool vc, float d2, bool self, int ow, int t2,
+                                                          const RowRegs &rw) {
+            const bool c = vc && !self;
+            const bool in = c && d2 < lo_thr;
+            const bool band = c && !in && d2 <= hi_thr;
+            if (__any_sync(FULL, in || band)) {
+                const int jj = __shfl_sync(FULL, rw.j, ow);
+                const int t0 = __shfl_sync(FULL, rw.t0, ow);
+                const int t1 = __shfl_sync(FULL, rw.t1, ow);
+                if ((in || band) && (abs(t0) > OFFSET_KEY_LIM || abs(t1) > OFFSET_KEY_LIM || abs(t2) > OFFSET_KEY_LIM))
+                    range_bad = true;
+                const unsigned long long jt = ((unsigned long long)(unsigned)jj << 32) | pack_t(t0, t1, t2);
+                const unsigned bin = __ballot_sync(FULL, in);
+                if (in) {
+                    const int p = m + __popc(bin & lt);
+                    if (p < k) sel[p] = jt;
+                }
+                m += __popc(bin);
+                XKey key = kinf(XKey{});
+                if (band) {
+                    const int64_t jr = (int64_t)Src.begin + jj;
+                    const double d = canon_d2(Src.L, Src.xi0, Src.xi1, Src.xi2, a.frac[3 * jr], a.frac[3 * jr + 1],
+                                              a.frac[3 * jr + 2], t0, t1, t2);
+                    key = XKey{(unsigned long long)__double_as_longlong(d), jt};
+                }
+                const bool ins = band && kless(key, ethr);
+                if (a.collect_stats) nre += __popc(__ballot_sync(FULL, band));
+                if (__any_sync(FULL, ins)) {
+                    ek.insert(ins ? key : kinf(XKey{}));
+                    ethr = ek.kth(k);
+                }
+            }
+        });
+        if (__any_sync(FULL, range_bad)) {
+            if (lane == 0) set_error(g.status, MG_ERR_OFFSET_RANGE, s);
+            continue;
+        }
+        if (m >= k) {  // cannot happen: at most k-1 FP32 distances lie below tau
+            if (lane == 0) set_error(g.status, MG_ERR_INTERNAL, s);
+            continue;
+        }
+        const int need = k - m;
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+            const int p = q * 32 + lane;
+            if (p < need) sel[m + p] = ek.a[q].jt;
+        }
+        __syncwarp();
+        // canonical (j, t) order of the k winners
+        if (k <= 32) {
+            unsigned long long v = lane < k ? sel[lane] : ~0ull;
+            // 64-bit bitonic sort across lanes
+#pragma unroll
+            for (int size = 2; size <= 32; size <<= 1) {
+                const bool desc = (lane & size) != 0;
+#pragma unroll
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    const unsigned long long y = __shfl_xor_sync(FULL, v, stride);
+                    const bool lower = (lane & stride) == 0;
+                    v = (lower != desc) ? (v < y ? v : y) : (v < y ? y : v);
+                }
+            }
+            if (lane < k) sel[lane] = v;
+            __syncwarp();
+        } else {
+            int P = 64;
+            while (P < k) P <<= 1;
+            warp_smem_sort_u64(sel, k, P);
+        }
+        // write k edges at rows i*k .. i*k + k - 1
+        for (int q = lane; q < k; q += 32) {
+            const unsigned long long jt = sel[q];
+            const int jl = (int)(jt >> 32);
+            int t0, t1, t2;
+            unpack_t((uint32_t)(jt & 0xffffffffull), t0, t1, t2);
+            const int64_t jr = (int64_t)Src.begin + jl;
+            const int64_t e = (int64_t)i * k + q;
+            g.src[e] = i;
+            g.dst[e] = (int32_t)jr;
+            g.offset[3 * e + 0] = t0;
+            g.offset[3 * e + 1] = t1;
+            g.offset[3 * e + 2] = t2;
+            if (g.vec || g.len) {
+                const float3 v = edge_vec_ff(Src.L, Src.xi0, Src.xi1, Src.xi2, a.frac[3 * jr], a.frac[3 * jr + 1],
+                                             a.frac[3 * jr + 2], t0, t1, t2);
+                if (g.vec) {
+                    g.vec[3 * e + 0] = v.x;
+                    g.vec[3 * e + 1] = v.y;
+                    g.vec[3 * e + 2] = v.z;
+                }
+                if (g.len) g.len[e] = vec_len(v);
+            }
+        }
+        __syncwarp();
+    }
+    if (a.collect_stats && lane == 0 && (ncand || nre)) {
+        Status *st = reinterpret_cast<Status *>(g.status);
+        atomicAdd(&st->rechecked, nre);
+        atomicAdd(&st->candidates, ncand);
+    }
+}
+
+template <int S>
+static cudaError_t launch_knn_s(const BuildArgs &a, const Work &w, cudaStream_t s) {
+    const int atoms = a.atom_hi - a.atom_lo;
+    const int threads = KNN_WARPS * 32;
+    const int flat_blocks = (atoms + KNN_WARPS - 1) / KNN_WARPS;
+    if (a.schedule == 2) {
+        cudaError_t e = launch_reset_queue(w, s);
+        if (e) return e;
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, knn_kernel<S, 2>, threads, 0);
+        int blocks = max(1, per_sm) * num_sms();
+        blocks = min(blocks, flat_blocks);
+        knn_kernel<S, 2><<<blocks, threads, 0, s>>>(a, w);
+    } else {
+        knn_kernel<S, 1><<<flat_blocks, threads, 0, s>>>(a, w);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_knn(const BuildArgs &a, const Work &w, cudaStream_t s) {
+    if (a.atom_hi <= a.atom_lo) return cudaSuccess;
+    if (a.knn_k <= 32) return launch_knn_s<1>(a, w, s);
+    if (a.knn_k <= 64) return launch_knn_s<2>(a, w, s);
+    return launch_knn_s<4>(a, w, s);
+}
+
+// src_ptr[i] = k i, edge_ptr[s] = k atom_ptr[s], status counts.
+__global__ void knn_pointers_kernel(int B, int N, int k, const int32_t *__restrict__ atom_ptr,
+                                    int64_t *__restrict__ src_ptr, int64_t *__restrict__ edge_ptr,
+                                    mg_device_status_t *status, int atom_lo, int atom_hi, int s_lo, int s_hi) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (src_ptr)
+        for (int64_t q = atom_lo + tid; q <= atom_hi; q += stride) src_ptr[q] = q * k;
+    for (int64_t q = s_lo + tid; q <= s_hi; q += stride) edge_ptr[q] = (int64_t)(q == B ? N : atom_ptr[q]) * k;
+    if (tid == 0 && s_hi == B) {
+        Status *st = reinterpret_cast<Status *>(status);
+        st->num_edges = (unsigned long long)N * k;
+        st->required_capacity = (unsigned long long)N * k;
+    }
+}
+
+cudaError_t launch_knn_pointers(const BuildArgs &a, const Work &, cudaStream_t s) {
+    // structures [0, B] and atoms [atom_lo, atom_hi] of this call
+    const int n = max(a.atom_hi - a.atom_lo + 1, a.B + 1);
+    const int threads = 256;
+    const int blocks = min(1024, (n + threads - 1) / threads);
+    knn_pointers_kernel<<<blocks, threads, 0, s>>>(a.B, a.N, a.knn_k, a.atom_ptr, a.src_ptr, a.g.edge_ptr,
+                                                    a.g.status, a.atom_lo, a.atom_hi, 0, a.B);
+    return cudaGetLastError();
+}
+
+}  // namespace mg

@@ -1,0 +1,90 @@
+// Internal launch interface between the C-ABI host layer (api.cu) and the kernel
+// translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "matgraph.h"
+
+namespace mg {
+
+struct StructRec;
+
+// Device scratch carved from the caller's workspace.
+struct Work {
+    StructRec *recs;          // [B]
+    float4 *pos;              // [N] Cartesian positions (FP32)
+    int32_t *atom_struct;     // [N] structure of each atom row
+    int32_t *cnt;             // [N] per-atom counts (edges out / edges in)
+    int32_t *cursor;          // [N] scatter cursors
+    long long *tile_sum;      // [n_tiles + 1] scan partials
+    int64_t *src_ptr;         // [N+1] used when the graph has none
+    double *gpart;            // [N][3] source-side gradient partials
+    double *lpart;            // [N][9] per-atom lattice-gradient partials
+    int32_t *sort_tmp;        // [max_edges] scratch for long destination segments
+    unsigned int *queue;      // [4] work-queue counters
+    int64_t max_edges;
+};
+
+constexpr int SCAN_TILE = 4096;
+
+struct PrepArgs {
+    int B, N;
+    const float *lattice, *frac;
+    const int32_t *atom_ptr;
+    float cutoff;              // cutoff graphs: constant radius (if cutoff_ps NULL)
+    const float *cutoff_ps;    // per-structure radii or NULL
+    int knn_k;                 // > 0: KNN graph (starting radius from density)
+    float band_rel;
+    mg_device_status_t *status;
+};
+
+cudaError_t launch_prep(const PrepArgs &a, const Work &w, cudaStream_t s);
+
+struct ScanArgs {
+    int n;                     // counts
+    const int32_t *cnt;
+    int64_t *out_ptr;          // [n+1] exclusive prefix, out_ptr[n] = total
+};
+cudaError_t launch_scan(const ScanArgs &a, const Work &w, cudaStream_t s);
+
+struct BuildArgs {
+    int B, N;
+    const float *frac;
+    const int32_t *atom_ptr;
+    int schedule;              // 1 flat, 2 persistent queue
+    int collect_stats;
+    mg_graph_t g;
+    int64_t *src_ptr;          // graph's or workspace's
+    int knn_k;
+    float band_rel;
+    int atom_lo, atom_hi;      // atom row range to process (per-structure builds)
+};
+
+cudaError_t launch_cutoff_count(const BuildArgs &a, const Work &w, cudaStream_t s);
+// Edge pointers, status and capacity check after the scan of counts.
+cudaError_t launch_cutoff_finalize(const BuildArgs &a, const Work &w, cudaStream_t s);
+cudaError_t launch_cutoff_write(const BuildArgs &a, const Work &w, cudaStream_t s);
+cudaError_t launch_knn(const BuildArgs &a, const Work &w, cudaStream_t s);
+cudaError_t launch_knn_pointers(const BuildArgs &a, const Work &w, cudaStream_t s);
+cudaError_t launch_dst_sort(const BuildArgs &a, const Work &w, cudaStream_t s, int *launches);
+cudaError_t launch_reset_queue(const Work &w, cudaStream_t s);
+
+struct EdgeVecArgs {
+    int B, N;
+    const float *lattice, *frac;
+    const int32_t *atom_ptr;
+    mg_graph_t g;
+    const float *grad_vec, *grad_len, *vec, *len;
+    float *out_vec, *out_len;
+    float *grad_frac, *grad_lattice;
+};
+cudaError_t launch_edgevec_fwd(const EdgeVecArgs &a, cudaStream_t s);
+cudaError_t launch_bwd_src(const EdgeVecArgs &a, const Work &w, cudaStream_t s);
+cudaError_t launch_bwd_dst(const EdgeVecArgs &a, const Work &w, cudaStream_t s);
+cudaError_t launch_bwd_lat(const EdgeVecArgs &a, const Work &w, cudaStream_t s);
+
+int num_sms();
+
+}  // namespace mg

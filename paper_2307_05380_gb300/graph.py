@@ -1,0 +1,359 @@
+"""PyTorch-facing binding of the matgraph C-ABI.
+
+Torch supplies device memory and the current CUDA stream; every step of the graph
+build, the edge vectors and their backward pass runs in the library's CUDA kernels.
+Functions here only marshal arguments, allocate caller-owned buffers, read the device
+status word and resize on MG_ERR_CAPACITY.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+from typing import Optional
+
+import torch
+
+from . import _capi
+from ._capi import MgBatch, MgGraph, MgOpts
+
+_CTX: dict = {}
+
+
+def _dev_index(device: torch.device) -> int:
+    return device.index if device.index is not None else torch.cuda.current_device()
+
+
+def context(device=None) -> ctypes.c_void_p:
+    """The library context of a CUDA device (created on first use)."""
+    device = torch.device("cuda") if device is None else torch.device(device)
+    idx = _dev_index(device)
+    if idx not in _CTX:
+        lib = _capi.load()
+        h = ctypes.c_void_p()
+        _capi.check(lib.mg_create(ctypes.byref(h), idx), "mg_create")
+        _CTX[idx] = h
+    return _CTX[idx]
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def make_opts(band_rel: float = 1e-5, schedule: int = 0, collect_stats: bool = False) -> MgOpts:
+    return MgOpts(float(band_rel), 0, int(schedule), int(bool(collect_stats)))
+
+
+class Batch:
+    """A batch of crystal structures on one CUDA device.
+
+    frac [N, 3] float32 fractional coordinates, lattice [B, 3, 3] float32 (row r is
+    lattice vector r, Angstrom), atom_ptr [B+1] int32 atom row ranges."""
+
+    def __init__(self, frac: torch.Tensor, lattice: torch.Tensor, atom_ptr: torch.Tensor,
+                 max_atoms: Optional[int] = None):
+        if not (frac.is_cuda and lattice.is_cuda and atom_ptr.is_cuda):
+            raise ValueError("frac, lattice and atom_ptr must be CUDA tensors")
+        if frac.dtype != torch.float32 or lattice.dtype != torch.float32 or atom_ptr.dtype != torch.int32:
+            raise TypeError("frac/lattice must be float32 and atom_ptr int32")
+        if frac.dim() != 2 or frac.shape[1] != 3 or lattice.shape[-2:] != (3, 3):
+            raise ValueError("frac must be [N, 3] and lattice [B, 3, 3]")
+        if atom_ptr.numel() != lattice.reshape(-1, 9).shape[0] + 1:
+            raise ValueError("atom_ptr must have B + 1 entries")
+        self.frac = frac.contiguous()
+        self.lattice = lattice.reshape(-1, 3, 3).contiguous()
+        self.atom_ptr = atom_ptr.contiguous()
+        self.device = frac.device
+        if max_atoms is None:
+            max_atoms = int((self.atom_ptr[1:] - self.atom_ptr[:-1]).max().item()) if self.B else 0
+        self.max_atoms = int(max_atoms)
+        self._c = MgBatch(self.B, self.N, self.max_atoms, self.lattice.data_ptr(),
+                          self.frac.data_ptr() if self.N else None, self.atom_ptr.data_ptr())
+
+    @property
+    def B(self) -> int:
+        return int(self.lattice.shape[0])
+
+    @property
+    def N(self) -> int:
+        return int(self.frac.shape[0])
+
+    def with_geometry(self, frac: torch.Tensor, lattice: torch.Tensor) -> "Batch":
+        return Batch(frac, lattice, self.atom_ptr, self.max_atoms)
+
+    @property
+    def c(self) -> MgBatch:
+        return self._c
+
+
+@dataclass
+class Graph:
+    """Graph buffers (caller-owned device memory) and the result of the last build.
+
+    The first ``num_edges`` rows of src/dst/offset/vec/len are valid, in canonical
+    order (src, dst, tx, ty, tz).  edge_ptr [B+1] splits them by structure and
+    src_ptr [N+1] by source atom; perm_dst/dst_ptr list edge ids by (dst, src, t)."""
+    kind: int
+    batch: Batch
+    cutoff: float
+    k: int
+    capacity: int
+    src: torch.Tensor
+    dst: torch.Tensor
+    offset: torch.Tensor
+    vec: Optional[torch.Tensor]
+    len: Optional[torch.Tensor]
+    edge_ptr: torch.Tensor
+    src_ptr: torch.Tensor
+    perm_dst: Optional[torch.Tensor]
+    dst_ptr: Optional[torch.Tensor]
+    status: torch.Tensor
+    ws: torch.Tensor
+    opts: MgOpts
+    num_edges: int = -1
+    last_status: dict = field(default_factory=dict)
+    _c: Optional[MgGraph] = None
+
+    @property
+    def c(self) -> MgGraph:
+        if self._c is None:
+            self._c = MgGraph(self.capacity, self.src.data_ptr(), self.dst.data_ptr(), self.offset.data_ptr(),
+                              _ptr(self.vec), _ptr(self.len), self.edge_ptr.data_ptr(), self.src_ptr.data_ptr(),
+                              _ptr(self.perm_dst), _ptr(self.dst_ptr), self.status.data_ptr())
+        return self._c
+
+    def edges(self):
+        """(src, dst, offset) views of the valid edges (after a synchronised build)."""
+        E = self.num_edges
+        return self.src[:E], self.dst[:E], self.offset[:E]
+
+    def read_status(self) -> dict:
+        """Synchronise the stream and decode the device status word."""
+        raw = self.status.cpu()
+        code = int(raw[0].item() & 0xFFFFFFFF)
+        first_bad = int((raw[0].item() >> 32) & 0xFFFFFFFF)
+        if first_bad >= 2 ** 31:
+            first_bad -= 2 ** 32
+        st = dict(code=code, first_bad_structure=None if first_bad == 2 ** 31 - 1 else first_bad,
+                  num_edges=int(raw[1]), required_capacity=int(raw[2]), rechecked=int(raw[3]),
+                  candidates=int(raw[4]))
+        self.last_status = st
+        if code == 0:
+            self.num_edges = st["num_edges"]
+        return st
+
+
+def _alloc_graph(kind, batch: Batch, cutoff, k, capacity, with_vectors, with_perm, opts, ws_edges=None) -> Graph:
+    dev = batch.device
+    capacity = int(max(capacity, 1))
+    lib = _capi.load()
+    ctx = context(dev)
+    nbytes = ctypes.c_size_t(0)
+    _capi.check(lib.mg_workspace_size(ctx, ctypes.byref(batch.c), int(ws_edges or capacity), ctypes.byref(nbytes)),
+                "mg_workspace_size")
+    i32 = dict(dtype=torch.int32, device=dev)
+    f32 = dict(dtype=torch.float32, device=dev)
+    i64 = dict(dtype=torch.int64, device=dev)
+    return Graph(kind=kind, batch=batch, cutoff=float(cutoff), k=int(k), capacity=capacity,
+                 src=torch.empty(capacity, **i32), dst=torch.empty(capacity, **i32),
+                 offset=torch.empty(capacity, 3, **i32),
+                 vec=torch.empty(capacity, 3, **f32) if with_vectors else None,
+                 len=torch.empty(capacity, **f32) if with_vectors else None,
+                 edge_ptr=torch.empty(batch.B + 1, **i64), src_ptr=torch.empty(batch.N + 1, **i64),
+                 perm_dst=torch.empty(capacity, **i32) if with_perm else None,
+                 dst_ptr=torch.empty(batch.N + 1, **i64) if with_perm else None,
+                 status=torch.zeros(5, **i64), ws=torch.empty(int(nbytes.value), dtype=torch.uint8, device=dev),
+                 opts=opts)
+
+
+def _launch_build(g: Graph, per_structure: bool = False, atom_ptr_host=None):
+    lib = _capi.load()
+    ctx = context(g.batch.device)
+    st = _stream(g.batch.device)
+    if per_structure:
+        ap = (ctypes.c_int32 * len(atom_ptr_host))(*atom_ptr_host)
+        g._ap_keepalive = ap
+        rc = lib.mg_build_per_structure(ctx, ctypes.byref(g.batch.c), g.kind, float(g.cutoff), int(g.k), ap,
+                                        ctypes.byref(g.opts), ctypes.byref(g.c), _ptr(g.ws), g.ws.numel(), st)
+        _capi.check(rc, "mg_build_per_structure")
+    elif g.kind == _capi.MG_KIND_CUTOFF:
+        rc = lib.mg_cutoff_graph(ctx, ctypes.byref(g.batch.c), float(g.cutoff), None, ctypes.byref(g.opts),
+                                 ctypes.byref(g.c), _ptr(g.ws), g.ws.numel(), st)
+        _capi.check(rc, "mg_cutoff_graph")
+    else:
+        rc = lib.mg_knn_graph(ctx, ctypes.byref(g.batch.c), int(g.k), ctypes.byref(g.opts), ctypes.byref(g.c),
+                              _ptr(g.ws), g.ws.numel(), st)
+        _capi.check(rc, "mg_knn_graph")
+
+
+def _finish(g: Graph, sync: bool) -> Graph:
+    if not sync:
+        return g
+    st = g.read_status()
+    if st["code"] != 0:
+        raise RuntimeError(f"matgraph build failed: {_capi.status_name(st['code'])} "
+                           f"(structure {st['first_bad_structure']})")
+    return g
+
+
+def _build(kind, batch: Batch, cutoff, k, capacity, with_vectors, with_perm, opts, sync, per_structure=False):
+    if opts is None:
+        opts = make_opts()
+    atom_ptr_host = batch.atom_ptr.cpu().tolist() if per_structure else None
+    if kind == _capi.MG_KIND_KNN:
+        capacity = int(k) * batch.N
+    elif capacity is None:
+        capacity = 64 * batch.N + 1024
+    g = _alloc_graph(kind, batch, cutoff, k, capacity, with_vectors, with_perm, opts)
+    _launch_build(g, per_structure, atom_ptr_host)
+    if not sync:
+        return g
+    st = g.read_status()
+    if st["code"] == 4 and kind == _capi.MG_KIND_CUTOFF:  # MG_ERR_CAPACITY: exact size known now
+        g = _alloc_graph(kind, batch, cutoff, k, st["required_capacity"], with_vectors, with_perm, opts)
+        _launch_build(g, per_structure, atom_ptr_host)
+    return _finish(g, True)
+
+
+def cutoff_graph(batch: Batch, cutoff: float, *, capacity: Optional[int] = None, with_vectors: bool = True,
+                 with_perm: bool = True, opts: Optional[MgOpts] = None, sync: bool = True) -> Graph:
+    """Cutoff multigraph (Def. 3 with a constant cutoff): every (i, j, t) with
+    |(x_j - x_i + t) L| < cutoff, (i, i, 0) excluded."""
+    return _build(_capi.MG_KIND_CUTOFF, batch, cutoff, 0, capacity, with_vectors, with_perm, opts, sync)
+
+
+def knn_graph(batch: Batch, k: int, *, with_vectors: bool = True, with_perm: bool = True,
+              opts: Optional[MgOpts] = None, sync: bool = True) -> Graph:
+    """KNN multigraph: exactly k edges per atom, ties by (distance, j, t)."""
+    return _build(_capi.MG_KIND_KNN, batch, 0.0, k, None, with_vectors, with_perm, opts, sync)
+
+
+def build_per_structure(batch: Batch, kind: str, cutoff: float = 0.0, k: int = 0, *, capacity=None,
+                        with_vectors=True, with_perm=True, opts=None, sync=True) -> Graph:
+    """The plain comparison build: the same kernels, one launch sequence per structure."""
+    kd = _capi.MG_KIND_CUTOFF if kind == "cutoff" else _capi.MG_KIND_KNN
+    return _build(kd, batch, cutoff, k, capacity, with_vectors, with_perm, opts, sync, per_structure=True)
+
+
+def rebuild(g: Graph, sync: bool = True) -> Graph:
+    """Run the build again into the same buffers (same parameters)."""
+    _launch_build(g)
+    return _finish(g, sync)
+
+
+def update_graph(g: Graph, frac: Optional[torch.Tensor] = None, lattice: Optional[torch.Tensor] = None,
+                 sync: bool = True) -> Graph:
+    """Rebuild ``g`` for new geometry (Sec. 1: the graph follows the geometry inside a
+    generative model).  New coordinates/lattices are copied into the graph's batch
+    buffers; the recorded build is replayed as a CUDA graph.  If the edge count
+    outgrows the capacity, the graph is rebuilt into larger buffers."""
+    if frac is not None:
+        g.batch.frac.copy_(frac)
+    if lattice is not None:
+        g.batch.lattice.copy_(lattice.reshape(g.batch.lattice.shape))
+    lib = _capi.load()
+    rc = lib.mg_update_graph(context(g.batch.device), ctypes.byref(g.batch.c), ctypes.byref(g.c), _ptr(g.ws),
+                             g.ws.numel(), _stream(g.batch.device))
+    _capi.check(rc, "mg_update_graph")
+    if not sync:
+        return g
+    st = g.read_status()
+    if st["code"] == 4:
+        return _build(g.kind, g.batch, g.cutoff, g.k, st["required_capacity"], g.vec is not None,
+                      g.perm_dst is not None, g.opts, True)
+    return _finish(g, True)
+
+
+def profile_enable(on: bool = True, device=None) -> None:
+    """Record CUDA events between kernel stages of later builds and edge-vector calls."""
+    _capi.check(_capi.load().mg_profile_enable(context(device), int(bool(on))), "mg_profile_enable")
+
+
+def stage_times(which: str, device=None) -> dict:
+    """{stage: milliseconds} of the last profiled call of kind 'cutoff', 'knn', 'fwd'
+    or 'bwd' (waits for its events)."""
+    code = {"cutoff": 0, "knn": 1, "fwd": 2, "bwd": 3}[which]
+    names = (ctypes.c_char_p * 16)()
+    ms = (ctypes.c_float * 16)()
+    n = _capi.load().mg_stage_times(context(device), code, 16, names, ms)
+    return {} if n < 0 else {names[q].decode(): float(ms[q]) for q in range(n)}
+
+
+def last_launch_count(device=None) -> int:
+    return int(_capi.load().mg_last_launch_count(context(device)))
+
+
+def autotune(batch: Batch, kind: str, cutoff: float = 0.0, k: int = 0, capacity=None) -> None:
+    """Time the schedules on this batch and keep the fastest for its size class."""
+    kd = _capi.MG_KIND_CUTOFF if kind == "cutoff" else _capi.MG_KIND_KNN
+    g = _build(kd, batch, cutoff, k, capacity, True, False, None, True)
+    rc = _capi.load().mg_autotune(context(batch.device), ctypes.byref(batch.c), kd, float(cutoff), int(k),
+                                  ctypes.byref(g.c), _ptr(g.ws), g.ws.numel(), _stream(batch.device))
+    _capi.check(rc, "mg_autotune")
+
+
+# ---------------------------------------------------------------------------- edge vectors
+
+def edge_vectors_fwd(g: Graph, batch: Optional[Batch] = None, out_vec=None, out_len=None):
+    """vec = (x_j - x_i + t) L and len = |vec| for the graph's fixed edge set, from the
+    batch's current coordinates (default: the graph's own batch)."""
+    batch = g.batch if batch is None else batch
+    dev = batch.device
+    if out_vec is None:
+        out_vec = torch.empty(g.capacity, 3, dtype=torch.float32, device=dev)
+    if out_len is None:
+        out_len = torch.empty(g.capacity, dtype=torch.float32, device=dev)
+    rc = _capi.load().mg_edge_vectors_fwd(context(dev), ctypes.byref(batch.c), ctypes.byref(g.c), _ptr(out_vec),
+                                          _ptr(out_len), _stream(dev))
+    _capi.check(rc, "mg_edge_vectors_fwd")
+    return out_vec, out_len
+
+
+def edge_vectors_bwd(g: Graph, batch: Batch, grad_vec, grad_len, vec, ln, grad_frac=None, grad_lattice=None):
+    """Gradients of a loss through vec/len w.r.t. frac [N,3] and lattice [B,3,3]."""
+    dev = batch.device
+    if grad_frac is None:
+        grad_frac = torch.empty(batch.N, 3, dtype=torch.float32, device=dev)
+    if grad_lattice is None:
+        grad_lattice = torch.empty(batch.B, 3, 3, dtype=torch.float32, device=dev)
+    rc = _capi.load().mg_edge_vectors_bwd(context(dev), ctypes.byref(batch.c), ctypes.byref(g.c), _ptr(grad_vec),
+                                          _ptr(grad_len), _ptr(vec), _ptr(ln), _ptr(grad_frac),
+                                          _ptr(grad_lattice), _ptr(g.ws), g.ws.numel(), _stream(dev))
+    _capi.check(rc, "mg_edge_vectors_bwd")
+    return grad_frac, grad_lattice
+
+
+class EdgeVectors(torch.autograd.Function):
+    """Differentiable edge vectors and lengths for a fixed edge set.
+
+    forward(frac, lattice, graph) -> (vec [E,3], len [E]); backward gives gradients
+    w.r.t. frac and lattice through the library's deterministic segmented kernels."""
+
+    @staticmethod
+    def forward(ctx, frac, lattice, graph: Graph):
+        batch = graph.batch.with_geometry(frac.detach().contiguous(), lattice.detach().contiguous())
+        vec, ln = edge_vectors_fwd(graph, batch)
+        E = graph.num_edges
+        ctx.graph = graph
+        ctx.batch = batch
+        ctx.save_for_backward(vec, ln)
+        return vec[:E], ln[:E]
+
+    @staticmethod
+    def backward(ctx, gvec, glen):
+        vec, ln = ctx.saved_tensors
+        g = ctx.graph
+        gv = None if gvec is None else gvec.contiguous()
+        gl = None if glen is None else glen.contiguous()
+        if g.perm_dst is None:
+            raise RuntimeError("edge-vector backward needs a graph built with with_perm=True")
+        gf, gL = edge_vectors_bwd(g, ctx.batch, gv, gl, vec, ln)
+        return gf, gL, None
+
+
+def edge_vectors(frac: torch.Tensor, lattice: torch.Tensor, graph: Graph):
+    """Differentiable (vec, len) of the graph's edges for coordinates frac and lattice."""
+    return EdgeVectors.apply(frac, lattice, graph)

@@ -1,0 +1,59 @@
+"""Shared test helpers: moving synthetic batches to the GPU and comparing graphs."""
+import numpy as np
+
+import oracle
+
+
+def to_device(b, dev="cuda:0"):
+    import torch
+
+    import paper_2307_05380_gb300 as mg
+    return mg.Batch(torch.from_numpy(b.frac).to(dev), torch.from_numpy(b.lattice).to(dev),
+                    torch.from_numpy(b.atom_ptr).to(dev), max_atoms=b.max_atoms)
+
+
+def graph_arrays(g):
+    E = g.num_edges
+    out = dict(src=g.src[:E].cpu().numpy(), dst=g.dst[:E].cpu().numpy(), offset=g.offset[:E].cpu().numpy(),
+               edge_ptr=g.edge_ptr.cpu().numpy(), src_ptr=g.src_ptr.cpu().numpy())
+    if g.vec is not None:
+        out["vec"] = g.vec[:E].cpu().numpy()
+        out["len"] = g.len[:E].cpu().numpy()
+    if g.perm_dst is not None:
+        out["perm_dst"] = g.perm_dst[:E].cpu().numpy()
+        out["dst_ptr"] = g.dst_ptr.cpu().numpy()
+    return out
+
+
+def assert_same_edges(got, want, what=""):
+    """Bit-exact comparison of canonical edge lists."""
+    assert got["src"].shape == want["src"].shape, f"{what}: {got['src'].shape[0]} vs {want['src'].shape[0]} edges"
+    np.testing.assert_array_equal(got["src"], want["src"], err_msg=what)
+    np.testing.assert_array_equal(got["dst"], want["dst"], err_msg=what)
+    np.testing.assert_array_equal(got["offset"], want["offset"], err_msg=what)
+
+
+def assert_vectors(b, got, rtol=1e-6):
+    """vec/len within rtol of the FP64 oracle (vec error relative to the length)."""
+    vec, ln = oracle.edge_vectors(b.lattice, b.frac, b.atom_ptr, got["src"], got["dst"], got["offset"])
+    lerr = np.abs(got["len"].astype(np.float64) - ln) / ln
+    verr = np.linalg.norm(got["vec"].astype(np.float64) - vec, axis=1) / ln
+    assert lerr.max(initial=0) <= rtol, f"len rel err {lerr.max()}"
+    assert verr.max(initial=0) <= rtol, f"vec rel err {verr.max()}"
+    return lerr.max(initial=0), verr.max(initial=0)
+
+
+def assert_perm_dst(got, N):
+    """perm_dst lists edge ids by (dst, src, t); dst_ptr is its CSR."""
+    E = got["src"].shape[0]
+    order = np.lexsort((got["offset"][:, 2], got["offset"][:, 1], got["offset"][:, 0], got["src"], got["dst"]))
+    np.testing.assert_array_equal(got["perm_dst"], order)
+    counts = np.bincount(got["dst"], minlength=N)
+    np.testing.assert_array_equal(got["dst_ptr"], np.concatenate([[0], np.cumsum(counts)]))
+    assert got["dst_ptr"][-1] == E
+
+
+def pointers_ok(got, b):
+    edge_ptr, src_ptr = oracle.pointers(got["src"], b.atom_ptr)
+    np.testing.assert_array_equal(got["edge_ptr"], edge_ptr)
+    np.testing.assert_array_equal(got["src_ptr"], src_ptr)

@@ -1,0 +1,324 @@
+"""GPU parity: the CUDA path against the FP64 oracle, element by element.
+
+Edge sets bit-exact after canonical order; vec/len within 1e-6 relative; gradients
+within a condition-aware bound.  Every call goes through the C-ABI library.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import (assert_perm_dst, assert_same_edges, assert_vectors, graph_arrays, pointers_ok,
+                     to_device)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2307_05380_gb300 as mg  # noqa: E402
+
+
+def cutoff_parity(b, r, **kw):
+    g = mg.cutoff_graph(to_device(b), r, **kw)
+    got = graph_arrays(g)
+    want = oracle.cutoff(b.lattice, b.frac, b.atom_ptr, r)
+    assert_same_edges(got, want, f"cutoff r={r}")
+    pointers_ok(got, b)
+    if g.vec is not None:
+        assert_vectors(b, got)
+    if g.perm_dst is not None:
+        assert_perm_dst(got, b.total_atoms)
+    return got
+
+
+def knn_parity(b, k, **kw):
+    g = mg.knn_graph(to_device(b), k, **kw)
+    got = graph_arrays(g)
+    want = oracle.knn(b.lattice, b.frac, b.atom_ptr, k)
+    assert_same_edges(got, want, f"knn k={k}")
+    pointers_ok(got, b)
+    if g.vec is not None:
+        assert_vectors(b, got)
+    if g.perm_dst is not None:
+        assert_perm_dst(got, b.total_atoms)
+    return got
+
+
+# ------------------------------------------------------------------ workloads
+
+def test_config1_cutoff_and_knn():
+    b = synth.make_batch(1)
+    cutoff_parity(b, 5.0)
+    knn_parity(b, 12)
+
+
+def test_config2_full_batch_cutoff_and_knn():
+    b = synth.make_batch(2)
+    cutoff_parity(b, 6.0)
+    knn_parity(b, 16)
+
+
+@pytest.mark.parametrize("r", [4.0, 6.0, 8.0])
+def test_config3_sampled_structures_cutoff(r):
+    """Full 8192-structure batch on the GPU; every structure of a seeded sample (skewed
+    cells included) compared with the oracle."""
+    b = synth.make_batch(3)
+    g = mg.cutoff_graph(to_device(b), r, with_perm=False)
+    got = graph_arrays(g)
+    rng = np.random.default_rng(int(r))
+    sample = sorted(set(rng.choice(b.num_structures, 48, replace=False).tolist()) |
+                    {int(np.argmax(np.diff(b.atom_ptr)))})
+    for s in sample:
+        lo, hi = got["edge_ptr"][s], got["edge_ptr"][s + 1]
+        sub = b.subset([s])
+        want = oracle.cutoff(sub.lattice, sub.frac, sub.atom_ptr, r)
+        part = {key: got[key][lo:hi] for key in ("src", "dst", "offset", "vec", "len")}
+        part["src"] = part["src"] - b.atom_ptr[s]
+        part["dst"] = part["dst"] - b.atom_ptr[s]
+        assert_same_edges(part, want, f"structure {s}")
+        assert_vectors(sub, part)
+
+
+@pytest.mark.parametrize("k", [8, 16, 32])
+def test_config3_sampled_structures_knn(k):
+    b = synth.make_batch(3)
+    g = mg.knn_graph(to_device(b), k, with_perm=False)
+    got = graph_arrays(g)
+    rng = np.random.default_rng(k)
+    sample = sorted(rng.choice(b.num_structures, 64, replace=False).tolist())
+    for s in sample:
+        lo, hi = got["edge_ptr"][s], got["edge_ptr"][s + 1]
+        sub = b.subset([s])
+        want = oracle.knn(sub.lattice, sub.frac, sub.atom_ptr, k)
+        part = {key: got[key][lo:hi] for key in ("src", "dst", "offset", "vec", "len")}
+        part["src"] = part["src"] - b.atom_ptr[s]
+        part["dst"] = part["dst"] - b.atom_ptr[s]
+        assert_same_edges(part, want, f"structure {s}")
+        assert_vectors(sub, part)
+
+
+def test_config5_supercells_sampled_sources():
+    """Supercells up to 21,952 atoms: sampled source atoms against the oracle, plus the
+    symmetry property on whole structures."""
+    b = synth.make_batch(5)
+    g = mg.cutoff_graph(to_device(b), 8.0, with_perm=False)
+    src_ptr = g.src_ptr.cpu().numpy()
+    rng = np.random.default_rng(5)
+    for s in range(0, b.num_structures, 4):
+        lo, hi = b.atom_ptr[s], b.atom_ptr[s + 1]
+        srcs = np.sort(rng.choice(np.arange(lo, hi), 3, replace=False)).astype(np.int32)
+        want = oracle.cutoff(b.lattice, b.frac, b.atom_ptr, 8.0, sources=srcs)
+        parts = []
+        for a in srcs:
+            e0, e1 = src_ptr[a], src_ptr[a + 1]
+            parts.append((g.src[e0:e1].cpu().numpy(), g.dst[e0:e1].cpu().numpy(), g.offset[e0:e1].cpu().numpy()))
+        got = dict(src=np.concatenate([p[0] for p in parts]), dst=np.concatenate([p[1] for p in parts]),
+                   offset=np.concatenate([p[2] for p in parts]))
+        assert_same_edges(got, want, f"supercell {s}")
+    # degree symmetry: in-degree equals out-degree for a constant cutoff
+    E = g.num_edges
+    deg_out = np.diff(src_ptr)
+    deg_in = np.bincount(g.dst[:E].cpu().numpy(), minlength=b.total_atoms)
+    np.testing.assert_array_equal(deg_out, deg_in)
+
+
+def test_config5_knn_sampled_sources():
+    b = synth.make_batch(5)
+    k = 32
+    g = mg.knn_graph(to_device(b), k, with_perm=False)
+    rng = np.random.default_rng(55)
+    for s in range(0, b.num_structures, 8):
+        lo, hi = b.atom_ptr[s], b.atom_ptr[s + 1]
+        srcs = np.sort(rng.choice(np.arange(lo, hi), 2, replace=False)).astype(np.int32)
+        want = oracle.knn(b.lattice, b.frac, b.atom_ptr, k, sources=srcs)
+        rows = np.concatenate([np.arange(a * k, a * k + k) for a in srcs])
+        idx = torch.from_numpy(rows).to(g.src.device)
+        got = dict(src=g.src[idx].cpu().numpy(), dst=g.dst[idx].cpu().numpy(), offset=g.offset[idx].cpu().numpy())
+        assert_same_edges(got, want, f"supercell {s}")
+
+
+# ------------------------------------------------------------------ closed forms and edge cases
+
+def test_closed_forms_on_gpu():
+    sc = synth.crystal(np.eye(3), [[0, 0, 0]])
+    for r, deg in [(1.0, 0), (1.01, 6), (1.42, 18), (1.74, 26)]:
+        g = mg.cutoff_graph(to_device(sc), r)
+        assert g.num_edges == deg
+    a = 3.6
+    fcc = synth.crystal(np.array([[0, .5, .5], [.5, 0, .5], [.5, .5, 0]]) * a, [[0, 0, 0]])
+    g = mg.knn_graph(to_device(fcc), 12)
+    np.testing.assert_allclose(g.len[:12].cpu().numpy(), a / np.sqrt(2), rtol=1e-6)
+    tie = synth.crystal(np.eye(3), [[0.25, 0.5, 0.75]])
+    g = mg.knn_graph(to_device(tie), 8)
+    assert g.offset[:8].cpu().numpy().tolist() == [[-1, -1, 0], [-1, 0, -1], [-1, 0, 0], [0, -1, 0],
+                                                    [0, 0, -1], [0, 0, 1], [0, 1, 0], [1, 0, 0]]
+
+
+def edge_case_batch():
+    parts = [
+        synth.crystal(np.eye(3) * 2.0, [[0.1, 0.2, 0.3]]),                      # one atom
+        synth.crystal([[4, 0, 0], [3.6, 1.7, 0], [0.2, 0.3, 5]], [[0, 0, 0], [0.3, 0.6, 0.2]]),  # ~25 deg skew
+        synth.crystal(np.eye(3) * 3.0, [[1.3, -2.2, 0.7], [-0.4, 0.5, 3.9]]),    # unwrapped coordinates
+        synth.crystal([[2.5, 0, 0], [0, 14, 0], [0, 0, 30]], [[0.5, 0.5, 0.5], [0.9, 0.1, 0.2]]),  # long cell
+        synth.make_batch(2, B=8),
+    ]
+    b = synth.concat(parts)
+    # insert an empty structure in the middle
+    counts = np.diff(b.atom_ptr).tolist()
+    counts.insert(3, 0)
+    lat = np.concatenate([b.lattice[:3], np.eye(3, dtype=np.float32)[None] * 5, b.lattice[3:]])
+    ptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    return synth.Batch(lat, b.frac, ptr)
+
+
+def test_edge_cases_cutoff():
+    b = edge_case_batch()
+    for r in (3.0, 5.5):
+        cutoff_parity(b, r)
+
+
+def test_edge_cases_knn():
+    b = edge_case_batch()
+    for k in (1, 5, 27, 33, 64, 100, 128):
+        knn_parity(b, k)
+
+
+def test_ragged_sizes_many_tiles():
+    """Batches whose atom counts straddle warp and scan-tile boundaries."""
+    b = synth.concat([synth.make_batch(3, B=40), synth.make_batch(1, B=5)])
+    cutoff_parity(b, 5.0)
+    knn_parity(b, 9)
+
+
+def test_capacity_error_then_exact_rebuild():
+    b = synth.make_batch(1)
+    batch = to_device(b)
+    g = mg.cutoff_graph(batch, 5.0, capacity=10, sync=False)
+    st = g.read_status()
+    want = oracle.cutoff(b.lattice, b.frac, b.atom_ptr, 5.0)
+    assert st["code"] == 4 and st["required_capacity"] == len(want["src"])
+    g2 = mg.cutoff_graph(batch, 5.0, capacity=st["required_capacity"])
+    assert g2.num_edges == len(want["src"])
+
+
+def test_bad_inputs_reported_on_device():
+    b = synth.make_batch(1, B=3)
+    lat = b.lattice.copy()
+    lat[1] = 0.0  # singular
+    frac = b.frac.copy()
+    frac[b.atom_ptr[2]] = np.nan
+    g = mg.cutoff_graph(to_device(synth.Batch(lat, frac, b.atom_ptr)), 5.0, sync=False)
+    st = g.read_status()
+    assert st["code"] in (2, 3) and st["first_bad_structure"] == 1
+    # the good structure is still built
+    want = oracle.cutoff(b.lattice[:1], b.frac[:b.atom_ptr[1]], b.atom_ptr[:2], 5.0)
+    E0 = int(g.edge_ptr[1].item())
+    assert E0 == len(want["src"])
+
+
+# ------------------------------------------------------------------ schedules, per-structure, update
+
+def test_schedules_and_per_structure_identical():
+    b = synth.make_batch(2)
+    batch = to_device(b)
+    ref = graph_arrays(mg.cutoff_graph(batch, 6.0, opts=mg.make_opts(schedule=1)))
+    per = graph_arrays(mg.cutoff_graph(batch, 6.0, opts=mg.make_opts(schedule=2)))
+    ps = graph_arrays(mg.build_per_structure(batch, "cutoff", cutoff=6.0))
+    for other in (per, ps):
+        for key in ref:
+            np.testing.assert_array_equal(ref[key], other[key], err_msg=key)
+    kref = graph_arrays(mg.knn_graph(batch, 16, opts=mg.make_opts(schedule=1)))
+    kper = graph_arrays(mg.knn_graph(batch, 16, opts=mg.make_opts(schedule=2)))
+    kps = graph_arrays(mg.build_per_structure(batch, "knn", k=16))
+    for other in (kper, kps):
+        for key in kref:
+            np.testing.assert_array_equal(kref[key], other[key], err_msg=key)
+
+
+def test_update_graph_replay_tracks_geometry():
+    b = synth.make_batch(4, B=64)
+    batch = to_device(b)
+    g = mg.cutoff_graph(batch, 5.0, capacity=400000)
+    cur = b
+    for step in range(3):
+        cur = synth.perturb(cur, seed=11, step=step)
+        g = mg.update_graph(g, torch.from_numpy(cur.frac).cuda(), torch.from_numpy(cur.lattice).cuda())
+        got = graph_arrays(g)
+        want = oracle.cutoff(cur.lattice, cur.frac, cur.atom_ptr, 5.0)
+        assert_same_edges(got, want, f"step {step}")
+        assert_vectors(cur, got)
+
+
+def test_stats_counters():
+    b = synth.make_batch(2, B=32)
+    g = mg.cutoff_graph(to_device(b), 6.0, opts=mg.make_opts(collect_stats=True))
+    st = g.last_status
+    assert st["candidates"] >= g.num_edges > 0
+    assert 0 <= st["rechecked"] < st["candidates"]
+
+
+# ------------------------------------------------------------------ edge vectors and gradients
+
+def test_edge_vectors_fwd_matches_build():
+    b = synth.make_batch(2)
+    g = mg.cutoff_graph(to_device(b), 6.0)
+    vec, ln = mg.edge_vectors_fwd(g)
+    E = g.num_edges
+    assert torch.equal(vec[:E], g.vec[:E]) and torch.equal(ln[:E], g.len[:E])
+
+
+def _grad_check(b, g, w, sigma=1.5):
+    batch = g.batch
+    frac = batch.frac.clone().requires_grad_(True)
+    lat = batch.lattice.clone().requires_grad_(True)
+    vec, ln = mg.edge_vectors(frac, lat, g)
+    wt = torch.from_numpy(w).cuda()
+    loss = (wt * torch.exp(-ln ** 2 / (2 * sigma ** 2))).sum()
+    loss.backward()
+    got = graph_arrays(g)
+    ov, ol = oracle.edge_vectors(b.lattice, b.frac, b.atom_ptr, got["src"], got["dst"], got["offset"])
+    _, dlen = oracle.gaussian_loss_grads(ov, ol, w, sigma)
+    gf, gL = oracle.edge_grad(b.lattice, b.frac, b.atom_ptr, got["src"], got["dst"], got["offset"], None, dlen)
+    # condition-aware bound: 1e-5 of the summed magnitudes of the contributions
+    gabs = np.abs(dlen)[:, None] * np.ones((1, 3))
+    scale_f = np.zeros_like(gf)
+    Lt = np.abs(b.lattice.astype(np.float64))
+    atom_s = np.repeat(np.arange(b.num_structures), np.diff(b.atom_ptr))
+    # |g_e| L^T magnitudes per edge and component (|dLoss/dlen| bounds |g_e| componentwise)
+    h = np.einsum("ec,ekc->ek", gabs, Lt[atom_s[got["src"]]])
+    np.add.at(scale_f, got["src"], h)
+    np.add.at(scale_f, got["dst"], h)
+    err_f = np.abs(frac.grad.cpu().numpy() - gf)
+    assert np.all(err_f <= 1e-5 * scale_f + 1e-12), err_f.max()
+    df = (b.frac[got["dst"]].astype(np.float64) - b.frac[got["src"]] + got["offset"])
+    scale_L = np.zeros((b.num_structures, 3, 3))
+    np.add.at(scale_L, atom_s[got["src"]], np.abs(df)[:, :, None] * gabs[:, None, :])
+    err_L = np.abs(lat.grad.cpu().numpy() - gL)
+    assert np.all(err_L <= 1e-5 * scale_L + 1e-12), err_L.max()
+    return frac.grad.clone(), lat.grad.clone()
+
+
+def test_gradients_match_oracle_and_are_deterministic():
+    b = synth.make_batch(4, B=128)
+    g = mg.cutoff_graph(to_device(b), 5.0)
+    w = synth.normal(4, 0, g.num_edges)
+    g1 = _grad_check(b, g, w)
+    g2 = _grad_check(b, g, w)
+    assert torch.equal(g1[0], g2[0]) and torch.equal(g1[1], g2[1])
+
+
+def test_gradients_knn_graph_grad_vec_path():
+    b = synth.make_batch(2, B=64)
+    g = mg.knn_graph(to_device(b), 16)
+    frac = g.batch.frac.clone().requires_grad_(True)
+    lat = g.batch.lattice.clone().requires_grad_(True)
+    vec, ln = mg.edge_vectors(frac, lat, g)
+    c = torch.from_numpy(synth.normal(5, 1, 3 * g.num_edges).reshape(-1, 3)).cuda()
+    (vec * c).sum().backward()
+    got = graph_arrays(g)
+    gf, gL = oracle.edge_grad(b.lattice, b.frac, b.atom_ptr, got["src"], got["dst"], got["offset"],
+                              c.cpu().numpy().astype(np.float64), None)
+    np.testing.assert_allclose(frac.grad.cpu().numpy(), gf, rtol=1e-4, atol=1e-4 * np.abs(gf).max())
+    np.testing.assert_allclose(lat.grad.cpu().numpy(), gL, rtol=1e-4, atol=1e-4 * np.abs(gL).max())
