@@ -1,0 +1,431 @@
+#!/usr/bin/env python
+"""Benchmark of the batched periodic-graph hot path on GB300.
+
+One step = the whole path over one batch: the cutoff multigraph build (prep,
+interplanar-box FP32 scan with FP64 re-test, count / scan / write, destination sort),
+the KNN build (adaptive radius, register top-k, FP64 re-rank) and the edge-vector
+forward and backward passes on the cutoff graph.  Both builds replay their captured
+CUDA-graph plans (mg_update_graph).  Units are edges built per step (cutoff + KNN).
+
+Default workload: 256 synthetic structures with 1..64 atoms (log-uniform), lengths
+U[2.5,12] A, angles U[50,130] deg, 0.9 A separation; cutoff 6 A, k = 16.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "edges/s batched vs per-structure build (+bwd), bit-exact edges; % roofline"
+UNIT = "edges/s"
+L2_FLUSH_BYTES = 256 << 20
+FP32_LANES_PER_SM = 128
+SMS = 152
+WORKLOADS = {
+    1: dict(cutoff=5.0, k=12, name="16 structures x 4-16 atoms, lengths U[3,8] A, cutoff 5 A, k=12"),
+    2: dict(cutoff=6.0, k=16, name="256 structures x 1-64 atoms (log-uniform), lengths U[2.5,12] A, "
+                                    "angles U[50,130] deg, cutoff 6 A, k=16"),
+    3: dict(cutoff=6.0, k=16, name="8192 structures, 70/25/5% mixture up to 400 atoms, 10% skewed cells, "
+                                    "cutoff 6 A, k=16"),
+    4: dict(cutoff=5.0, k=16, name="1024 structures x 8-64 atoms, cutoff 5 A, k=16"),
+    5: dict(cutoff=8.0, k=32, name="32 supercells of 1728-21952 atoms, cutoff 8 A, k=32"),
+}
+# Algorithmic work per unit of each stage (bytes or FP32 flops per edge, per atom).
+# Edge record: src 4 + dst 4 + offset 12 + vec 12 + len 4 = 36 B.
+STAGE_MODEL = {
+    ("cutoff", "write"): ("hbm", 36.0, "cut"),
+    ("cutoff", "count"): ("alu", 21.0, "cut"),
+    ("knn", "knn"): ("hbm", 36.0, "knn"),
+    ("fwd", "fwd"): ("hbm", 36.0, "cut"),
+    ("bwd", "bwd_src"): ("hbm", 36.0, "cut"),
+    ("bwd", "bwd_dst"): ("hbm", 24.0, "cut"),
+    ("bwd", "bwd_lat"): ("hbm", 0.0, "cut"),
+}
+# Stages that are one kernel launch; the roofline reports the slowest of these (the
+# others bundle several launches: status init + prep, the three scan kernels, the
+# destination sort's histogram / scan / scatter / segment sort).
+SINGLE_KERNEL_STAGES = {("cutoff", "count"), ("cutoff", "write"), ("cutoff", "finalize"), ("knn", "knn"),
+                        ("knn", "pointers"), ("fwd", "fwd"), ("bwd", "bwd_src"), ("bwd", "bwd_dst"),
+                        ("bwd", "bwd_lat")}
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    p.add_argument("--config", type=int, default=2, choices=sorted(WORKLOADS))
+    p.add_argument("--no-baselines", action="store_true", help="skip the CPU oracle and per-structure legs")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2307_05380_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(f.encode())
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+def recorded_traffic(config, stage_key):
+    """DRAM bytes per launch from a committed ncu summary, if taken on this kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    ent = d.get(f"config{config}", {}).get(f"{stage_key[0]}.{stage_key[1]}")
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"mg_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- reference arm
+
+def run_reference(args, rank):
+    """The FP64 oracle on the host cores, same workload, metric and unit."""
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    import synth
+    wl = WORKLOADS[args.config]
+    b = synth.make_batch(args.config)
+    sample_B = b.num_structures if args.config in (1, 2, 4) else 64
+    sub = b.subset(range(sample_B))
+
+    def step():
+        g = oracle.cutoff(sub.lattice, sub.frac, sub.atom_ptr, wl["cutoff"])
+        h = oracle.knn(sub.lattice, sub.frac, sub.atom_ptr, wl["k"])
+        vec, ln = oracle.edge_vectors(sub.lattice, sub.frac, sub.atom_ptr, g["src"], g["dst"], g["offset"])
+        oracle.edge_grad(sub.lattice, sub.frac, sub.atom_ptr, g["src"], g["dst"], g["offset"], None, ln)
+        return len(g["src"]) + len(h["src"])
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    edges = sum(step() for _ in range(args.steps))
+    dt = time.perf_counter() - t0
+    v = edges / dt
+    sample = f"{sample_B} of {b.num_structures} structures per step (whole batch)" if sample_B == b.num_structures \
+        else f"first {sample_B} of {b.num_structures} structures per step"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl["name"], "impl_note": "FP64 brute-force oracle, 1 thread"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------- our arm
+
+def cpu_baseline_leg(args, b, wl, budget_s=12.0):
+    import oracle
+    sub = b if args.config in (1, 2, 4) else b.subset(range(32))
+    edges, passes = 0, 0
+    t0 = time.perf_counter()
+    while True:
+        g = oracle.cutoff(sub.lattice, sub.frac, sub.atom_ptr, wl["cutoff"])
+        h = oracle.knn(sub.lattice, sub.frac, sub.atom_ptr, wl["k"])
+        vec, ln = oracle.edge_vectors(sub.lattice, sub.frac, sub.atom_ptr, g["src"], g["dst"], g["offset"])
+        oracle.edge_grad(sub.lattice, sub.frac, sub.atom_ptr, g["src"], g["dst"], g["offset"], None, ln)
+        edges += len(g["src"]) + len(h["src"])
+        passes += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": edges / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{passes} passes of cutoff+KNN+edge vectors+gradient over {sub.num_structures} structures "
+                      f"({dt:.1f} s, single thread)"}
+
+
+def run_mine(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2307_05380_gb300 as mg
+    import synth
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = WORKLOADS[args.config]
+    # weak scaling: every rank builds its own seeded batch of the full workload size
+    b = synth.make_batch(args.config, seed=synth.BASE_SEED + args.config + 1000 * rank)
+    batch = mg.Batch(torch.from_numpy(b.frac).to(dev), torch.from_numpy(b.lattice).to(dev),
+                     torch.from_numpy(b.atom_ptr).to(dev), max_atoms=b.max_atoms)
+    g_cut = mg.cutoff_graph(batch, wl["cutoff"])
+    g_knn = mg.knn_graph(batch, wl["k"])
+    E_cut, E_knn = g_cut.num_edges, g_knn.num_edges
+    units = E_cut + E_knn
+    grad_len = torch.from_numpy(synth.normal(17, 0, g_cut.capacity)).to(dev)
+    out_vec = torch.empty(g_cut.capacity, 3, device=dev)
+    out_len = torch.empty(g_cut.capacity, device=dev)
+    grad_frac = torch.empty(batch.N, 3, device=dev)
+    grad_lat = torch.empty(batch.B, 3, 3, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    mg.profile_enable(True, dev)
+
+    launches = {"n": 0}
+
+    def step():
+        n = 0
+        mg.update_graph(g_cut, sync=False)
+        n += mg.last_launch_count(dev)
+        mg.update_graph(g_knn, sync=False)
+        n += mg.last_launch_count(dev)
+        mg.edge_vectors_fwd(g_cut, out_vec=out_vec, out_len=out_len)
+        n += mg.last_launch_count(dev)
+        mg.edge_vectors_bwd(g_cut, batch, None, grad_len, out_vec, out_len, grad_frac, grad_lat)
+        n += mg.last_launch_count(dev)
+        launches["n"] += n
+
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(dev)
+    st = g_cut.read_status()
+    sk = g_knn.read_status()
+    assert st["code"] == 0 and sk["code"] == 0 and g_cut.num_edges == E_cut, (st, sk)
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    stage_tot: dict = {}
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches["n"] = 0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        ev0[s].record(stream)
+        step()
+        ev1[s].record(stream)
+        for which in ("cutoff", "knn", "fwd", "bwd"):  # live per-stage CUDA events
+            for name, ms in mg.stage_times(which, dev).items():
+                stage_tot[(which, name)] = stage_tot.get((which, name), 0.0) + ms
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [ev0[s].elapsed_time(ev1[s]) for s in range(args.steps)]
+    total_ms = sum(step_ms)
+    gpu_launches = launches["n"]
+
+    # whole-job aggregate: all ranks' edges over the slowest rank's time
+    tot_units, max_ms = units * args.steps, total_ms
+    if world > 1:
+        t = torch.tensor([float(tot_units), total_ms], dtype=torch.float64, device=dev)
+        u = t[:1].clone()
+        torch.distributed.all_reduce(u, op=torch.distributed.ReduceOp.SUM)
+        m = t[1:].clone()
+        torch.distributed.all_reduce(m, op=torch.distributed.ReduceOp.MAX)
+        tot_units, max_ms = float(u.item()), float(m.item())
+    value = tot_units / (max_ms / 1e3)
+
+    # e2e through the public API: pinned host inputs in, results out, every step
+    frac_h = torch.from_numpy(b.frac).pin_memory()
+    lat_h = torch.from_numpy(b.lattice).pin_memory()
+    ptr_h = torch.from_numpy(b.atom_ptr).pin_memory()
+    w_dev = grad_len[:E_cut]
+    e2e_steps = max(5, min(args.steps, 50))
+    host_out = {}
+
+    def e2e_step():
+        batch.frac.copy_(frac_h, non_blocking=True)
+        batch.lattice.copy_(lat_h, non_blocking=True)
+        batch.atom_ptr.copy_(ptr_h, non_blocking=True)
+        gc = mg.update_graph(g_cut)
+        gk = mg.update_graph(g_knn)
+        fr = batch.frac.detach().requires_grad_(True)
+        la = batch.lattice.detach().requires_grad_(True)
+        vec, ln = mg.edge_vectors(fr, la, gc)
+        (ln * w_dev[:gc.num_edges]).sum().backward()
+        outs = [gc.src[:gc.num_edges], gc.dst[:gc.num_edges], gc.offset[:gc.num_edges], vec.detach(),
+                ln.detach(), gk.src[:gk.num_edges], gk.dst[:gk.num_edges], gk.offset[:gk.num_edges],
+                gk.vec[:gk.num_edges], gk.len[:gk.num_edges], fr.grad, la.grad]
+        d2h = 0
+        for q, t in enumerate(outs):
+            if q not in host_out or host_out[q].shape != t.shape:
+                host_out[q] = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+            host_out[q].copy_(t, non_blocking=True)
+            d2h += t.numel() * t.element_size()
+        torch.cuda.synchronize(dev)
+        return gc.num_edges + gk.num_edges, d2h
+
+    e2e_step()
+    e2e_t, e2e_units, d2h = 0.0, 0, 0
+    for _ in range(e2e_steps):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        u_, d2h = e2e_step()
+        e2e_t += time.perf_counter() - t0
+        e2e_units += u_
+    h2d = (frac_h.numel() * 4 + lat_h.numel() * 4 + ptr_h.numel() * 4)
+    e2e_val = e2e_units / e2e_t
+    if world > 1:
+        t = torch.tensor([e2e_val], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+        e2e_val = float(t.item())
+
+    # plain comparison: the same kernels, one launch sequence per structure
+    per_structure = None
+    if not args.no_baselines:
+        ap_host = b.atom_ptr.tolist()
+        ps_cut = mg.cutoff_graph(batch, wl["cutoff"], capacity=E_cut)
+        ps_knn = mg.knn_graph(batch, wl["k"])
+        ps_ms = []
+        for rep in range(4):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mg.rebuild(ps_cut, sync=False, per_structure=True, atom_ptr_host=ap_host)
+            mg.rebuild(ps_knn, sync=False, per_structure=True, atom_ptr_host=ap_host)
+            mg.edge_vectors_fwd(ps_cut, out_vec=out_vec, out_len=out_len)
+            mg.edge_vectors_bwd(ps_cut, batch, None, grad_len, out_vec, out_len, grad_frac, grad_lat)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if rep:
+                ps_ms.append(e0.elapsed_time(e1))
+        assert ps_cut.read_status()["num_edges"] == E_cut
+        ps_step = statistics.mean(ps_ms)
+        per_structure = {"value": units / (ps_step / 1e3), "unit": UNIT, "ms_per_step": ps_step,
+                         "speedup_batched": ps_step / (total_ms / args.steps)}
+
+    clocks = sampler.stop()
+
+    # roofline of the dominant stage
+    hbm_peak, sm_max, peak_src = measured_peaks()
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    stages = {f"{k[0]}.{k[1]}": v / args.steps for k, v in stage_tot.items()}
+    singles = {k: v for k, v in stage_tot.items() if k in SINGLE_KERNEL_STAGES and k in STAGE_MODEL}
+    dom = max(singles, key=singles.get)
+    bound, per_unit, which_units = STAGE_MODEL.get(dom, ("hbm", 36.0, "cut"))
+    n_units = E_cut if which_units == "cut" else E_knn
+    t_launch = stage_tot[dom] / args.steps / 1e3
+    if bound == "hbm":
+        achieved = per_unit * n_units / t_launch / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak}
+    else:
+        achieved = per_unit * n_units / t_launch / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak}
+    roof["kernel"] = f"{dom[0]}.{dom[1]}"
+    roof["peak_source"] = f"{peak_src} ({'MEASURED_PEAKS.json hbm_gbs' if bound == 'hbm' else 'FP32 lanes x clock'})"
+    roof["traffic"] = recorded_traffic(args.config, dom)
+    roof["work_per_launch"] = f"{per_unit:g} {'B' if bound == 'hbm' else 'flop'}/edge x {n_units} edges"
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_baselines:
+            cpu = cpu_baseline_leg(args, b, wl)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl["name"], "structures": b.num_structures, "atoms": b.total_atoms,
+                           "cutoff_A": wl["cutoff"], "k": wl["k"], "edges_per_step": {"cutoff": E_cut, "knn": E_knn},
+                           "l2": "flushed between timed steps (256 MiB write, outside the step events)",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                           "step": "cutoff build + KNN build (CUDA-graph plans) + edge-vector fwd + bwd"},
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": gpu_launches, "clocks": clocks, "per_structure": per_structure,
+                "stage_ms_per_step": stages, "wall_s_timed_region": t_wall}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank)
+    return run_mine(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

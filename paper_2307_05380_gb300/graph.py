@@ -238,9 +238,12 @@ def build_per_structure(batch: Batch, kind: str, cutoff: float = 0.0, k: int = 0
     return _build(kd, batch, cutoff, k, capacity, with_vectors, with_perm, opts, sync, per_structure=True)
 
 
-def rebuild(g: Graph, sync: bool = True) -> Graph:
-    """Run the build again into the same buffers (same parameters)."""
-    _launch_build(g)
+def rebuild(g: Graph, sync: bool = True, per_structure: bool = False, atom_ptr_host=None) -> Graph:
+    """Run the build again into the same buffers (same parameters); per_structure
+    selects the one-launch-sequence-per-structure comparison build."""
+    if per_structure and atom_ptr_host is None:
+        atom_ptr_host = g.batch.atom_ptr.cpu().tolist()
+    _launch_build(g, per_structure, atom_ptr_host)
     return _finish(g, sync)
 
 
