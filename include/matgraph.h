@@ -195,6 +195,28 @@ int64_t mg_last_launch_count(mg_context_t ctx);
  * (MG_PROF_CUTOFF, MG_PROF_KNN, MG_PROF_FWD, MG_PROF_BWD), then writes up to max_stages
  * stage names (static strings) and durations in milliseconds.  Returns the number of
  * stages, or -1 if that kind has not run with profiling on. */
+/* Cutoff graph without a caller workspace (no counterpart in the paper; a library
+ * convenience).  Some callers cannot hand the library a workspace: code that runs
+ * inside another framework's allocator (which owns all device memory through its own
+ * pool), plug-ins that may not call cudaMalloc because it can synchronise the device,
+ * or real-time loops that must not allocate after start-up.  This entry point takes
+ * the same inputs and outputs as mg_cutoff_graph but keeps its scratch in a fixed
+ * array of MG_NOALLOC_SCRATCH_BYTES bytes that the library holds in device memory on
+ * every GPU where it is loaded, until the process exits.  It never allocates.
+ *   - Limit: a batch whose scratch (mg_workspace_size with max_edges = capacity when
+ *     perm_dst is requested, else 0) exceeds MG_NOALLOC_SCRATCH_BYTES is rejected
+ *     with MG_ERR_WORKSPACE before anything is launched.
+ *   - The first call on a device looks up the array's device address (with that device
+ *     current); make that first call before any stream capture.
+ *   - All calls on one device share the array, and the previous call's contents stay
+ *     in it (the kernels clear what they need).  Calls whose work overlaps on the GPU
+ *     (different streams, no ordering between them) race on the array: order them.
+ * Output is identical to mg_cutoff_graph's; the build is not recorded for
+ * mg_update_graph. */
+#define MG_NOALLOC_SCRATCH_BYTES (32u << 20)
+mg_status_t mg_cutoff_graph_noalloc(mg_context_t ctx, const mg_batch_t *batch, float cutoff,
+                                    const mg_opts_t *opts, mg_graph_t *graph, void *stream);
+
 #define MG_PROF_CUTOFF 0
 #define MG_PROF_KNN 1
 #define MG_PROF_FWD 2

@@ -61,6 +61,8 @@ SIGNATURES = [
     ("mg_autotune", c_int32, [c_void_p, ctypes.POINTER(MgBatch), c_int32, c_float, c_int32,
                               ctypes.POINTER(MgGraph), c_void_p, c_size_t, c_void_p]),
     ("mg_last_launch_count", c_int64, [c_void_p]),
+    ("mg_cutoff_graph_noalloc", c_int32, [c_void_p, ctypes.POINTER(MgBatch), c_float, ctypes.POINTER(MgOpts),
+                                          ctypes.POINTER(MgGraph), c_void_p]),
     ("mg_profile_enable", c_int32, [c_void_p, c_int32]),
     ("mg_stage_times", c_int32, [c_void_p, c_int32, c_int32, ctypes.POINTER(ctypes.c_char_p),
                                  ctypes.POINTER(c_float)]),

@@ -321,6 +321,34 @@ mg_status_t build_and_record(mg_context *ctx, int kind, const mg_batch_t *b, flo
 
 }  // namespace
 
+// Scratch for mg_cutoff_graph_noalloc: a fixed device array, so that callers which
+// cannot provide a workspace (see matgraph.h) never make the library allocate.  Its
+// name in host code is only a host-side handle: kernels receive the device address that
+// cudaGetSymbolAddress returns for the current device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MG_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device, looked up once per device.
+mg_status_t noalloc_scratch(void **out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return MG_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MG_ERR_CUDA;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return MG_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 mg_status_t mg_create(mg_context_t *ctx, int device) {
@@ -598,6 +626,29 @@ mg_status_t mg_edge_vectors_bwd(mg_context_t ctx, const mg_batch_t *b, const mg_
     const int n = 3;
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->last_launches = n;
+    return MG_OK;
+}
+
+mg_status_t mg_cutoff_graph_noalloc(mg_context_t ctx, const mg_batch_t *b, float cutoff, const mg_opts_t *opts,
+                                    mg_graph_t *g, void *stream) {
+    // Same launch sequence as mg_cutoff_graph, with the fixed scratch array as workspace.
+    // Nothing here allocates device memory; the sequence's own memset nodes clear the
+    // scratch words that must start at zero (work-queue counters, histogram cursors).
+    const mg_opts_t o = defaults(opts);
+    mg_status_t r = check_build_args(ctx, b, o, g);
+    if (r) return r;
+    if (!(cutoff > 0.f)) return MG_ERR_INVALID_ARGUMENT;
+    const size_t need = layout(b->num_structures, b->total_atoms, g->perm_dst ? g->capacity : 0).total;
+    if (need > (size_t)MG_NOALLOC_SCRATCH_BYTES) return MG_ERR_WORKSPACE;  // batch too large for the array
+    void *scratch = nullptr;
+    r = noalloc_scratch(&scratch);
+    if (r) return r;
+    int launches = 0;
+    r = enqueue_build(ctx, MG_KIND_CUTOFF, b, cutoff, nullptr, 0, o, g, scratch, need,
+                      static_cast<cudaStream_t>(stream), &launches);
+    if (r) return r;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->last_launches = launches;
     return MG_OK;
 }
 
