@@ -91,9 +91,12 @@ struct Marker {
 size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-    size_t recs, pos, atom_struct, cnt, cursor, tile_sum, src_ptr, gpart, lpart, sort_tmp, queue, total;
+    size_t recs, pos, atom_struct, cnt, cursor, tile_sum, src_ptr, gpart, lpart, queue, bin_cnt, bin_cursor,
+        cell_start, cell_atoms, atom_bin, sort_tmp, total;
 };
 
+// Workspace regions, 256-byte aligned; the edge-sized sort scratch comes last so that
+// any workspace size maps to an exact edge limit.
 Layout layout(int B, int N, int64_t max_edges) {
     Layout L{};
     size_t off = 0;
@@ -103,7 +106,8 @@ Layout layout(int B, int N, int64_t max_edges) {
         return at;
     };
     const size_t n = (size_t)(N > 0 ? N : 1);
-    const size_t tiles = (size_t)((N + 1 + SCAN_TILE - 1) / SCAN_TILE + 2);
+    const size_t nbins = (size_t)N + (size_t)(B > 0 ? B : 1);
+    const size_t tiles = (nbins + 1 + SCAN_TILE - 1) / SCAN_TILE + 2;
     L.recs = take(sizeof(StructRec) * (size_t)(B > 0 ? B : 1));
     L.pos = take(sizeof(float4) * n);
     L.atom_struct = take(sizeof(int32_t) * n);
@@ -113,9 +117,15 @@ Layout layout(int B, int N, int64_t max_edges) {
     L.src_ptr = take(sizeof(int64_t) * (n + 1));
     L.gpart = take(sizeof(double) * 3 * n);
     L.lpart = take(sizeof(double) * 9 * n);
-    L.sort_tmp = take(sizeof(int32_t) * (size_t)(max_edges > 0 ? max_edges : 1));
     L.queue = take(16 * sizeof(unsigned int));
-    L.total = off;
+    L.bin_cnt = take(sizeof(int32_t) * nbins);
+    L.bin_cursor = take(sizeof(int32_t) * nbins);
+    L.cell_start = take(sizeof(int64_t) * (nbins + 1));
+    L.cell_atoms = take(sizeof(int32_t) * n);
+    L.atom_bin = take(sizeof(int32_t) * n);
+    L.sort_tmp = off;
+    off += sizeof(int32_t) * (size_t)(max_edges > 0 ? max_edges : 0);
+    L.total = align_up(off);
     return L;
 }
 
@@ -132,17 +142,22 @@ Work carve(void *ws, int B, int N, int64_t max_edges) {
     w.src_ptr = reinterpret_cast<int64_t *>(b + L.src_ptr);
     w.gpart = reinterpret_cast<double *>(b + L.gpart);
     w.lpart = reinterpret_cast<double *>(b + L.lpart);
-    w.sort_tmp = reinterpret_cast<int32_t *>(b + L.sort_tmp);
     w.queue = reinterpret_cast<unsigned int *>(b + L.queue);
+    w.bin_cnt = reinterpret_cast<int32_t *>(b + L.bin_cnt);
+    w.bin_cursor = reinterpret_cast<int32_t *>(b + L.bin_cursor);
+    w.cell_start = reinterpret_cast<int64_t *>(b + L.cell_start);
+    w.cell_atoms = reinterpret_cast<int32_t *>(b + L.cell_atoms);
+    w.atom_bin = reinterpret_cast<int32_t *>(b + L.atom_bin);
+    w.sort_tmp = reinterpret_cast<int32_t *>(b + L.sort_tmp);
     w.max_edges = max_edges;
     return w;
 }
 
-// Largest edge count a workspace of ws_bytes supports for this batch.
+// Largest edge count a workspace of ws_bytes supports for this batch (-1: too small).
 int64_t ws_max_edges(int B, int N, size_t ws_bytes) {
     const Layout L0 = layout(B, N, 0);
     if (ws_bytes < L0.total) return -1;
-    return (int64_t)((ws_bytes - L0.total) / sizeof(int32_t));
+    return (int64_t)((ws_bytes - L0.sort_tmp) / sizeof(int32_t));
 }
 
 mg_opts_t defaults(const mg_opts_t *o) {
@@ -202,16 +217,22 @@ mg_status_t enqueue_build(mg_context *ctx, int kind, const mg_batch_t *b, float 
     const int B = b->num_structures, N = b->total_atoms;
     const int64_t me = ws_max_edges(B, N, ws_bytes);
     if (!ws || me < 0) return MG_ERR_WORKSPACE;
+    if (g->perm_dst && me < g->capacity) return MG_ERR_WORKSPACE;  // destination sort scratch
     const Work w = carve(ws, B, N, me);
     int n = 0;
     Marker mk(ctx, kind == MG_KIND_CUTOFF ? MG_PROF_CUTOFF : MG_PROF_KNN, st);
     status_init_kernel<<<1, 1, 0, st>>>(g->status);
     ++n;
     PrepArgs pa{B, N, b->lattice, b->frac, b->atom_ptr, cutoff, cutoff_ps, kind == MG_KIND_KNN ? k : 0,
-                o.band_rel, g->status};
+                o.band_rel, g->status, 0};
     if (launch_prep(pa, w, st)) return MG_ERR_CUDA;
     ++n;
     mk.mark("prep");
+    if (b->max_atoms <= 0 || b->max_atoms >= CELL_MIN_ATOMS) {  // some structure may use a cell list
+        if (launch_bins(B, N, b->frac, w, st)) return MG_ERR_CUDA;
+        n += 6;
+        mk.mark("bin");
+    }
     BuildArgs ba;
     ba.B = B;
     ba.N = N;
@@ -489,6 +510,7 @@ mg_status_t mg_build_per_structure(mg_context_t ctx, const mg_batch_t *b, int32_
     const int B = b->num_structures, N = b->total_atoms;
     const int64_t me = ws_max_edges(B, N, ws_bytes);
     if (!ws || me < 0) return MG_ERR_WORKSPACE;
+    if (g->perm_dst && me < g->capacity) return MG_ERR_WORKSPACE;
     const Work w0 = carve(ws, B, N, me);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int n = 0;
@@ -501,9 +523,13 @@ mg_status_t mg_build_per_structure(mg_context_t ctx, const mg_batch_t *b, int32_
         Work w = w0;
         w.recs = w0.recs + s;  // the structure's record sits at local index 0
         PrepArgs pa{1, hi - lo, b->lattice + 9 * (size_t)s, b->frac, b->atom_ptr + s, cutoff, nullptr,
-                    kind == MG_KIND_KNN ? k : 0, o.band_rel, g->status};
+                    kind == MG_KIND_KNN ? k : 0, o.band_rel, g->status, s};
         if (launch_prep(pa, w, st)) return MG_ERR_CUDA;
         ++n;
+        if (hi - lo >= CELL_MIN_ATOMS) {  // this structure may use a cell list
+            if (launch_bins_one(lo, hi, lo + s, b->frac, w, st)) return MG_ERR_CUDA;
+            n += 7;
+        }
         BuildArgs ba;
         ba.B = B;
         ba.N = N;

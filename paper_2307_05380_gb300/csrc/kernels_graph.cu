@@ -118,6 +118,34 @@ __global__ void __launch_bounds__(128) prep_kernel(PrepArgs a, StructRec *__rest
     R.n_atoms = n;
     R.bad = bad;
     R.pad = 0;
+    // Cell list for large structures: bins at least half the radius wide along each
+    // plane normal (n_k = floor(2 d_k / c)), at most n_atoms bins in total; used when the
+    // bins a source visits cover less than half the cell.
+    R.nb[0] = R.nb[1] = R.nb[2] = 0;
+    R.bin_base = begin + s + a.struct_offset;
+    if (!bad && n >= CELL_MIN_ATOMS) {
+        int nk[3];
+        double prod = 1.0;
+        for (int k = 0; k < 3; ++k) {
+            const double dk = 1.0 / invd[k];
+            nk[k] = (int)fmin(fmax(floor(2.0 * dk / cr), 1.0), 1024.0);
+            prod *= nk[k];
+        }
+        if (prod > n) {
+            const double f = cbrt((double)n / prod);
+            for (int k = 0; k < 3; ++k) nk[k] = max(1, (int)floor(nk[k] * f));
+        }
+        while ((int64_t)nk[0] * nk[1] * nk[2] > n) {  // rounding left too many: trim the largest
+            int kmax = 0;
+            for (int k = 1; k < 3; ++k)
+                if (nk[k] > nk[kmax]) kmax = k;
+            --nk[kmax];
+        }
+        double visited = 1.0;
+        for (int k = 0; k < 3; ++k) visited *= fmin(1.0, (2.0 * cr * invd[k] * nk[k] + 2.0) / nk[k]);
+        if (visited < 0.5)
+            for (int k = 0; k < 3; ++k) R.nb[k] = nk[k];
+    }
     recs[s] = R;
     if (bad) set_error(a.status, bad, s);
 }
@@ -226,6 +254,74 @@ cudaError_t launch_scan(const ScanArgs &a, const Work &w, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ============================================================================ cell list
+
+__global__ void bin_assign_kernel(int atom_lo, int atom_hi, const int32_t *__restrict__ atom_struct,
+                                  const StructRec *__restrict__ recs, const float *__restrict__ frac,
+                                  int32_t *__restrict__ bin_cnt, int32_t *__restrict__ atom_bin) {
+    for (int r = atom_lo + blockIdx.x * blockDim.x + threadIdx.x; r < atom_hi; r += gridDim.x * blockDim.x) {
+        const StructRec &R = recs[atom_struct[r]];
+        if (R.nb[0] == 0) {
+            atom_bin[r] = -1;
+            continue;
+        }
+        const int b0 = bin_of(wrap01(frac[3 * (int64_t)r + 0]), R.nb[0]);
+        const int b1 = bin_of(wrap01(frac[3 * (int64_t)r + 1]), R.nb[1]);
+        const int b2 = bin_of(wrap01(frac[3 * (int64_t)r + 2]), R.nb[2]);
+        const int g = R.bin_base + (b0 * R.nb[1] + b1) * R.nb[2] + b2;
+        atom_bin[r] = g;
+        atomicAdd(&bin_cnt[g], 1);
+    }
+}
+
+__global__ void bin_scatter_kernel(int atom_lo, int atom_hi, const int32_t *__restrict__ atom_struct,
+                                   const StructRec *__restrict__ recs, const int32_t *__restrict__ atom_bin,
+                                   const int64_t *__restrict__ cell_start, int32_t *__restrict__ cursor,
+                                   int32_t *__restrict__ cell_atoms) {
+    for (int r = atom_lo + blockIdx.x * blockDim.x + threadIdx.x; r < atom_hi; r += gridDim.x * blockDim.x) {
+        const int g = atom_bin[r];
+        if (g < 0) continue;
+        const int64_t slot = cell_start[g] + atomicAdd(&cursor[g], 1);
+        cell_atoms[slot] = r - recs[atom_struct[r]].atom_begin;
+    }
+}
+
+__global__ void add_const_kernel(int64_t *__restrict__ out, int n, int64_t c) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q <= n; q += gridDim.x * blockDim.x) out[q] += c;
+}
+
+cudaError_t launch_bins(int B, int N, const float *frac, const Work &w, cudaStream_t s) {
+    const int nbins = N + B;
+    cudaMemsetAsync(w.bin_cnt, 0, sizeof(int32_t) * (size_t)nbins, s);
+    cudaMemsetAsync(w.bin_cursor, 0, sizeof(int32_t) * (size_t)nbins, s);
+    const int grid = max(1, min(4 * num_sms(), (N + 255) / 256));
+    bin_assign_kernel<<<grid, 256, 0, s>>>(0, N, w.atom_struct, w.recs, frac, w.bin_cnt, w.atom_bin);
+    ScanArgs sa{nbins, w.bin_cnt, w.cell_start};
+    cudaError_t e = launch_scan(sa, w, s);
+    if (e) return e;
+    bin_scatter_kernel<<<grid, 256, 0, s>>>(0, N, w.atom_struct, w.recs, w.atom_bin, w.cell_start, w.bin_cursor,
+                                            w.cell_atoms);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bins_one(int atom_lo, int atom_hi, int bin_base, const float *frac, const Work &w,
+                            cudaStream_t s) {
+    const int n = atom_hi - atom_lo;
+    const int nbins = n + 1;
+    cudaMemsetAsync(w.bin_cnt + bin_base, 0, sizeof(int32_t) * (size_t)nbins, s);
+    cudaMemsetAsync(w.bin_cursor + bin_base, 0, sizeof(int32_t) * (size_t)nbins, s);
+    const int grid = max(1, min(4 * num_sms(), (n + 255) / 256));
+    bin_assign_kernel<<<grid, 256, 0, s>>>(atom_lo, atom_hi, w.atom_struct, w.recs, frac, w.bin_cnt, w.atom_bin);
+    ScanArgs sa{nbins, w.bin_cnt + bin_base, w.cell_start + bin_base};
+    cudaError_t e = launch_scan(sa, w, s);
+    if (e) return e;
+    add_const_kernel<<<max(1, min(64, (nbins + 255) / 256)), 256, 0, s>>>(w.cell_start + bin_base, nbins,
+                                                                        (int64_t)atom_lo);
+    bin_scatter_kernel<<<grid, 256, 0, s>>>(atom_lo, atom_hi, w.atom_struct, w.recs, w.atom_bin, w.cell_start,
+                                            w.bin_cursor, w.cell_atoms);
+    return cudaGetLastError();
+}
+
 // ============================================================================ schedule
 
 // Work distribution over source atoms [lo, hi): flat (one warp per atom) or a persistent
@@ -268,8 +364,9 @@ __global__ void __launch_bounds__(256) cutoff_count_kernel(BuildArgs a, Work w) 
         const float thr_lo = R.thr_lo, thr_hi = R.thr_hi;
         const double rr = R.rr;
         int count = 0;
-        for_each_candidate(S, a.frac, w.pos, R.cut, [&](bool vc, float d2, bool self, int ow, int t2,
-                                                         const RowRegs &rw) {
+        const Cells cells{w.cell_start, w.cell_atoms};
+        for_each_candidate(S, a.frac, w.pos, cells, true, R.cut, [&](bool vc, float d2, bool self, int ow, int t2,
+                                                                      const RowRegs &rw) {
             const bool cand = vc && !self;
             bool in = cand && d2 < thr_lo;
             const bool band = cand && !in && d2 <= thr_hi;
@@ -360,10 +457,40 @@ cudaError_t launch_cutoff_finalize(const BuildArgs &a, const Work &w, cudaStream
 
 // ============================================================================ cutoff write
 
+constexpr int WRITE_WARPS = 4;
+
+// Emission of one source's edges: edge q of the source goes to row base + q.
+__device__ __forceinline__ void emit_edge(const mg_graph_t &g, const Source &S, int i, int64_t e, int64_t jr,
+                                          float xj0, float xj1, float xj2, int t0, int t1, int t2) {
+    g.src[e] = i;
+    g.dst[e] = (int32_t)jr;
+    g.offset[3 * e + 0] = t0;
+    g.offset[3 * e + 1] = t1;
+    g.offset[3 * e + 2] = t2;
+    if (g.vec || g.len) {
+        const float3 v = edge_vec_ff(S.L, S.xi0, S.xi1, S.xi2, xj0, xj1, xj2, t0, t1, t2);
+        if (g.vec) {
+            g.vec[3 * e + 0] = v.x;
+            g.vec[3 * e + 1] = v.y;
+            g.vec[3 * e + 2] = v.z;
+        }
+        if (g.len) g.len[e] = vec_len(v);
+    }
+}
+
+// The count kernel's scan again, emitting each source's edges at its scanned offset in
+// canonical order.  All-pairs structures emit in enumeration order (already canonical,
+// ballot/popc positions).  Cell-list structures gather the source's (j, t) keys in
+// shared memory, sort them, then emit; a source with more edges than WRITE_CAP or an
+// offset beyond the packed key range is emitted through the all-pairs enumeration.
 template <int SCHED>
-__global__ void __launch_bounds__(256) cutoff_write_kernel(BuildArgs a, Work w) {
+__global__ void __launch_bounds__(WRITE_WARPS * 32) cutoff_write_kernel(BuildArgs a, Work w) {
+    __shared__ unsigned long long keys_all[WRITE_WARPS][WRITE_CAP];
+    unsigned long long *keys = keys_all[threadIdx.x >> 5];
     AtomLoop<SCHED> loop{a.atom_lo, a.atom_hi, w.queue};
     const mg_graph_t g = a.g;
+    const Cells cells{w.cell_start, w.cell_atoms};
+    const unsigned lt = (1u << lane_id()) - 1u;
     for (int i = loop.first(); i < a.atom_hi; i = loop.next()) {
         const int64_t base = a.src_ptr[i];
         const int64_t endp = a.src_ptr[i + 1];
@@ -375,10 +502,56 @@ __global__ void __launch_bounds__(256) cutoff_write_kernel(BuildArgs a, Work w) 
         load_source(S, w.recs, s, a.frac, w.pos, i);
         const float thr_lo = R.thr_lo, thr_hi = R.thr_hi;
         const double rr = R.rr;
+        const int64_t deg = endp - base;
+        bool done = false;
+        if (S.nb[0] != 0 && deg <= WRITE_CAP) {
+            int m = 0;
+            bool range_bad = false;
+            for_each_candidate(S, a.frac, w.pos, cells, true, R.cut, [&](bool vc, float d2, bool self, int ow,
+                                                                          int t2, const RowRegs &rw) {
+                const bool cand = vc && !self;
+                bool in = cand && d2 < thr_lo;
+                const bool band = cand && !in && d2 <= thr_hi;
+                if (__any_sync(FULL, in || band)) {
+                    const int jj = __shfl_sync(FULL, rw.j, ow);
+                    const int t0 = __shfl_sync(FULL, rw.t0, ow);
+                    const int t1 = __shfl_sync(FULL, rw.t1, ow);
+                    if (band) {
+                        const int64_t jr = (int64_t)S.begin + jj;
+                        in = canon_d2(S.L, S.xi0, S.xi1, S.xi2, a.frac[3 * jr], a.frac[3 * jr + 1],
+                                      a.frac[3 * jr + 2], t0, t1, t2) < rr;
+                    }
+                    const unsigned bal = __ballot_sync(FULL, in);
+                    if (in) {
+                        if (abs(t0) > OFFSET_KEY_LIM || abs(t1) > OFFSET_KEY_LIM || abs(t2) > OFFSET_KEY_LIM)
+                            range_bad = true;
+                        const int p = m + __popc(bal & lt);
+                        if (p < WRITE_CAP)
+                            keys[p] = ((unsigned long long)(unsigned)jj << 32) | pack_t(t0, t1, t2);
+                    }
+                    m += __popc(bal);
+                }
+            });
+            if (!__any_sync(FULL, range_bad) && m == deg) {
+                int P = 64;
+                while (P < m) P <<= 1;
+                warp_smem_sort_u64(keys, m, P);
+                for (int q = lane_id(); q < m; q += 32) {
+                    const unsigned long long key = keys[q];
+                    int t0, t1, t2;
+                    unpack_t((uint32_t)(key & 0xffffffffull), t0, t1, t2);
+                    const int64_t jr = (int64_t)S.begin + (int)(key >> 32);
+                    emit_edge(g, S, i, base + q, jr, a.frac[3 * jr], a.frac[3 * jr + 1], a.frac[3 * jr + 2], t0,
+                              t1, t2);
+                }
+                done = true;
+            }
+            __syncwarp();
+        }
+        if (done) continue;
         int64_t out = base;
-        const unsigned lt = (1u << lane_id()) - 1u;
-        for_each_candidate(S, a.frac, w.pos, R.cut, [&](bool vc, float d2, bool self, int ow, int t2,
-                                                         const RowRegs &rw) {
+        for_each_candidate(S, a.frac, w.pos, cells, false, R.cut, [&](bool vc, float d2, bool self, int ow,
+                                                                       int t2, const RowRegs &rw) {
             const bool cand = vc && !self;
             bool in = cand && d2 < thr_lo;
             const bool band = cand && !in && d2 <= thr_hi;
@@ -397,22 +570,7 @@ __global__ void __launch_bounds__(256) cutoff_write_kernel(BuildArgs a, Work w) 
                 const unsigned bal = __ballot_sync(FULL, in);
                 if (in) {
                     const int64_t e = out + __popc(bal & lt);
-                    if (e < endp) {
-                        g.src[e] = i;
-                        g.dst[e] = (int32_t)jr;
-                        g.offset[3 * e + 0] = t0;
-                        g.offset[3 * e + 1] = t1;
-                        g.offset[3 * e + 2] = t2;
-                        if (g.vec || g.len) {
-                            const float3 v = edge_vec_ff(S.L, S.xi0, S.xi1, S.xi2, xj0, xj1, xj2, t0, t1, t2);
-                            if (g.vec) {
-                                g.vec[3 * e + 0] = v.x;
-                                g.vec[3 * e + 1] = v.y;
-                                g.vec[3 * e + 2] = v.z;
-                            }
-                            if (g.len) g.len[e] = vec_len(v);
-                        }
-                    }
+                    if (e < endp) emit_edge(g, S, i, e, jr, xj0, xj1, xj2, t0, t1, t2);
                 }
                 out += __popc(bal);
             }
@@ -424,7 +582,7 @@ __global__ void __launch_bounds__(256) cutoff_write_kernel(BuildArgs a, Work w) 
 cudaError_t launch_cutoff_write(const BuildArgs &a, const Work &w, cudaStream_t s) {
     const int atoms = a.atom_hi - a.atom_lo;
     if (atoms <= 0) return cudaSuccess;
-    const int threads = 256;
+    const int threads = WRITE_WARPS * 32;
     if (a.schedule == 2) {
         cudaError_t e = launch_reset_queue(w, s);
         if (e) return e;

@@ -113,28 +113,6 @@ struct TopK {
     }
 };
 
-// Sort n (<= P, P a power of two >= 64) 64-bit keys in shared memory with one warp.
-__device__ __forceinline__ void warp_smem_sort_u64(unsigned long long *b, int n, int P) {
-    const int lane = lane_id();
-    for (int q = n + lane; q < P; q += 32) b[q] = ~0ull;
-    __syncwarp();
-    for (int size = 2; size <= P; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int q = lane; q < P / 2; q += 32) {
-                const int x = 2 * stride * (q / stride) + (q % stride);
-                const int y = x + stride;
-                const bool asc = (x & size) == 0;
-                const unsigned long long vx = b[x], vy = b[y];
-                if ((vx > vy) == asc) {
-                    b[x] = vy;
-                    b[y] = vx;
-                }
-            }
-            __syncwarp();
-        }
-    }
-}
-
 // Work distribution over source atoms (same scheme as the cutoff kernels).
 template <int SCHED>
 struct KnnLoop {
@@ -164,6 +142,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_kernel(BuildArgs a, Work w
     const unsigned lt = (1u << lane) - 1u;
     const mg_graph_t g = a.g;
     KnnLoop<SCHED> loop{a.atom_lo, a.atom_hi, w.queue};
+    const Cells cells{w.cell_start, w.cell_atoms};
     unsigned long long nre = 0, ncand = 0;
 
     for (int i = loop.first(); i < a.atom_hi; i = loop.next()) {
@@ -182,7 +161,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_kernel(BuildArgs a, Work w
             float thr = F_INF;
             int found = 0;
             const float rho2 = rho * rho;
-            for_each_candidate(Src, a.frac, w.pos, rho, [&](bool vc, float d2, bool self, int, int,
+            for_each_candidate(Src, a.frac, w.pos, cells, true, rho,[&](bool vc, float d2, bool self, int, int,
                                                               const RowRegs &) {
                 const bool c = vc && !self && d2 < rho2;
                 found += __popc(__ballot_sync(FULL, c));
@@ -216,7 +195,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_kernel(BuildArgs a, Work w
         TopK<XKey, S> ek;
         ek.init();
         XKey ethr = kinf(XKey{});
-        for_each_candidate(Src, a.frac, w.pos, rho, [&](bool vc, float d2, bool self, int ow, int t2,
+        for_each_candidate(Src, a.frac, w.pos, cells, true, rho,[&](bool vc, float d2, bool self, int ow, int t2,
                                                           const RowRegs &rw) {
             const bool c = vc && !self;
             const bool in = c && d2 < lo_thr;

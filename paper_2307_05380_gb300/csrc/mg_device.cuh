@@ -32,8 +32,14 @@ struct StructRec {
     int32_t atom_begin;
     int32_t n_atoms;
     int32_t bad;       // mg_status_t for this structure (0 = usable)
+    int32_t nb[3];     // cell-list bins per axis; nb[0] == 0: the structure uses all pairs
+    int32_t bin_base;  // first bin of the structure: atom_begin + structure index
     int32_t pad;
 };
+static_assert(sizeof(StructRec) == 144, "record layout");
+
+constexpr int CELL_MIN_ATOMS = 128;  // smallest structure that may use a cell list
+constexpr int WRITE_CAP = 1024;      // edges of one source sorted in shared memory
 
 struct alignas(8) Status {  // device mirror of mg_device_status_t
     int32_t code;
@@ -189,6 +195,29 @@ __device__ __forceinline__ void unpack_t(uint32_t p, int &t0, int &t1, int &t2) 
     t0 = (int)((p >> 20) & 1023u) - 512;
     t1 = (int)((p >> 10) & 1023u) - 512;
     t2 = (int)(p & 1023u) - 512;
+}
+
+// Sort n (<= P, P a power of two >= 64) 64-bit keys in shared memory with one warp
+// (bitonic network; pads [n, P) with the largest key).
+__device__ __forceinline__ void warp_smem_sort_u64(unsigned long long *b, int n, int P) {
+    const int lane = lane_id();
+    for (int q = n + lane; q < P; q += 32) b[q] = ~0ull;
+    __syncwarp();
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int q = lane; q < P / 2; q += 32) {
+                const int x = 2 * stride * (q / stride) + (q % stride);
+                const int y = x + stride;
+                const bool asc = (x & size) == 0;
+                const unsigned long long vx = b[x], vy = b[y];
+                if ((vx > vy) == asc) {
+                    b[x] = vy;
+                    b[y] = vx;
+                }
+            }
+            __syncwarp();
+        }
+    }
 }
 
 // ------------------------------------------------------------------ error model

@@ -5,13 +5,18 @@
 // directly from interplanar spacings: every image with |v| < rho satisfies
 // |x_j,k - x_i,k + t_k| <= rho ||L^-1[:, k]|| = rho / d_k, so each pair (i, j) gets an exact
 // per-axis offset box; each (t0, t1) row of that box is further trimmed to the chord of
-// the sphere along L_2.  The warp then walks the candidates 32 at a time in canonical
-// order (j ascending, then t0, t1, t2 ascending) through three flattening levels:
-//   level 1: lanes = target atoms j, each with its box (row count n0 * n1);
-//   level 2: lanes = rows (j, t0, t1), each with its trimmed t2 interval;
-//   level 3: lanes = candidates (j, t0, t1, t2).
-// Owners are found with a warp binary search over inclusive prefix counts, so each
-// step evaluates exactly 32 candidates and lane order equals canonical order.
+// the sphere along L_2.  The warp walks the candidates 32 at a time through flattening
+// levels (target atoms -> rows -> candidates), finding owners with a warp binary search
+// over inclusive prefix counts, so that each step evaluates exactly 32 candidates.
+//
+// Target atoms come from one of two drivers:
+//   all pairs  j = 0 .. n-1 in order, so lane order is canonical order (j, t0, t1, t2);
+//   cell list  the structure's atoms binned by fractional coordinate (frac(x) * n_k per
+//              axis, bins at least half the radius wide); a source visits only the bins
+//              its reach interval [frac(x_i) - R_k, frac(x_i) + R_k] touches on each axis
+//              (every bin at most once, also under wrap-around).  Bins only select
+//              targets: offsets still come from the exact per-pair box on the unwrapped
+//              coordinates, so every image within reach is found exactly once.
 #pragma once
 
 #include "mg_device.cuh"
@@ -28,6 +33,8 @@ struct Source {
     int i_loc;   // local index of the source atom within its structure
     int begin;   // global row of the structure's first atom
     int n;       // atoms in the structure
+    int nb[3];   // bins per axis (nb[0] == 0: all-pairs structure)
+    int bin_base;
 };
 
 __device__ __forceinline__ void load_source(Source &S, const StructRec *__restrict__ recs, int s,
@@ -37,7 +44,11 @@ __device__ __forceinline__ void load_source(Source &S, const StructRec *__restri
 #pragma unroll
     for (int q = 0; q < 9; ++q) S.L[q] = R.L[q];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) S.invd[k] = R.invd[k];
+    for (int k = 0; k < 3; ++k) {
+        S.invd[k] = R.invd[k];
+        S.nb[k] = R.nb[k];
+    }
+    S.bin_base = R.bin_base;
     S.L2norm2 = R.L2norm2;
     S.L2norm = R.L2norm;
     S.begin = R.atom_begin;
@@ -50,11 +61,135 @@ __device__ __forceinline__ void load_source(Source &S, const StructRec *__restri
     S.pi = make_float3(p.x, p.y, p.z);
 }
 
+// Cell list of the batch (device pointers in the workspace).
+struct Cells {
+    const int64_t *__restrict__ start;   // [bins + 1] first slot of each bin (global)
+    const int32_t *__restrict__ atoms;   // [slots] local atom index of each slot
+};
+
 // Row-level values a visitor may fetch from the row's owner lane (shuffle source ow).
 struct RowRegs {
     int j;   // local target index
     int t0, t1;
 };
+
+// Wrapped fractional coordinate in [0, 1).
+__device__ __forceinline__ float wrap01(float x) {
+    float w = __fsub_rn(x, floorf(x));
+    return w < 1.0f ? w : 0.0f;
+}
+
+// Bin of a wrapped coordinate along an axis with n bins.
+__device__ __forceinline__ int bin_of(float w, int n) {
+    return min(max((int)floorf(__fmul_rn(w, (float)n)), 0), n - 1);
+}
+
+// Levels 2 and 3 for the 32 target atoms held by the lanes (jl valid where vj).
+template <class Visit>
+__device__ __forceinline__ void visit_targets(const Source &S, const float *__restrict__ frac,
+                                              const float4 *__restrict__ pos, const float Rk[3],
+                                              float rho2p, float mu0, int jl, bool vj, Visit &visit) {
+    const int lane = lane_id();
+    int lo[3], nn[3];
+    float3 a = make_float3(0.f, 0.f, 0.f);
+    if (vj) {
+        const int64_t row = (int64_t)S.begin + jl;
+        const float dx[3] = {__fsub_rn(frac[3 * row + 0], S.xi0), __fsub_rn(frac[3 * row + 1], S.xi1),
+                             __fsub_rn(frac[3 * row + 2], S.xi2)};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float m = 1e-5f * (1.0f + fabsf(dx[k]) + Rk[k]);
+            lo[k] = (int)ceilf(-Rk[k] - dx[k] - m);
+            const int hi = (int)floorf(Rk[k] - dx[k] + m);
+            nn[k] = max(0, hi - lo[k] + 1);
+        }
+        const float4 pj = pos[row];
+        a = make_float3(__fsub_rn(pj.x, S.pi.x), __fsub_rn(pj.y, S.pi.y), __fsub_rn(pj.z, S.pi.z));
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = 0;
+            nn[k] = 0;
+        }
+    }
+    const int rows = (nn[2] > 0) ? nn[0] * nn[1] : 0;
+    const int incl = warp_incl_scan(rows);
+    const int total = __shfl_sync(FULL, incl, 31);
+    const int excl = incl - rows;
+
+    for (int rb = 0; rb < total; rb += 32) {
+        const int q = rb + lane;
+        const bool vr = q < total;
+        const int ow = warp_owner(incl, vr ? q : total - 1);
+        const int o_excl = __shfl_sync(FULL, excl, ow);
+        const int o_n1 = __shfl_sync(FULL, nn[1], ow);
+        const int o_lo0 = __shfl_sync(FULL, lo[0], ow);
+        const int o_lo1 = __shfl_sync(FULL, lo[1], ow);
+        const int o_lo2 = __shfl_sync(FULL, lo[2], ow);
+        const int o_n2 = __shfl_sync(FULL, nn[2], ow);
+        const float ax = __shfl_sync(FULL, a.x, ow);
+        const float ay = __shfl_sync(FULL, a.y, ow);
+        const float az = __shfl_sync(FULL, a.z, ow);
+        RowRegs rr;
+        rr.j = __shfl_sync(FULL, jl, ow);
+        const int rem = vr ? q - o_excl : 0;
+        const int d0 = rem / max(o_n1, 1);
+        rr.t0 = o_lo0 + d0;
+        rr.t1 = o_lo1 + (rem - d0 * o_n1);
+        // row base b = a + t0 L0 + t1 L1
+        const float ft0 = (float)rr.t0, ft1 = (float)rr.t1;
+        const float bx = __fmaf_rn(ft1, S.L[3], __fmaf_rn(ft0, S.L[0], ax));
+        const float by = __fmaf_rn(ft1, S.L[4], __fmaf_rn(ft0, S.L[1], ay));
+        const float bz = __fmaf_rn(ft1, S.L[5], __fmaf_rn(ft0, S.L[2], az));
+        // chord of the sphere along L_2: t2 in t2c +- w (widened)
+        int c_lo = o_lo2, c_hi = o_lo2 + o_n2 - 1;
+        {
+            const float bl = __fmaf_rn(bz, S.L[8], __fmaf_rn(by, S.L[7], __fmul_rn(bx, S.L[6])));
+            const float t2c = -bl / S.L2norm2;
+            const float px = __fmaf_rn(t2c, S.L[6], bx);
+            const float py = __fmaf_rn(t2c, S.L[7], by);
+            const float pz = __fmaf_rn(t2c, S.L[8], bz);
+            const float perp2 = __fmaf_rn(pz, pz, __fmaf_rn(py, py, __fmul_rn(px, px)));
+            const float scale =
+                sqrtf(__fmaf_rn(bz, bz, __fmaf_rn(by, by, __fmul_rn(bx, bx)))) + fabsf(t2c) * S.L2norm;
+            if (scale <= 100.0f * sqrtf(rho2p)) {  // trimming error analysis holds
+                const float wsq = (rho2p - perp2) / S.L2norm2;
+                if (wsq < 0.0f) {
+                    c_hi = c_lo - 1;
+                } else {
+                    const float w = sqrtf(wsq);
+                    const float mu = mu0 + 4e-7f * fabsf(t2c);
+                    c_lo = max(c_lo, (int)ceilf(t2c - w - mu));
+                    c_hi = min(c_hi, (int)floorf(t2c + w + mu));
+                }
+            }
+        }
+        const int clen = vr ? max(0, c_hi - c_lo + 1) : 0;
+        const bool row_self = (rr.j == S.i_loc) && rr.t0 == 0 && rr.t1 == 0;
+        const int incl2 = warp_incl_scan(clen);
+        const int total2 = __shfl_sync(FULL, incl2, 31);
+        const int excl2 = incl2 - clen;
+
+        for (int cb = 0; cb < total2; cb += 32) {
+            const int c = cb + lane;
+            const bool vc = c < total2;
+            const int ow2 = warp_owner(incl2, vc ? c : total2 - 1);
+            const int e2 = __shfl_sync(FULL, excl2, ow2);
+            const int clo = __shfl_sync(FULL, c_lo, ow2);
+            const float cbx = __shfl_sync(FULL, bx, ow2);
+            const float cby = __shfl_sync(FULL, by, ow2);
+            const float cbz = __shfl_sync(FULL, bz, ow2);
+            const bool cself = __shfl_sync(FULL, row_self ? 1 : 0, ow2) != 0;
+            const int t2 = clo + (c - e2);
+            const float ft2 = (float)t2;
+            const float vx = __fmaf_rn(ft2, S.L[6], cbx);
+            const float vy = __fmaf_rn(ft2, S.L[7], cby);
+            const float vz = __fmaf_rn(ft2, S.L[8], cbz);
+            const float d2 = __fmaf_rn(vz, vz, __fmaf_rn(vy, vy, __fmul_rn(vx, vx)));
+            visit(vc, d2, cself && t2 == 0, ow2, t2, rr);
+        }
+    }
+}
 
 // Visit all candidates with |v| < rho (a superset: box and chord are widened by safety
 // margins; the caller classifies by distance).  For each chunk of 32 candidates every
@@ -62,11 +197,12 @@ struct RowRegs {
 //     visit(valid, d2, is_self, owner_lane, t2, rows)
 // where d2 is the FP32 squared distance, is_self marks (i, i, 0), owner_lane is the lane
 // whose `rows` hold this candidate's j, t0, t1 (fetch them with __shfl_sync), t2 the
-// last offset component.  All calls are warp-uniform.
+// last offset component.  All calls are warp-uniform.  With use_cells, targets come from
+// the cell list (any order of j); otherwise in ascending j (canonical order).
 template <class Visit>
 __device__ __forceinline__ void for_each_candidate(const Source &S, const float *__restrict__ frac,
-                                                   const float4 *__restrict__ pos, float rho,
-                                                   Visit &&visit) {
+                                                   const float4 *__restrict__ pos, const Cells &cells,
+                                                   bool use_cells, float rho, Visit &&visit) {
     const int lane = lane_id();
     float Rk[3];
 #pragma unroll
@@ -74,104 +210,60 @@ __device__ __forceinline__ void for_each_candidate(const Source &S, const float 
     const float rho2p = rho * rho * 1.0002f;
     const float mu0 = 1e-3f * (1.0f + rho / S.L2norm);
 
-    for (int jb = 0; jb < S.n; jb += 32) {
-        const int jl = jb + lane;
-        const bool vj = jl < S.n;
-        int lo[3], nn[3];
-        float3 a = make_float3(0.f, 0.f, 0.f);
-        if (vj) {
-            const int64_t row = (int64_t)S.begin + jl;
-            const float dx[3] = {__fsub_rn(frac[3 * row + 0], S.xi0), __fsub_rn(frac[3 * row + 1], S.xi1),
-                                 __fsub_rn(frac[3 * row + 2], S.xi2)};
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const float m = 1e-5f * (1.0f + fabsf(dx[k]) + Rk[k]);
-                lo[k] = (int)ceilf(-Rk[k] - dx[k] - m);
-                const int hi = (int)floorf(Rk[k] - dx[k] + m);
-                nn[k] = max(0, hi - lo[k] + 1);
-            }
-            const float4 pj = pos[row];
-            a = make_float3(__fsub_rn(pj.x, S.pi.x), __fsub_rn(pj.y, S.pi.y), __fsub_rn(pj.z, S.pi.z));
-        } else {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) { lo[k] = 0; nn[k] = 0; }
+    if (!use_cells || S.nb[0] == 0) {
+        for (int jb = 0; jb < S.n; jb += 32) {
+            const int jl = jb + lane;
+            visit_targets(S, frac, pos, Rk, rho2p, mu0, jl, jl < S.n, visit);
         }
-        const int rows = (nn[2] > 0) ? nn[0] * nn[1] : 0;
-        const int incl = warp_incl_scan(rows);
+        return;
+    }
+    // bins touched by the reach interval on each axis (each bin once)
+    int blo[3], bcnt[3];
+    {
+        const float xw[3] = {wrap01(S.xi0), wrap01(S.xi1), wrap01(S.xi2)};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int nk = S.nb[k];
+            const float m = 1e-5f * (1.0f + Rk[k]);
+            const int lo = (int)floorf((xw[k] - Rk[k] - m) * (float)nk);
+            const int hi = (int)floorf((xw[k] + Rk[k] + m) * (float)nk);
+            if (hi - lo + 1 >= nk) {
+                blo[k] = 0;
+                bcnt[k] = nk;
+            } else {
+                blo[k] = lo;
+                bcnt[k] = hi - lo + 1;
+            }
+        }
+    }
+    const int nbins = bcnt[0] * bcnt[1] * bcnt[2];
+    for (int bb = 0; bb < nbins; bb += 32) {
+        const int q = bb + lane;
+        const bool vb = q < nbins;
+        int64_t st = 0;
+        int cnt = 0;
+        if (vb) {
+            const int c2 = q % bcnt[2];
+            const int c1 = (q / bcnt[2]) % bcnt[1];
+            const int c0 = q / (bcnt[2] * bcnt[1]);
+            const int b0 = ((blo[0] + c0) % S.nb[0] + S.nb[0]) % S.nb[0];
+            const int b1 = ((blo[1] + c1) % S.nb[1] + S.nb[1]) % S.nb[1];
+            const int b2 = ((blo[2] + c2) % S.nb[2] + S.nb[2]) % S.nb[2];
+            const int64_t g = (int64_t)S.bin_base + (b0 * S.nb[1] + b1) * S.nb[2] + b2;
+            st = cells.start[g];
+            cnt = (int)(cells.start[g + 1] - st);
+        }
+        const int incl = warp_incl_scan(cnt);
         const int total = __shfl_sync(FULL, incl, 31);
-        const int excl = incl - rows;
-
-        for (int rb = 0; rb < total; rb += 32) {
-            const int q = rb + lane;
-            const bool vr = q < total;
-            const int ow = warp_owner(incl, vr ? q : total - 1);
-            const int o_excl = __shfl_sync(FULL, excl, ow);
-            const int o_n1 = __shfl_sync(FULL, nn[1], ow);
-            const int o_lo0 = __shfl_sync(FULL, lo[0], ow);
-            const int o_lo1 = __shfl_sync(FULL, lo[1], ow);
-            const int o_lo2 = __shfl_sync(FULL, lo[2], ow);
-            const int o_n2 = __shfl_sync(FULL, nn[2], ow);
-            const float ax = __shfl_sync(FULL, a.x, ow);
-            const float ay = __shfl_sync(FULL, a.y, ow);
-            const float az = __shfl_sync(FULL, a.z, ow);
-            RowRegs rr;
-            rr.j = __shfl_sync(FULL, jl, ow);
-            const int rem = vr ? q - o_excl : 0;
-            const int d0 = rem / max(o_n1, 1);
-            rr.t0 = o_lo0 + d0;
-            rr.t1 = o_lo1 + (rem - d0 * o_n1);
-            // row base b = a + t0 L0 + t1 L1
-            const float ft0 = (float)rr.t0, ft1 = (float)rr.t1;
-            const float bx = __fmaf_rn(ft1, S.L[3], __fmaf_rn(ft0, S.L[0], ax));
-            const float by = __fmaf_rn(ft1, S.L[4], __fmaf_rn(ft0, S.L[1], ay));
-            const float bz = __fmaf_rn(ft1, S.L[5], __fmaf_rn(ft0, S.L[2], az));
-            // chord of the sphere along L_2: t2 in t2c +- w (widened)
-            int c_lo = o_lo2, c_hi = o_lo2 + o_n2 - 1;
-            {
-                const float bl = __fmaf_rn(bz, S.L[8], __fmaf_rn(by, S.L[7], __fmul_rn(bx, S.L[6])));
-                const float t2c = -bl / S.L2norm2;
-                const float px = __fmaf_rn(t2c, S.L[6], bx);
-                const float py = __fmaf_rn(t2c, S.L[7], by);
-                const float pz = __fmaf_rn(t2c, S.L[8], bz);
-                const float perp2 = __fmaf_rn(pz, pz, __fmaf_rn(py, py, __fmul_rn(px, px)));
-                const float scale = sqrtf(__fmaf_rn(bz, bz, __fmaf_rn(by, by, __fmul_rn(bx, bx)))) +
-                                    fabsf(t2c) * S.L2norm;
-                if (scale <= 100.0f * rho) {  // trimming error analysis holds
-                    const float wsq = (rho2p - perp2) / S.L2norm2;
-                    if (wsq < 0.0f) {
-                        c_hi = c_lo - 1;
-                    } else {
-                        const float w = sqrtf(wsq);
-                        const float mu = mu0 + 4e-7f * fabsf(t2c);
-                        c_lo = max(c_lo, (int)ceilf(t2c - w - mu));
-                        c_hi = min(c_hi, (int)floorf(t2c + w + mu));
-                    }
-                }
-            }
-            const int clen = vr ? max(0, c_hi - c_lo + 1) : 0;
-            const bool row_self = (rr.j == S.i_loc) && rr.t0 == 0 && rr.t1 == 0;
-            const int incl2 = warp_incl_scan(clen);
-            const int total2 = __shfl_sync(FULL, incl2, 31);
-            const int excl2 = incl2 - clen;
-
-            for (int cb = 0; cb < total2; cb += 32) {
-                const int c = cb + lane;
-                const bool vc = c < total2;
-                const int ow2 = warp_owner(incl2, vc ? c : total2 - 1);
-                const int e2 = __shfl_sync(FULL, excl2, ow2);
-                const int clo = __shfl_sync(FULL, c_lo, ow2);
-                const float cbx = __shfl_sync(FULL, bx, ow2);
-                const float cby = __shfl_sync(FULL, by, ow2);
-                const float cbz = __shfl_sync(FULL, bz, ow2);
-                const bool cself = __shfl_sync(FULL, row_self ? 1 : 0, ow2) != 0;
-                const int t2 = clo + (c - e2);
-                const float ft2 = (float)t2;
-                const float vx = __fmaf_rn(ft2, S.L[6], cbx);
-                const float vy = __fmaf_rn(ft2, S.L[7], cby);
-                const float vz = __fmaf_rn(ft2, S.L[8], cbz);
-                const float d2 = __fmaf_rn(vz, vz, __fmaf_rn(vy, vy, __fmul_rn(vx, vx)));
-                visit(vc, d2, cself && t2 == 0, ow2, t2, rr);
-            }
+        const int excl = incl - cnt;
+        for (int ab = 0; ab < total; ab += 32) {
+            const int q2 = ab + lane;
+            const bool va = q2 < total;
+            const int ow = warp_owner(incl, va ? q2 : total - 1);
+            const int64_t ost = __shfl_sync(FULL, st, ow);
+            const int oex = __shfl_sync(FULL, excl, ow);
+            const int jl = va ? cells.atoms[ost + (q2 - oex)] : 0;
+            visit_targets(S, frac, pos, Rk, rho2p, mu0, jl, va, visit);
         }
     }
 }

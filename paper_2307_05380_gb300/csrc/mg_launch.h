@@ -24,6 +24,11 @@ struct Work {
     double *lpart;            // [N][9] per-atom lattice-gradient partials
     int32_t *sort_tmp;        // [max_edges] scratch for long destination segments
     unsigned int *queue;      // [4] work-queue counters
+    int32_t *bin_cnt;         // [N+B] atoms per cell-list bin
+    int32_t *bin_cursor;      // [N+B] scatter cursors of the bins
+    int64_t *cell_start;      // [N+B+1] first slot of each bin
+    int32_t *cell_atoms;      // [N] local atom index of each slot (bin order)
+    int32_t *atom_bin;        // [N] global bin of each atom (-1: all-pairs structure)
     int64_t max_edges;
 };
 
@@ -38,9 +43,18 @@ struct PrepArgs {
     int knn_k;                 // > 0: KNN graph (starting radius from density)
     float band_rel;
     mg_device_status_t *status;
+    int struct_offset;         // global index of the first structure of this call
 };
 
 cudaError_t launch_prep(const PrepArgs &a, const Work &w, cudaStream_t s);
+
+// Fractional cell list of the structures that use one (after prep): bins counted,
+// scanned and filled.  Batched form: all atoms [0, N) and every bin.  Per-structure
+// form (atom_lo..atom_hi of one structure with host-known first bin and atom row):
+// slots of that structure start at its first atom row.
+cudaError_t launch_bins(int B, int N, const float *frac, const Work &w, cudaStream_t s);
+cudaError_t launch_bins_one(int atom_lo, int atom_hi, int bin_base, const float *frac, const Work &w,
+                            cudaStream_t s);
 
 struct ScanArgs {
     int n;                     // counts

@@ -185,6 +185,50 @@ def test_edge_cases_knn():
         knn_parity(b, k)
 
 
+def cell_list_batch():
+    """Structures large enough for the cell list: a skewed 2-atom cell tiled 6x6x6 with
+    some atoms moved by whole cells (unwrapped coordinates), and a noisy 5x5x5 tiling of
+    a random 8-atom cell."""
+    rng = np.random.default_rng(42)
+    base_L = np.array([[3.1, 0.0, 0.0], [2.2, 2.4, 0.0], [0.4, 0.6, 3.3]])
+    base_x = np.array([[0.1, 0.2, 0.3], [0.6, 0.55, 0.8]])
+    n = 6
+    xs = np.concatenate([(base_x + np.array(c)) / n for c in np.ndindex(n, n, n)])
+    xs[::7] += rng.integers(-2, 3, size=xs[::7].shape)
+    a = synth.Batch((n * base_L)[None], xs, np.array([0, len(xs)], np.int32))
+    b = synth.make_batch(5, B=1)
+    lo = b.atom_ptr[0]
+    m = 5
+    c8 = synth.make_batch(1, B=1)
+    xb = c8.frac[:min(8, len(c8.frac))].astype(np.float64)
+    xt = np.concatenate([(xb + np.array(c)) / m for c in np.ndindex(m, m, m)])
+    xt += rng.normal(0, 0.002, xt.shape)
+    c = synth.Batch((m * c8.lattice[0].astype(np.float64))[None], xt, np.array([0, len(xt)], np.int32))
+    del lo
+    return synth.concat([a, synth.crystal(np.eye(3) * 3.0, [[0.5, 0.5, 0.5]]), c])
+
+
+def test_cell_list_cutoff_and_knn_full_parity():
+    b = cell_list_batch()
+    for r in (2.5, 4.0):
+        cutoff_parity(b, r)
+    for k in (8, 40):
+        knn_parity(b, k)
+
+
+def test_cell_list_per_structure_build_identical():
+    b = cell_list_batch()
+    batch = to_device(b)
+    ref = graph_arrays(mg.cutoff_graph(batch, 4.0))
+    ps = graph_arrays(mg.build_per_structure(batch, "cutoff", cutoff=4.0))
+    for key in ref:
+        np.testing.assert_array_equal(ref[key], ps[key], err_msg=key)
+    kref = graph_arrays(mg.knn_graph(batch, 12))
+    kps = graph_arrays(mg.build_per_structure(batch, "knn", k=12))
+    for key in kref:
+        np.testing.assert_array_equal(kref[key], kps[key], err_msg=key)
+
+
 def test_ragged_sizes_many_tiles():
     """Batches whose atom counts straddle warp and scan-tile boundaries."""
     b = synth.concat([synth.make_batch(3, B=40), synth.make_batch(1, B=5)])
