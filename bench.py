@@ -48,16 +48,16 @@ STAGE_MODEL = {
     ("cutoff", "count"): ("alu", 21.0, "cut"),
     ("knn", "knn"): ("hbm", 36.0, "knn"),
     ("fwd", "fwd"): ("hbm", 36.0, "cut"),
+    ("bwd", "bwd_sym"): ("hbm", 68.0, "cut"),
     ("bwd", "bwd_src"): ("hbm", 36.0, "cut"),
     ("bwd", "bwd_dst"): ("hbm", 24.0, "cut"),
     ("bwd", "bwd_lat"): ("hbm", 0.0, "cut"),
 }
 # Stages that are one kernel launch; the roofline reports the slowest of these (the
-# others bundle several launches: status init + prep, the three scan kernels, the
-# destination sort's histogram / scan / scatter / segment sort).
-SINGLE_KERNEL_STAGES = {("cutoff", "count"), ("cutoff", "write"), ("cutoff", "finalize"), ("knn", "knn"),
-                        ("knn", "pointers"), ("fwd", "fwd"), ("bwd", "bwd_src"), ("bwd", "bwd_dst"),
-                        ("bwd", "bwd_lat")}
+# others bundle several launches: prep, the cell-list binning, the destination sort's
+# histogram / scan / scatter / segment sort).
+SINGLE_KERNEL_STAGES = {("cutoff", "count"), ("cutoff", "write"), ("knn", "knn"), ("fwd", "fwd"),
+                        ("bwd", "bwd_sym"), ("bwd", "bwd_src"), ("bwd", "bwd_dst"), ("bwd", "bwd_lat")}
 
 
 def parse_args():
@@ -222,6 +222,11 @@ def run_mine(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
+    # explicit streams: the legacy default stream cannot be captured into the plans that
+    # mg_update_graph replays; the KNN build runs on a second stream, concurrently
+    main_stream = torch.cuda.Stream(dev)
+    knn_stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(main_stream)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -230,7 +235,9 @@ def run_mine(args, rank, world, local_rank):
     b = synth.make_batch(args.config, seed=synth.BASE_SEED + args.config + 1000 * rank)
     batch = mg.Batch(torch.from_numpy(b.frac).to(dev), torch.from_numpy(b.lattice).to(dev),
                      torch.from_numpy(b.atom_ptr).to(dev), max_atoms=b.max_atoms)
-    g_cut = mg.cutoff_graph(batch, wl["cutoff"])
+    # the cutoff graph is symmetric: its backward needs no destination order, so the
+    # optional perm_dst output is not requested; the KNN graph builds its own
+    g_cut = mg.cutoff_graph(batch, wl["cutoff"], with_perm=False)
     g_knn = mg.knn_graph(batch, wl["k"])
     E_cut, E_knn = g_cut.num_edges, g_knn.num_edges
     units = E_cut + E_knn
@@ -245,16 +252,25 @@ def run_mine(args, rank, world, local_rank):
 
     launches = {"n": 0}
 
+    ev_fork = torch.cuda.Event()
+    ev_join = torch.cuda.Event()
+
     def step():
         n = 0
-        mg.update_graph(g_cut, sync=False)
-        n += mg.last_launch_count(dev)
+        ev_fork.record(main_stream)
+        knn_stream.wait_event(ev_fork)
+        torch.cuda.set_stream(knn_stream)
         mg.update_graph(g_knn, sync=False)
+        n += mg.last_launch_count(dev)
+        torch.cuda.set_stream(main_stream)
+        ev_join.record(knn_stream)
+        mg.update_graph(g_cut, sync=False)
         n += mg.last_launch_count(dev)
         mg.edge_vectors_fwd(g_cut, out_vec=out_vec, out_len=out_len)
         n += mg.last_launch_count(dev)
         mg.edge_vectors_bwd(g_cut, batch, None, grad_len, out_vec, out_len, grad_frac, grad_lat)
         n += mg.last_launch_count(dev)
+        main_stream.wait_event(ev_join)  # the step ends when both builds are done
         launches["n"] += n
 
     for _ in range(max(3, args.warmup)):
@@ -281,9 +297,6 @@ def run_mine(args, rank, world, local_rank):
         ev0[s].record(stream)
         step()
         ev1[s].record(stream)
-        for which in ("cutoff", "knn", "fwd", "bwd"):  # live per-stage CUDA events
-            for name, ms in mg.stage_times(which, dev).items():
-                stage_tot[(which, name)] = stage_tot.get((which, name), 0.0) + ms
     torch.cuda.synchronize(dev)
     t_wall = time.perf_counter() - t_wall
     if world > 1:
@@ -373,17 +386,31 @@ def run_mine(args, rank, world, local_rank):
         per_structure = {"value": units / (ps_step / 1e3), "unit": UNIT, "ms_per_step": ps_step,
                          "speedup_batched": ps_step / (total_ms / args.steps)}
 
+    # Per-kernel timing for the roofline: the same steps with both builds serialized on
+    # one stream (concurrent streams would make stage events overlap other kernels),
+    # CUDA events recorded by the library between its kernels, L2 flushed between steps.
+    n_roof = max(5, min(args.steps, 50))
+    for _ in range(n_roof):
+        flush.zero_()
+        mg.update_graph(g_knn, sync=False)
+        mg.update_graph(g_cut, sync=False)
+        mg.edge_vectors_fwd(g_cut, out_vec=out_vec, out_len=out_len)
+        mg.edge_vectors_bwd(g_cut, batch, None, grad_len, out_vec, out_len, grad_frac, grad_lat)
+        for which in ("cutoff", "knn", "fwd", "bwd"):
+            for name, ms in mg.stage_times(which, dev).items():
+                stage_tot[(which, name)] = stage_tot.get((which, name), 0.0) + ms
+
     clocks = sampler.stop()
 
     # roofline of the dominant stage
     hbm_peak, sm_max, peak_src = measured_peaks()
     fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
-    stages = {f"{k[0]}.{k[1]}": v / args.steps for k, v in stage_tot.items()}
+    stages = {f"{k[0]}.{k[1]}": v / n_roof for k, v in stage_tot.items()}
     singles = {k: v for k, v in stage_tot.items() if k in SINGLE_KERNEL_STAGES and k in STAGE_MODEL}
     dom = max(singles, key=singles.get)
     bound, per_unit, which_units = STAGE_MODEL.get(dom, ("hbm", 36.0, "cut"))
     n_units = E_cut if which_units == "cut" else E_knn
-    t_launch = stage_tot[dom] / args.steps / 1e3
+    t_launch = stage_tot[dom] / n_roof / 1e3
     if bound == "hbm":
         achieved = per_unit * n_units / t_launch / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",

@@ -24,7 +24,27 @@ int num_sms() { return g_num_sms > 0 ? g_num_sms : 152; }
 
 using namespace mg;
 
-// A recorded build: everything a rebuild of the same graph needs.
+// Stage events of one call (measurement support).
+struct Prof {
+    static constexpr int MAX = 16;
+    cudaEvent_t ev[MAX] = {};
+    const char *name[MAX] = {};
+    int n = 0;
+    bool valid = false;
+    bool create() {
+        for (auto &e : ev)
+            if (!e && cudaEventCreate(&e) != cudaSuccess) return false;
+        return true;
+    }
+    void destroy() {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+        *this = Prof();
+    }
+};
+
+// A recorded build: everything a rebuild of the same graph needs.  A captured plan
+// owns its own stage events (they are nodes of its CUDA graph).
 struct Plan {
     int kind = 0;
     float cutoff = 0.f;
@@ -37,22 +57,15 @@ struct Plan {
     size_t ws_bytes = 0;
     cudaGraphExec_t exec = nullptr;
     int launches = 0;
-};
-
-// Stage events of one call kind (measurement support).
-struct Prof {
-    static constexpr int MAX = 16;
-    cudaEvent_t ev[MAX] = {};
-    const char *name[MAX] = {};
-    int n = 0;
-    bool valid = false;
+    Prof prof;
 };
 
 struct mg_context {
     int device = 0;
     int sms = 152;
     bool prof_on = false;
-    Prof prof[4];
+    Prof prof[4];                // events of direct (not replayed) calls, per kind
+    Prof *last_prof[4] = {};     // events of the last call of each kind
     std::mutex mu;
     std::map<const void *, Plan> plans;      // keyed by graph->src
     int tuned[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};  // [kind-1][size class] -> schedule
@@ -63,25 +76,35 @@ namespace {
 
 constexpr size_t ALIGN = 256;
 
-// Stage marks: with profiling on, record the next event of set `which` on the stream.
+// Stage marks: with profiling on, record the next event of `prof` (default: the
+// context's set for `which`) on the stream.
 struct Marker {
     mg_context *ctx;
     int which;
     cudaStream_t st;
-    Marker(mg_context *c, int w, cudaStream_t s) : ctx(c), which(w), st(s) {
+    Prof *pr;
+    Marker(mg_context *c, int w, cudaStream_t s, Prof *p = nullptr) : ctx(c), which(w), st(s), pr(p) {
         if (on()) {
-            ctx->prof[which].n = 0;
-            ctx->prof[which].valid = false;
+            if (!pr) pr = &ctx->prof[which];
+            pr->n = 0;
+            pr->valid = false;
+            ctx->last_prof[which] = pr;
             mark("start");
         }
     }
     bool on() const { return ctx && which >= 0 && ctx->prof_on; }
     void mark(const char *name) {
         if (!on()) return;
-        Prof &p = ctx->prof[which];
+        Prof &p = *pr;
         if (p.n >= Prof::MAX) return;
         if (!p.ev[p.n]) return;
-        cudaEventRecord(p.ev[p.n], st);
+        // inside a capture the record must become a timing node of the graph
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (st) cudaStreamIsCapturing(st, &cs);
+        if (cs == cudaStreamCaptureStatusActive)
+            cudaEventRecordWithFlags(p.ev[p.n], st, cudaEventRecordExternal);
+        else
+            cudaEventRecord(p.ev[p.n], st);
         p.name[p.n] = name;
         ++p.n;
         p.valid = true;
@@ -92,7 +115,7 @@ size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
     size_t recs, pos, atom_struct, cnt, cursor, tile_sum, src_ptr, gpart, lpart, queue, bin_cnt, bin_cursor,
-        cell_start, cell_atoms, atom_bin, sort_tmp, total;
+        cell_start, cell_fx, cell_p, atom_bin, atom_tile, sort_tmp, total;
 };
 
 // Workspace regions, 256-byte aligned; the edge-sized sort scratch comes last so that
@@ -121,8 +144,10 @@ Layout layout(int B, int N, int64_t max_edges) {
     L.bin_cnt = take(sizeof(int32_t) * nbins);
     L.bin_cursor = take(sizeof(int32_t) * nbins);
     L.cell_start = take(sizeof(int64_t) * (nbins + 1));
-    L.cell_atoms = take(sizeof(int32_t) * n);
+    L.cell_fx = take(sizeof(float4) * n);
+    L.cell_p = take(sizeof(float4) * n);
     L.atom_bin = take(sizeof(int32_t) * n);
+    L.atom_tile = take(sizeof(long long) * (n / ATOM_TILE + 2));
     L.sort_tmp = off;
     off += sizeof(int32_t) * (size_t)(max_edges > 0 ? max_edges : 0);
     L.total = align_up(off);
@@ -146,8 +171,10 @@ Work carve(void *ws, int B, int N, int64_t max_edges) {
     w.bin_cnt = reinterpret_cast<int32_t *>(b + L.bin_cnt);
     w.bin_cursor = reinterpret_cast<int32_t *>(b + L.bin_cursor);
     w.cell_start = reinterpret_cast<int64_t *>(b + L.cell_start);
-    w.cell_atoms = reinterpret_cast<int32_t *>(b + L.cell_atoms);
+    w.cell_fx = reinterpret_cast<float4 *>(b + L.cell_fx);
+    w.cell_p = reinterpret_cast<float4 *>(b + L.cell_p);
     w.atom_bin = reinterpret_cast<int32_t *>(b + L.atom_bin);
+    w.atom_tile = reinterpret_cast<long long *>(b + L.atom_tile);
     w.sort_tmp = reinterpret_cast<int32_t *>(b + L.sort_tmp);
     w.max_edges = max_edges;
     return w;
@@ -213,18 +240,18 @@ __global__ void status_init_kernel(mg_device_status_t *st) {
 // The batched build's launch sequence (no host synchronisation).
 mg_status_t enqueue_build(mg_context *ctx, int kind, const mg_batch_t *b, float cutoff, const float *cutoff_ps,
                           int k, const mg_opts_t &o, const mg_graph_t *g, void *ws, size_t ws_bytes,
-                          cudaStream_t st, int *launches) {
+                          cudaStream_t st, int *launches, Prof *prof = nullptr) {
     const int B = b->num_structures, N = b->total_atoms;
     const int64_t me = ws_max_edges(B, N, ws_bytes);
     if (!ws || me < 0) return MG_ERR_WORKSPACE;
     if (g->perm_dst && me < g->capacity) return MG_ERR_WORKSPACE;  // destination sort scratch
     const Work w = carve(ws, B, N, me);
     int n = 0;
-    Marker mk(ctx, kind == MG_KIND_CUTOFF ? MG_PROF_CUTOFF : MG_PROF_KNN, st);
-    status_init_kernel<<<1, 1, 0, st>>>(g->status);
-    ++n;
+    Marker mk(ctx, kind == MG_KIND_CUTOFF ? MG_PROF_CUTOFF : MG_PROF_KNN, st, prof);
+    int64_t *src_ptr = g->src_ptr ? g->src_ptr : w.src_ptr;
+    // prep also resets the status word and, for KNN, writes the k-per-atom pointers
     PrepArgs pa{B, N, b->lattice, b->frac, b->atom_ptr, cutoff, cutoff_ps, kind == MG_KIND_KNN ? k : 0,
-                o.band_rel, g->status, 0};
+                o.band_rel, g->status, 0, kind == MG_KIND_CUTOFF ? 1 : 0, 1, src_ptr, g->edge_ptr};
     if (launch_prep(pa, w, st)) return MG_ERR_CUDA;
     ++n;
     mk.mark("prep");
@@ -234,6 +261,8 @@ mg_status_t enqueue_build(mg_context *ctx, int kind, const mg_batch_t *b, float 
         mk.mark("bin");
     }
     BuildArgs ba;
+    ba.fused_scan = 1;
+    ba.struct_offset = 0;
     ba.B = B;
     ba.N = N;
     ba.frac = b->frac;
@@ -241,35 +270,30 @@ mg_status_t enqueue_build(mg_context *ctx, int kind, const mg_batch_t *b, float 
     ba.schedule = pick_schedule(ctx, kind, b, o);
     ba.collect_stats = o.collect_stats;
     ba.g = *g;
-    ba.src_ptr = g->src_ptr ? g->src_ptr : w.src_ptr;
+    ba.src_ptr = src_ptr;
     ba.knn_k = k;
     ba.band_rel = o.band_rel;
     ba.atom_lo = 0;
     ba.atom_hi = N;
     if (kind == MG_KIND_CUTOFF) {
-        if (launch_cutoff_count(ba, w, st)) return MG_ERR_CUDA;
+        if (launch_cutoff_count(ba, w, st)) return MG_ERR_CUDA;  // also scans its totals
         n += 1 + (ba.schedule == 2);
         mk.mark("count");
-        ScanArgs sa{N, w.cnt, ba.src_ptr};
-        if (launch_scan(sa, w, st)) return MG_ERR_CUDA;
-        n += 3;
-        mk.mark("scan");
-        if (launch_cutoff_finalize(ba, w, st)) return MG_ERR_CUDA;
-        ++n;
-        mk.mark("finalize");
-        if (launch_cutoff_write(ba, w, st)) return MG_ERR_CUDA;
+        if (launch_cutoff_write(ba, w, st)) return MG_ERR_CUDA;  // also writes src_ptr, edge_ptr
         n += 1 + (ba.schedule == 2);
         mk.mark("write");
     } else {
-        if (launch_knn_pointers(ba, w, st)) return MG_ERR_CUDA;
-        ++n;
-        mk.mark("pointers");
         if (launch_knn(ba, w, st)) return MG_ERR_CUDA;
         n += 1 + (ba.schedule == 2);
         mk.mark("knn");
     }
     if (g->perm_dst) {
-        if (launch_dst_sort(ba, w, st, &n)) return MG_ERR_CUDA;
+        if (kind == MG_KIND_CUTOFF) {  // symmetric: destination order from the source order
+            if (launch_dst_perm_symmetric(ba, w, st)) return MG_ERR_CUDA;
+            ++n;
+        } else {
+            if (launch_dst_sort(ba, w, st, &n)) return MG_ERR_CUDA;
+        }
         mk.mark("dst_sort");
     }
     if (launches) *launches = n;
@@ -325,6 +349,9 @@ mg_status_t build_and_record(mg_context *ctx, int kind, const mg_batch_t *b, flo
                       p.ws_bytes == ws_bytes;
     if (!same) {
         if (p.exec) cudaGraphExecDestroy(p.exec);
+        const int which = p.kind == MG_KIND_KNN ? MG_PROF_KNN : MG_PROF_CUTOFF;
+        if (p.kind && ctx->last_prof[which] == &p.prof) ctx->last_prof[which] = nullptr;
+        p.prof.destroy();
         p = Plan();
         p.kind = kind;
         p.cutoff = cutoff;
@@ -388,11 +415,11 @@ mg_status_t mg_create(mg_context_t *ctx, int device) {
 
 mg_status_t mg_destroy(mg_context_t ctx) {
     if (!ctx) return MG_ERR_INVALID_ARGUMENT;
-    for (auto &kv : ctx->plans)
+    for (auto &kv : ctx->plans) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-    for (auto &p : ctx->prof)
-        for (auto &e : p.ev)
-            if (e) cudaEventDestroy(e);
+        kv.second.prof.destroy();
+    }
+    for (auto &p : ctx->prof) p.destroy();
     delete ctx;
     return MG_OK;
 }
@@ -452,11 +479,19 @@ mg_status_t mg_update_graph(mg_context_t ctx, const mg_batch_t *batch, mg_graph_
         ctx->last_launches = n;
         return r;
     }
+    const int which = p.kind == MG_KIND_KNN ? MG_PROF_KNN : MG_PROF_CUTOFF;
     if (!p.exec) {
+        // with profiling on, the plan gets its own stage events (created before capture)
+        Prof *prof = nullptr;
+        if (ctx->prof_on) {
+            if (!p.prof.create()) return MG_ERR_CUDA;
+            prof = &p.prof;
+        }
         cudaGraph_t cg = nullptr;
         if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MG_ERR_CUDA;
         int n = 0;
-        r = enqueue_build(ctx, p.kind, batch, p.cutoff, p.cutoff_ps, p.k, p.opts, graph, ws, ws_bytes, st, &n);
+        r = enqueue_build(ctx, p.kind, batch, p.cutoff, p.cutoff_ps, p.k, p.opts, graph, ws, ws_bytes, st, &n,
+                          prof);
         const cudaError_t ce = cudaStreamEndCapture(st, &cg);
         if (r) {
             if (cg) cudaGraphDestroy(cg);
@@ -473,6 +508,7 @@ mg_status_t mg_update_graph(mg_context_t ctx, const mg_batch_t *batch, mg_graph_
     }
     if (cudaGraphLaunch(p.exec, st) != cudaSuccess) return MG_ERR_CUDA;
     ctx->last_launches = p.launches;
+    if (p.prof.valid) ctx->last_prof[which] = &p.prof;  // the replay re-records the plan's events
     return MG_OK;
 }
 
@@ -523,7 +559,7 @@ mg_status_t mg_build_per_structure(mg_context_t ctx, const mg_batch_t *b, int32_
         Work w = w0;
         w.recs = w0.recs + s;  // the structure's record sits at local index 0
         PrepArgs pa{1, hi - lo, b->lattice + 9 * (size_t)s, b->frac, b->atom_ptr + s, cutoff, nullptr,
-                    kind == MG_KIND_KNN ? k : 0, o.band_rel, g->status, s};
+                    kind == MG_KIND_KNN ? k : 0, o.band_rel, g->status, s, 0, 0, nullptr, nullptr};
         if (launch_prep(pa, w, st)) return MG_ERR_CUDA;
         ++n;
         if (hi - lo >= CELL_MIN_ATOMS) {  // this structure may use a cell list
@@ -531,6 +567,8 @@ mg_status_t mg_build_per_structure(mg_context_t ctx, const mg_batch_t *b, int32_
             n += 7;
         }
         BuildArgs ba;
+        ba.fused_scan = 0;
+        ba.struct_offset = s;
         ba.B = B;
         ba.N = N;
         ba.frac = b->frac;
@@ -564,6 +602,8 @@ mg_status_t mg_build_per_structure(mg_context_t ctx, const mg_batch_t *b, int32_
         }
     }
     BuildArgs fa;
+    fa.fused_scan = 0;
+    fa.struct_offset = 0;
     fa.B = B;
     fa.N = N;
     fa.frac = b->frac;
@@ -583,7 +623,12 @@ mg_status_t mg_build_per_structure(mg_context_t ctx, const mg_batch_t *b, int32_
     per_structure_final_kernel<<<1, 1, 0, st>>>(B, N, g->edge_ptr, g->capacity, g->status);
     ++n;
     if (g->perm_dst) {
-        if (launch_dst_sort(fa, w0, st, &n)) return MG_ERR_CUDA;
+        if (kind == MG_KIND_CUTOFF) {
+            if (launch_dst_perm_symmetric(fa, w0, st)) return MG_ERR_CUDA;
+            ++n;
+        } else {
+            if (launch_dst_sort(fa, w0, st, &n)) return MG_ERR_CUDA;
+        }
     }
     if (cudaGetLastError() != cudaSuccess) return MG_ERR_CUDA;
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -620,10 +665,19 @@ mg_status_t mg_edge_vectors_bwd(mg_context_t ctx, const mg_batch_t *b, const mg_
     if (!ctx) return MG_ERR_INVALID_ARGUMENT;
     mg_status_t r = check_batch(b);
     if (r) return r;
-    if (!g || !g->src_ptr || !g->edge_ptr || !g->dst || !g->offset || !g->perm_dst || !g->dst_ptr || !grad_frac ||
-        !grad_lattice)
+    if (!g || !g->src_ptr || !g->edge_ptr || !g->dst || !g->offset || !grad_frac || !grad_lattice)
         return MG_ERR_INVALID_ARGUMENT;
     if (grad_len && (!vec || !len)) return MG_ERR_INVALID_ARGUMENT;
+    // A cutoff graph built on this context is symmetric: its in-edges are found as the
+    // reverses of out-edges and no destination order is needed.  Other graphs need one.
+    bool symmetric = false;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto it = ctx->plans.find((const void *)g->src);
+        symmetric = it != ctx->plans.end() && it->second.kind == MG_KIND_CUTOFF && it->second.cutoff_ps == nullptr &&
+                    same_graph(it->second.graph, *g);
+    }
+    if (!symmetric && (!g->perm_dst || !g->dst_ptr)) return MG_ERR_INVALID_ARGUMENT;
     const int B = b->num_structures, N = b->total_atoms;
     const int64_t me = ws_max_edges(B, N, ws_bytes);
     if (!ws || me < 0) return MG_ERR_WORKSPACE;
@@ -643,13 +697,20 @@ mg_status_t mg_edge_vectors_bwd(mg_context_t ctx, const mg_batch_t *b, const mg_
     a.grad_lattice = grad_lattice;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Marker mk(ctx, MG_PROF_BWD, st);
-    if (launch_bwd_src(a, w, st)) return MG_ERR_CUDA;
-    mk.mark("bwd_src");
-    if (launch_bwd_dst(a, w, st)) return MG_ERR_CUDA;
-    mk.mark("bwd_dst");
+    int n = 0;
+    if (symmetric) {
+        if (launch_bwd_sym(a, w, st)) return MG_ERR_CUDA;
+        mk.mark("bwd_sym");
+        n = 2;
+    } else {
+        if (launch_bwd_src(a, w, st)) return MG_ERR_CUDA;
+        mk.mark("bwd_src");
+        if (launch_bwd_dst(a, w, st)) return MG_ERR_CUDA;
+        mk.mark("bwd_dst");
+        n = 3;
+    }
     if (launch_bwd_lat(a, w, st)) return MG_ERR_CUDA;
     mk.mark("bwd_lat");
-    const int n = 3;
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->last_launches = n;
     return MG_OK;
@@ -733,7 +794,9 @@ mg_status_t mg_profile_enable(mg_context_t ctx, int32_t on) {
 
 int32_t mg_stage_times(mg_context_t ctx, int32_t which, int32_t max_stages, const char **names, float *ms) {
     if (!ctx || which < 0 || which > 3) return -1;
-    Prof &p = ctx->prof[which];
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->last_prof[which]) return -1;
+    const Prof &p = *ctx->last_prof[which];
     if (!p.valid || p.n < 2) return -1;
     if (cudaEventSynchronize(p.ev[p.n - 1]) != cudaSuccess) return -1;
     const int stages = p.n - 1;

@@ -183,6 +183,83 @@ __global__ void __launch_bounds__(256) bwd_lat_kernel(EdgeVecArgs a, const doubl
     }
 }
 
+// First position in [lo, hi) of the sorted keys with key >= v (or > v when upper).
+__device__ __forceinline__ int64_t key_bound(const int32_t *__restrict__ keys, int64_t lo, int64_t hi, int v,
+                                             bool upper) {
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const int k = keys[mid];
+        if (k < v || (upper && k == v)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Backward of a symmetric (cutoff) graph in one pass over source segments: the in-edge
+// of j matching out-edge p = (j, i, t) is its reverse (i, j, -t), which sits in i's
+// segment at s_ij + (rhi - 1 - p) (the run of i's edges to j holds the reversed run in
+// the opposite offset order; s_ij its start, [rlo, rhi) the run of p in j's segment).
+// grad_frac[j] = sum_p (g_rev(p) - g_p) L^T; the lattice partial sums (x_i - x_j + t)^T g_p.
+// Fixed per-lane order and a fixed warp reduction: deterministic, no destination order.
+__global__ void __launch_bounds__(256) bwd_sym_kernel(EdgeVecArgs a, double *__restrict__ lpart) {
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = lane_id();
+    if (j >= a.N) return;
+    const int64_t E = a.g.edge_ptr[a.B];
+    const int64_t lo = a.g.src_ptr[j], hi = (E > a.g.capacity) ? lo : a.g.src_ptr[j + 1];
+    const float xj[3] = {a.frac[3 * (int64_t)j], a.frac[3 * (int64_t)j + 1], a.frac[3 * (int64_t)j + 2]};
+    float acc[3] = {0.f, 0.f, 0.f};
+    float M[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) M[q] = 0.f;
+    for (int64_t p = lo + lane; p < hi; p += 32) {
+        const float3 g = edge_g(a, p);
+        const int i = a.g.dst[p];
+        const int64_t rhi = key_bound(a.g.dst, p, hi, i, true);  // end of p's run
+        const int64_t sij = key_bound(a.g.dst, a.g.src_ptr[i], a.g.src_ptr[i + 1], j, false);
+        const float3 gr = edge_g(a, sij + (rhi - 1 - p));
+        acc[0] += gr.x - g.x;
+        acc[1] += gr.y - g.y;
+        acc[2] += gr.z - g.z;
+        const int t[3] = {a.g.offset[3 * p], a.g.offset[3 * p + 1], a.g.offset[3 * p + 2]};
+        const float xi[3] = {a.frac[3 * (int64_t)i], a.frac[3 * (int64_t)i + 1], a.frac[3 * (int64_t)i + 2]};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float s1, e1, s2, e2;
+            two_sum(xi[k], -xj[k], s1, e1);
+            two_sum(s1, (float)t[k], s2, e2);
+            const float df = __fadd_rn(s2, __fadd_rn(e2, e1));
+            M[3 * k + 0] = __fmaf_rn(df, g.x, M[3 * k + 0]);
+            M[3 * k + 1] = __fmaf_rn(df, g.y, M[3 * k + 1]);
+            M[3 * k + 2] = __fmaf_rn(df, g.z, M[3 * k + 2]);
+        }
+    }
+    double r[12];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) r[q] = warp_sum_d((double)acc[q]);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) r[3 + q] = warp_sum_d((double)M[q]);
+    if (lane < 3) {
+        const int s = structure_of(a.atom_ptr, a.B, j);
+        const float *L = a.lattice + 9 * (int64_t)s;
+        // (g L^T)_k = sum_c g_c L[k][c]
+        const double h = r[0] * (double)L[3 * lane + 0] + r[1] * (double)L[3 * lane + 1] + r[2] * (double)L[3 * lane + 2];
+        a.grad_frac[3 * (int64_t)j + lane] = (float)h;
+    }
+    if (lane < 9) {
+        double v = r[3];
+#pragma unroll
+        for (int q = 1; q < 9; ++q)
+            if (lane == q) v = r[3 + q];
+        lpart[9 * (int64_t)j + lane] = v;
+    }
+}
+
+cudaError_t launch_bwd_sym(const EdgeVecArgs &a, const Work &w, cudaStream_t s) {
+    if (a.N > 0) bwd_sym_kernel<<<(a.N + 7) / 8, 256, 0, s>>>(a, w.lpart);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bwd_src(const EdgeVecArgs &a, const Work &w, cudaStream_t s) {
     if (a.N > 0) bwd_src_kernel<<<(a.N + 7) / 8, 256, 0, s>>>(a, w.gpart, w.lpart);
     return cudaGetLastError();

@@ -19,11 +19,45 @@ namespace mg {
 
 __global__ void __launch_bounds__(128) prep_kernel(PrepArgs a, StructRec *__restrict__ recs,
                                                     float4 *__restrict__ pos,
-                                                    int32_t *__restrict__ atom_struct) {
+                                                    int32_t *__restrict__ atom_struct,
+                                                    long long *__restrict__ atom_tile,
+                                                    unsigned int *__restrict__ queue) {
+    if (a.zero_tiles) {  // the fused count scan accumulates into these
+        const int ntiles = (a.N + ATOM_TILE - 1) / ATOM_TILE + 1;
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x)
+            atom_tile[t] = 0;
+        if (blockIdx.x == 0 && threadIdx.x == 0) queue[2] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (a.init_status || (a.knn_k > 0 && a.edge_ptr))) {
+        // nothing else writes the status word before the kernels that follow prep
+        Status *st = reinterpret_cast<Status *>(a.status);
+        if (a.init_status) {
+            st->code = 0;
+            st->first_bad_structure = 0x7fffffff;
+            st->rechecked = 0;
+            st->candidates = 0;
+            st->num_edges = 0;
+            st->required_capacity = 0;
+        }
+        if (a.knn_k > 0 && a.edge_ptr) {  // exactly k edges per atom
+            st->num_edges = (unsigned long long)a.N * a.knn_k;
+            st->required_capacity = (unsigned long long)a.N * a.knn_k;
+        }
+    }
     const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = lane_id();
     if (s >= a.B) return;
     const int begin = a.atom_ptr[s], end = a.atom_ptr[s + 1];
+    if (a.knn_k > 0 && a.edge_ptr) {  // KNN pointers: k edges per atom
+        for (int r = begin + lane; r < end; r += 32) a.src_ptr[r] = (int64_t)r * a.knn_k;
+        if (lane == 0) {
+            a.edge_ptr[s] = (int64_t)begin * a.knn_k;
+            if (s == a.B - 1) {
+                a.edge_ptr[a.B] = (int64_t)a.N * a.knn_k;
+                a.src_ptr[a.N] = (int64_t)a.N * a.knn_k;
+            }
+        }
+    }
     float Lf[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) Lf[q] = a.lattice[9 * (int64_t)s + q];
@@ -146,15 +180,14 @@ __global__ void __launch_bounds__(128) prep_kernel(PrepArgs a, StructRec *__rest
         if (visited < 0.5)
             for (int k = 0; k < 3; ++k) R.nb[k] = nk[k];
     }
-    recs[s] = R;
-    if (bad) set_error(a.status, bad, s);
+    recs[s] = R;  // a bad structure is reported by the kernel that scans its first atom
 }
 
 cudaError_t launch_prep(const PrepArgs &a, const Work &w, cudaStream_t s) {
     if (a.B <= 0) return cudaSuccess;
     const int threads = 128;
     const int blocks = (a.B * 32 + threads - 1) / threads;
-    prep_kernel<<<blocks, threads, 0, s>>>(a, w.recs, w.pos, w.atom_struct);
+    prep_kernel<<<blocks, threads, 0, s>>>(a, w.recs, w.pos, w.atom_struct, w.atom_tile, w.queue);
     return cudaGetLastError();
 }
 
@@ -277,12 +310,16 @@ __global__ void bin_assign_kernel(int atom_lo, int atom_hi, const int32_t *__res
 __global__ void bin_scatter_kernel(int atom_lo, int atom_hi, const int32_t *__restrict__ atom_struct,
                                    const StructRec *__restrict__ recs, const int32_t *__restrict__ atom_bin,
                                    const int64_t *__restrict__ cell_start, int32_t *__restrict__ cursor,
-                                   int32_t *__restrict__ cell_atoms) {
+                                   const float *__restrict__ frac, const float4 *__restrict__ pos,
+                                   float4 *__restrict__ cell_fx, float4 *__restrict__ cell_p) {
     for (int r = atom_lo + blockIdx.x * blockDim.x + threadIdx.x; r < atom_hi; r += gridDim.x * blockDim.x) {
         const int g = atom_bin[r];
         if (g < 0) continue;
         const int64_t slot = cell_start[g] + atomicAdd(&cursor[g], 1);
-        cell_atoms[slot] = r - recs[atom_struct[r]].atom_begin;
+        const int jl = r - recs[atom_struct[r]].atom_begin;
+        cell_fx[slot] = make_float4(frac[3 * (int64_t)r], frac[3 * (int64_t)r + 1], frac[3 * (int64_t)r + 2],
+                                    __int_as_float(jl));
+        cell_p[slot] = pos[r];
     }
 }
 
@@ -300,7 +337,7 @@ cudaError_t launch_bins(int B, int N, const float *frac, const Work &w, cudaStre
     cudaError_t e = launch_scan(sa, w, s);
     if (e) return e;
     bin_scatter_kernel<<<grid, 256, 0, s>>>(0, N, w.atom_struct, w.recs, w.atom_bin, w.cell_start, w.bin_cursor,
-                                            w.cell_atoms);
+                                            frac, w.pos, w.cell_fx, w.cell_p);
     return cudaGetLastError();
 }
 
@@ -318,7 +355,7 @@ cudaError_t launch_bins_one(int atom_lo, int atom_hi, int bin_base, const float 
     add_const_kernel<<<max(1, min(64, (nbins + 255) / 256)), 256, 0, s>>>(w.cell_start + bin_base, nbins,
                                                                         (int64_t)atom_lo);
     bin_scatter_kernel<<<grid, 256, 0, s>>>(atom_lo, atom_hi, w.atom_struct, w.recs, w.atom_bin, w.cell_start,
-                                            w.bin_cursor, w.cell_atoms);
+                                            w.bin_cursor, frac, w.pos, w.cell_fx, w.cell_p);
     return cudaGetLastError();
 }
 
@@ -356,7 +393,10 @@ __global__ void __launch_bounds__(256) cutoff_count_kernel(BuildArgs a, Work w) 
         const int s = w.atom_struct[i];
         const StructRec &R = w.recs[s];
         if (R.bad) {
-            if (lane_id() == 0) w.cnt[i] = 0;
+            if (lane_id() == 0) {
+                w.cnt[i] = 0;
+                if (i == R.atom_begin) set_error(a.g.status, R.bad, s + a.struct_offset);
+            }
             continue;
         }
         Source S;
@@ -364,7 +404,7 @@ __global__ void __launch_bounds__(256) cutoff_count_kernel(BuildArgs a, Work w) 
         const float thr_lo = R.thr_lo, thr_hi = R.thr_hi;
         const double rr = R.rr;
         int count = 0;
-        const Cells cells{w.cell_start, w.cell_atoms};
+        const Cells cells{w.cell_start, w.cell_fx, w.cell_p};
         for_each_candidate(S, a.frac, w.pos, cells, true, R.cut, [&](bool vc, float d2, bool self, int ow, int t2,
                                                                       const RowRegs &rw) {
             const bool cand = vc && !self;
@@ -385,7 +425,48 @@ __global__ void __launch_bounds__(256) cutoff_count_kernel(BuildArgs a, Work w) 
             count += __popc(__ballot_sync(FULL, in));
             ncand += __popc(__ballot_sync(FULL, cand));
         });
-        if (lane_id() == 0) w.cnt[i] = count;
+        if (lane_id() == 0) {
+            w.cnt[i] = count;
+            if (a.fused_scan && count)
+                atomicAdd(reinterpret_cast<unsigned long long *>(&w.atom_tile[i / ATOM_TILE]),
+                          (unsigned long long)count);
+        }
+    }
+    if (a.fused_scan) {
+        // The last block to finish turns the tile totals into tile offsets (integer
+        // atomics, so the result does not depend on the order blocks finish in).
+        __shared__ unsigned int s_ticket;
+        __shared__ long long sm[64];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            s_ticket = atomicAdd(&w.queue[2], 1u);
+        }
+        __syncthreads();
+        if (s_ticket == gridDim.x - 1) {
+            __threadfence();
+            const int ntiles = (a.N + ATOM_TILE - 1) / ATOM_TILE;
+            long long carry = 0;
+            for (int b0 = 0; b0 < ntiles; b0 += 256) {
+                const int q = b0 + threadIdx.x;
+                const long long v = q < ntiles ? __ldcg(&w.atom_tile[q]) : 0;
+                long long tot;
+                const long long ex = block_excl_scan_ll(v, sm, tot);
+                if (q < ntiles) w.atom_tile[q] = carry + ex;
+                carry += tot;
+            }
+            if (threadIdx.x == 0) {
+                w.atom_tile[ntiles] = carry;
+                Status *st = reinterpret_cast<Status *>(a.g.status);
+                st->num_edges = (unsigned long long)carry;
+                st->required_capacity = (unsigned long long)carry;
+                if (carry > a.g.capacity) set_error(a.g.status, MG_ERR_CAPACITY, -1);
+                a.src_ptr[a.N] = carry;
+                a.g.edge_ptr[a.B] = carry;
+                for (int s = a.B - 1; s >= 0 && a.atom_ptr[s] == a.N; --s) a.g.edge_ptr[s] = carry;
+                w.queue[2] = 0;
+            }
+        }
     }
     if (a.collect_stats && lane_id() == 0 && ncand) {
         Status *st = reinterpret_cast<Status *>(a.g.status);
@@ -489,13 +570,28 @@ __global__ void __launch_bounds__(WRITE_WARPS * 32) cutoff_write_kernel(BuildArg
     unsigned long long *keys = keys_all[threadIdx.x >> 5];
     AtomLoop<SCHED> loop{a.atom_lo, a.atom_hi, w.queue};
     const mg_graph_t g = a.g;
-    const Cells cells{w.cell_start, w.cell_atoms};
+    const Cells cells{w.cell_start, w.cell_fx, w.cell_p};
     const unsigned lt = (1u << lane_id()) - 1u;
     for (int i = loop.first(); i < a.atom_hi; i = loop.next()) {
-        const int64_t base = a.src_ptr[i];
-        const int64_t endp = a.src_ptr[i + 1];
-        if (endp > g.capacity || endp == base) continue;  // capacity error already reported
         const int s = w.atom_struct[i];
+        int64_t base, endp;
+        if (a.fused_scan) {
+            // src_ptr[i] = offset of i's tile + counts of the tile's earlier atoms
+            const int t0 = (i / ATOM_TILE) * ATOM_TILE;
+            long long pre = 0;
+            for (int q = t0 + lane_id(); q < i; q += 32) pre += w.cnt[q];
+            pre = warp_sum(pre);
+            base = w.atom_tile[i / ATOM_TILE] + pre;
+            endp = base + w.cnt[i];
+            if (lane_id() == 0) {
+                a.src_ptr[i] = base;
+                for (int q = s; q >= 0 && a.atom_ptr[q] == i; --q) g.edge_ptr[q] = base;  // structures starting at i
+            }
+        } else {
+            base = a.src_ptr[i];
+            endp = a.src_ptr[i + 1];
+        }
+        if (endp > g.capacity || endp == base) continue;  // capacity error already reported
         const StructRec &R = w.recs[s];
         if (R.bad) continue;
         Source S;
@@ -685,6 +781,60 @@ __global__ void __launch_bounds__(128) dst_segsort_kernel(int N, const int64_t *
         for (int64_t r = lo; r < hi; ++r) rank += tmp[r] < v;
         perm[lo + rank] = v;
     }
+}
+
+// First position in [lo, hi) of sorted keys with key >= v (or > v when upper).
+__device__ __forceinline__ int64_t bound32(const int32_t *__restrict__ keys, int64_t lo, int64_t hi, int v,
+                                           bool upper) {
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const int k = keys[mid];
+        if (k < v || (upper && k == v)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Destination order of a symmetric graph ((i, j, t) present iff (j, i, -t) is, as for a
+// cutoff graph: the canonical distance is sign-symmetric).  j's in-edges are the
+// reverses of its out-edges, so dst_ptr = src_ptr, and for the run of j's out-edges to
+// atom i (positions [rlo, rhi), offsets ascending) the reversed edges (i, j, -t) form
+// the run of i's out-edges to j in the opposite order: out-edge p of the run maps to
+// edge s_ij + (rhi - 1 - p) and to in-list position rlo + (rhi - 1 - p).
+__global__ void __launch_bounds__(256) dst_perm_symmetric_kernel(int N, const int64_t *__restrict__ src_ptr,
+                                                                 const int32_t *__restrict__ dst,
+                                                                 const int64_t *__restrict__ E_dev, int64_t capacity,
+                                                                 int32_t *__restrict__ perm,
+                                                                 int64_t *__restrict__ dst_ptr,
+                                                                 mg_device_status_t *status) {
+    if (*E_dev > capacity) return;
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= N) return;
+    const int64_t lo = src_ptr[j], hi = src_ptr[j + 1];
+    if (lane_id() == 0) {
+        dst_ptr[j] = lo;
+        if (j == N - 1) dst_ptr[N] = hi;
+    }
+    for (int64_t p = lo + lane_id(); p < hi; p += 32) {
+        const int i = dst[p];
+        const int64_t rlo = bound32(dst, lo, hi, i, false);
+        const int64_t rhi = bound32(dst, lo, hi, i, true);
+        const int64_t ilo = src_ptr[i], ihi = src_ptr[i + 1];
+        const int64_t sij = bound32(dst, ilo, ihi, j, false);
+        if (p == rlo) {  // the reverse run must have the same length
+            const int64_t len = rhi - rlo;
+            const bool ok = sij + len <= ihi && dst[sij + len - 1] == j && (sij + len == ihi || dst[sij + len] != j);
+            if (!ok) set_error(status, MG_ERR_INTERNAL, -1);
+        }
+        perm[rlo + (rhi - 1 - p)] = (int32_t)(sij + (rhi - 1 - p));
+    }
+}
+
+cudaError_t launch_dst_perm_symmetric(const BuildArgs &a, const Work &, cudaStream_t s) {
+    if (a.N <= 0) return cudaSuccess;
+    dst_perm_symmetric_kernel<<<(a.N + 7) / 8, 256, 0, s>>>(a.N, a.src_ptr, a.g.dst, a.g.edge_ptr + a.B, a.g.capacity,
+                                                          a.g.perm_dst, a.g.dst_ptr, a.g.status);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_dst_sort(const BuildArgs &a, const Work &w, cudaStream_t s, int *launches) {

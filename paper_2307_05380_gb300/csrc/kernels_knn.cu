@@ -142,13 +142,16 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_kernel(BuildArgs a, Work w
     const unsigned lt = (1u << lane) - 1u;
     const mg_graph_t g = a.g;
     KnnLoop<SCHED> loop{a.atom_lo, a.atom_hi, w.queue};
-    const Cells cells{w.cell_start, w.cell_atoms};
+    const Cells cells{w.cell_start, w.cell_fx, w.cell_p};
     unsigned long long nre = 0, ncand = 0;
 
     for (int i = loop.first(); i < a.atom_hi; i = loop.next()) {
         const int s = w.atom_struct[i];
         const StructRec &R = w.recs[s];
-        if (R.bad) continue;
+        if (R.bad) {
+            if (lane == 0 && i == R.atom_begin) set_error(g.status, R.bad, s + a.struct_offset);
+            continue;
+        }
         Source Src;
         load_source(Src, w.recs, s, a.frac, w.pos, i);
 

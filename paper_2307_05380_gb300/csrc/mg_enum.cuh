@@ -64,7 +64,8 @@ __device__ __forceinline__ void load_source(Source &S, const StructRec *__restri
 // Cell list of the batch (device pointers in the workspace).
 struct Cells {
     const int64_t *__restrict__ start;   // [bins + 1] first slot of each bin (global)
-    const int32_t *__restrict__ atoms;   // [slots] local atom index of each slot
+    const float4 *__restrict__ fx;       // [slots] fractional coordinates, .w = local index bits
+    const float4 *__restrict__ p;        // [slots] FP32 Cartesian positions
 };
 
 // Row-level values a visitor may fetch from the row's owner lane (shuffle source ow).
@@ -84,18 +85,19 @@ __device__ __forceinline__ int bin_of(float w, int n) {
     return min(max((int)floorf(__fmul_rn(w, (float)n)), 0), n - 1);
 }
 
-// Levels 2 and 3 for the 32 target atoms held by the lanes (jl valid where vj).
+// Levels 2 and 3 for the 32 target atoms held by the lanes (jl valid where vj; xj the
+// target's fractional coordinates, pj its FP32 Cartesian position).  With `single`
+// (reach below half a cell on every axis) a target has at most one image in reach, so
+// each lane tests its own candidate directly and the flattening levels are skipped.
 template <class Visit>
-__device__ __forceinline__ void visit_targets(const Source &S, const float *__restrict__ frac,
-                                              const float4 *__restrict__ pos, const float Rk[3],
-                                              float rho2p, float mu0, int jl, bool vj, Visit &visit) {
+__device__ __forceinline__ void visit_targets(const Source &S, const float Rk[3], float rho2p, float mu0,
+                                              bool single, int jl, bool vj, float4 xj, float4 pj,
+                                              Visit &visit) {
     const int lane = lane_id();
     int lo[3], nn[3];
     float3 a = make_float3(0.f, 0.f, 0.f);
     if (vj) {
-        const int64_t row = (int64_t)S.begin + jl;
-        const float dx[3] = {__fsub_rn(frac[3 * row + 0], S.xi0), __fsub_rn(frac[3 * row + 1], S.xi1),
-                             __fsub_rn(frac[3 * row + 2], S.xi2)};
+        const float dx[3] = {__fsub_rn(xj.x, S.xi0), __fsub_rn(xj.y, S.xi1), __fsub_rn(xj.z, S.xi2)};
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const float m = 1e-5f * (1.0f + fabsf(dx[k]) + Rk[k]);
@@ -103,7 +105,6 @@ __device__ __forceinline__ void visit_targets(const Source &S, const float *__re
             const int hi = (int)floorf(Rk[k] - dx[k] + m);
             nn[k] = max(0, hi - lo[k] + 1);
         }
-        const float4 pj = pos[row];
         a = make_float3(__fsub_rn(pj.x, S.pi.x), __fsub_rn(pj.y, S.pi.y), __fsub_rn(pj.z, S.pi.z));
     } else {
 #pragma unroll
@@ -111,6 +112,25 @@ __device__ __forceinline__ void visit_targets(const Source &S, const float *__re
             lo[k] = 0;
             nn[k] = 0;
         }
+    }
+    if (single) {
+        // same operation order as the general path: b = a + t0 L0 + t1 L1, v = b + t2 L2
+        const bool has = vj && nn[0] > 0 && nn[1] > 0 && nn[2] > 0;
+        const float ft0 = (float)lo[0], ft1 = (float)lo[1], ft2 = (float)lo[2];
+        const float bx = __fmaf_rn(ft1, S.L[3], __fmaf_rn(ft0, S.L[0], a.x));
+        const float by = __fmaf_rn(ft1, S.L[4], __fmaf_rn(ft0, S.L[1], a.y));
+        const float bz = __fmaf_rn(ft1, S.L[5], __fmaf_rn(ft0, S.L[2], a.z));
+        const float vx = __fmaf_rn(ft2, S.L[6], bx);
+        const float vy = __fmaf_rn(ft2, S.L[7], by);
+        const float vz = __fmaf_rn(ft2, S.L[8], bz);
+        const float d2 = __fmaf_rn(vz, vz, __fmaf_rn(vy, vy, __fmul_rn(vx, vx)));
+        RowRegs rr;
+        rr.j = jl;
+        rr.t0 = lo[0];
+        rr.t1 = lo[1];
+        const bool self = jl == S.i_loc && lo[0] == 0 && lo[1] == 0 && lo[2] == 0;
+        visit(has, d2, self, lane, lo[2], rr);
+        return;
     }
     const int rows = (nn[2] > 0) ? nn[0] * nn[1] : 0;
     const int incl = warp_incl_scan(rows);
@@ -209,11 +229,19 @@ __device__ __forceinline__ void for_each_candidate(const Source &S, const float 
     for (int k = 0; k < 3; ++k) Rk[k] = rho * S.invd[k];
     const float rho2p = rho * rho * 1.0002f;
     const float mu0 = 1e-3f * (1.0f + rho / S.L2norm);
+    const bool single = fmaxf(Rk[0], fmaxf(Rk[1], Rk[2])) < 0.49f;
 
     if (!use_cells || S.nb[0] == 0) {
         for (int jb = 0; jb < S.n; jb += 32) {
             const int jl = jb + lane;
-            visit_targets(S, frac, pos, Rk, rho2p, mu0, jl, jl < S.n, visit);
+            const bool vj = jl < S.n;
+            float4 xj = make_float4(0.f, 0.f, 0.f, 0.f), pj = xj;
+            if (vj) {
+                const int64_t row = (int64_t)S.begin + jl;
+                xj = make_float4(frac[3 * row + 0], frac[3 * row + 1], frac[3 * row + 2], 0.f);
+                pj = pos[row];
+            }
+            visit_targets(S, Rk, rho2p, mu0, single, jl, vj, xj, pj, visit);
         }
         return;
     }
@@ -262,8 +290,12 @@ __device__ __forceinline__ void for_each_candidate(const Source &S, const float 
             const int ow = warp_owner(incl, va ? q2 : total - 1);
             const int64_t ost = __shfl_sync(FULL, st, ow);
             const int oex = __shfl_sync(FULL, excl, ow);
-            const int jl = va ? cells.atoms[ost + (q2 - oex)] : 0;
-            visit_targets(S, frac, pos, Rk, rho2p, mu0, jl, va, visit);
+            float4 xj = make_float4(0.f, 0.f, 0.f, 0.f), pj = xj;
+            if (va) {
+                xj = cells.fx[ost + (q2 - oex)];
+                pj = cells.p[ost + (q2 - oex)];
+            }
+            visit_targets(S, Rk, rho2p, mu0, single, va ? __float_as_int(xj.w) : 0, va, xj, pj, visit);
         }
     }
 }

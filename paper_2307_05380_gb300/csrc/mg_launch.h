@@ -27,12 +27,15 @@ struct Work {
     int32_t *bin_cnt;         // [N+B] atoms per cell-list bin
     int32_t *bin_cursor;      // [N+B] scatter cursors of the bins
     int64_t *cell_start;      // [N+B+1] first slot of each bin
-    int32_t *cell_atoms;      // [N] local atom index of each slot (bin order)
+    float4 *cell_fx;          // [N] fractional coordinates of each slot, .w = local index bits
+    float4 *cell_p;           // [N] FP32 Cartesian position of each slot (bin order)
     int32_t *atom_bin;        // [N] global bin of each atom (-1: all-pairs structure)
+    long long *atom_tile;     // [N/ATOM_TILE + 2] edges per tile of atoms, then tile offsets
     int64_t max_edges;
 };
 
 constexpr int SCAN_TILE = 4096;
+constexpr int ATOM_TILE = 256;   // atoms per tile of the fused count scan
 
 struct PrepArgs {
     int B, N;
@@ -44,6 +47,10 @@ struct PrepArgs {
     float band_rel;
     mg_device_status_t *status;
     int struct_offset;         // global index of the first structure of this call
+    int zero_tiles;            // 1: clear the fused count scan's tile sums and counter
+    int init_status;           // 1: reset the status word (first kernel of a build)
+    int64_t *src_ptr;          // KNN: written here (k per atom); may be NULL otherwise
+    int64_t *edge_ptr;         // KNN: written here
 };
 
 cudaError_t launch_prep(const PrepArgs &a, const Work &w, cudaStream_t s);
@@ -74,6 +81,9 @@ struct BuildArgs {
     int knn_k;
     float band_rel;
     int atom_lo, atom_hi;      // atom row range to process (per-structure builds)
+    int fused_scan;            // 1: count kernel scans its own totals, write kernel derives
+                               //    src_ptr/edge_ptr (batched builds); 0: separate scan kernels
+    int struct_offset;         // global index of local structure 0 (per-structure builds)
 };
 
 cudaError_t launch_cutoff_count(const BuildArgs &a, const Work &w, cudaStream_t s);
@@ -83,6 +93,8 @@ cudaError_t launch_cutoff_write(const BuildArgs &a, const Work &w, cudaStream_t 
 cudaError_t launch_knn(const BuildArgs &a, const Work &w, cudaStream_t s);
 cudaError_t launch_knn_pointers(const BuildArgs &a, const Work &w, cudaStream_t s);
 cudaError_t launch_dst_sort(const BuildArgs &a, const Work &w, cudaStream_t s, int *launches);
+// Destination order of a symmetric (cutoff) graph from its source order, one kernel.
+cudaError_t launch_dst_perm_symmetric(const BuildArgs &a, const Work &w, cudaStream_t s);
 cudaError_t launch_reset_queue(const Work &w, cudaStream_t s);
 
 struct EdgeVecArgs {
@@ -95,6 +107,7 @@ struct EdgeVecArgs {
     float *grad_frac, *grad_lattice;
 };
 cudaError_t launch_edgevec_fwd(const EdgeVecArgs &a, cudaStream_t s);
+cudaError_t launch_bwd_sym(const EdgeVecArgs &a, const Work &w, cudaStream_t s);  // symmetric graphs
 cudaError_t launch_bwd_src(const EdgeVecArgs &a, const Work &w, cudaStream_t s);
 cudaError_t launch_bwd_dst(const EdgeVecArgs &a, const Work &w, cudaStream_t s);
 cudaError_t launch_bwd_lat(const EdgeVecArgs &a, const Work &w, cudaStream_t s);

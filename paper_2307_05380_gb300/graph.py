@@ -351,8 +351,8 @@ class EdgeVectors(torch.autograd.Function):
         g = ctx.graph
         gv = None if gvec is None else gvec.contiguous()
         gl = None if glen is None else glen.contiguous()
-        if g.perm_dst is None:
-            raise RuntimeError("edge-vector backward needs a graph built with with_perm=True")
+        # cutoff graphs need no destination order; other graphs need with_perm=True
+        # (the library answers MG_ERR_INVALID_ARGUMENT otherwise)
         gf, gL = edge_vectors_bwd(g, ctx.batch, gv, gl, vec, ln)
         return gf, gL, None
 

@@ -353,6 +353,23 @@ def test_gradients_match_oracle_and_are_deterministic():
     assert torch.equal(g1[0], g2[0]) and torch.equal(g1[1], g2[1])
 
 
+def test_symmetric_and_destination_order_backward_agree():
+    """A cutoff graph's backward through reverse edges (no perm_dst) against the
+    destination-order path (a per-structure build is not recorded as symmetric)."""
+    b = synth.make_batch(4, B=64)
+    batch = to_device(b)
+    g_sym = mg.cutoff_graph(batch, 5.0, with_perm=False)
+    g_gen = mg.build_per_structure(batch, "cutoff", cutoff=5.0)
+    assert g_sym.num_edges == g_gen.num_edges
+    gl = torch.from_numpy(synth.normal(3, 0, g_sym.num_edges)).cuda()
+    v1, l1 = mg.edge_vectors_fwd(g_sym)
+    v2, l2 = mg.edge_vectors_fwd(g_gen)
+    f1, L1 = mg.edge_vectors_bwd(g_sym, batch, None, gl, v1, l1)
+    f2, L2 = mg.edge_vectors_bwd(g_gen, batch, None, gl, v2, l2)
+    torch.testing.assert_close(f1, f2, rtol=1e-5, atol=1e-5 * float(f2.abs().max()))
+    torch.testing.assert_close(L1, L2, rtol=1e-5, atol=1e-5 * float(L2.abs().max()))
+
+
 def test_gradients_knn_graph_grad_vec_path():
     b = synth.make_batch(2, B=64)
     g = mg.knn_graph(to_device(b), 16)
