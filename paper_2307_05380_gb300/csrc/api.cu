@@ -115,7 +115,7 @@ size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
     size_t recs, pos, atom_struct, cnt, cursor, tile_sum, src_ptr, gpart, lpart, queue, bin_cnt, bin_cursor,
-        cell_start, cell_fx, cell_p, atom_bin, atom_tile, sort_tmp, total;
+        cell_start, cell_fx, cell_p, atom_bin, tile_flags, sort_tmp, total;
 };
 
 // Workspace regions, 256-byte aligned; the edge-sized sort scratch comes last so that
@@ -147,7 +147,7 @@ Layout layout(int B, int N, int64_t max_edges) {
     L.cell_fx = take(sizeof(float4) * n);
     L.cell_p = take(sizeof(float4) * n);
     L.atom_bin = take(sizeof(int32_t) * n);
-    L.atom_tile = take(sizeof(long long) * (n / ATOM_TILE + 2));
+    L.tile_flags = take(sizeof(unsigned long long) * (n / BUILD_TILE + 2));
     L.sort_tmp = off;
     off += sizeof(int32_t) * (size_t)(max_edges > 0 ? max_edges : 0);
     L.total = align_up(off);
@@ -174,7 +174,7 @@ Work carve(void *ws, int B, int N, int64_t max_edges) {
     w.cell_fx = reinterpret_cast<float4 *>(b + L.cell_fx);
     w.cell_p = reinterpret_cast<float4 *>(b + L.cell_p);
     w.atom_bin = reinterpret_cast<int32_t *>(b + L.atom_bin);
-    w.atom_tile = reinterpret_cast<long long *>(b + L.atom_tile);
+    w.tile_flags = reinterpret_cast<unsigned long long *>(b + L.tile_flags);
     w.sort_tmp = reinterpret_cast<int32_t *>(b + L.sort_tmp);
     w.max_edges = max_edges;
     return w;
@@ -261,7 +261,6 @@ mg_status_t enqueue_build(mg_context *ctx, int kind, const mg_batch_t *b, float 
         mk.mark("bin");
     }
     BuildArgs ba;
-    ba.fused_scan = 1;
     ba.struct_offset = 0;
     ba.B = B;
     ba.N = N;
@@ -276,11 +275,9 @@ mg_status_t enqueue_build(mg_context *ctx, int kind, const mg_batch_t *b, float 
     ba.atom_lo = 0;
     ba.atom_hi = N;
     if (kind == MG_KIND_CUTOFF) {
-        if (launch_cutoff_count(ba, w, st)) return MG_ERR_CUDA;  // also scans its totals
-        n += 1 + (ba.schedule == 2);
-        mk.mark("count");
-        if (launch_cutoff_write(ba, w, st)) return MG_ERR_CUDA;  // also writes src_ptr, edge_ptr
-        n += 1 + (ba.schedule == 2);
+        // one pass: scan, look-back offsets, write (also src_ptr, edge_ptr, edge count)
+        if (launch_cutoff_build(ba, w, st)) return MG_ERR_CUDA;
+        ++n;
         mk.mark("write");
     } else {
         if (launch_knn(ba, w, st)) return MG_ERR_CUDA;
@@ -567,7 +564,6 @@ mg_status_t mg_build_per_structure(mg_context_t ctx, const mg_batch_t *b, int32_
             n += 7;
         }
         BuildArgs ba;
-        ba.fused_scan = 0;
         ba.struct_offset = s;
         ba.B = B;
         ba.N = N;
@@ -602,7 +598,6 @@ mg_status_t mg_build_per_structure(mg_context_t ctx, const mg_batch_t *b, int32_
         }
     }
     BuildArgs fa;
-    fa.fused_scan = 0;
     fa.struct_offset = 0;
     fa.B = B;
     fa.N = N;

@@ -20,13 +20,13 @@ namespace mg {
 __global__ void __launch_bounds__(128) prep_kernel(PrepArgs a, StructRec *__restrict__ recs,
                                                     float4 *__restrict__ pos,
                                                     int32_t *__restrict__ atom_struct,
-                                                    long long *__restrict__ atom_tile,
+                                                    unsigned long long *__restrict__ tile_flags,
                                                     unsigned int *__restrict__ queue) {
-    if (a.zero_tiles) {  // the fused count scan accumulates into these
-        const int ntiles = (a.N + ATOM_TILE - 1) / ATOM_TILE + 1;
+    if (a.zero_tiles) {  // the one-pass build's look-back words and tile ticket start at zero
+        const int ntiles = (a.N + BUILD_TILE - 1) / BUILD_TILE + 1;
         for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x)
-            atom_tile[t] = 0;
-        if (blockIdx.x == 0 && threadIdx.x == 0) queue[2] = 0;
+            tile_flags[t] = 0;
+        if (blockIdx.x == 0 && threadIdx.x == 0) queue[3] = 0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && (a.init_status || (a.knn_k > 0 && a.edge_ptr))) {
         // nothing else writes the status word before the kernels that follow prep
@@ -187,7 +187,7 @@ cudaError_t launch_prep(const PrepArgs &a, const Work &w, cudaStream_t s) {
     if (a.B <= 0) return cudaSuccess;
     const int threads = 128;
     const int blocks = (a.B * 32 + threads - 1) / threads;
-    prep_kernel<<<blocks, threads, 0, s>>>(a, w.recs, w.pos, w.atom_struct, w.atom_tile, w.queue);
+    prep_kernel<<<blocks, threads, 0, s>>>(a, w.recs, w.pos, w.atom_struct, w.tile_flags, w.queue);
     return cudaGetLastError();
 }
 
@@ -425,48 +425,7 @@ __global__ void __launch_bounds__(256) cutoff_count_kernel(BuildArgs a, Work w) 
             count += __popc(__ballot_sync(FULL, in));
             ncand += __popc(__ballot_sync(FULL, cand));
         });
-        if (lane_id() == 0) {
-            w.cnt[i] = count;
-            if (a.fused_scan && count)
-                atomicAdd(reinterpret_cast<unsigned long long *>(&w.atom_tile[i / ATOM_TILE]),
-                          (unsigned long long)count);
-        }
-    }
-    if (a.fused_scan) {
-        // The last block to finish turns the tile totals into tile offsets (integer
-        // atomics, so the result does not depend on the order blocks finish in).
-        __shared__ unsigned int s_ticket;
-        __shared__ long long sm[64];
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            s_ticket = atomicAdd(&w.queue[2], 1u);
-        }
-        __syncthreads();
-        if (s_ticket == gridDim.x - 1) {
-            __threadfence();
-            const int ntiles = (a.N + ATOM_TILE - 1) / ATOM_TILE;
-            long long carry = 0;
-            for (int b0 = 0; b0 < ntiles; b0 += 256) {
-                const int q = b0 + threadIdx.x;
-                const long long v = q < ntiles ? __ldcg(&w.atom_tile[q]) : 0;
-                long long tot;
-                const long long ex = block_excl_scan_ll(v, sm, tot);
-                if (q < ntiles) w.atom_tile[q] = carry + ex;
-                carry += tot;
-            }
-            if (threadIdx.x == 0) {
-                w.atom_tile[ntiles] = carry;
-                Status *st = reinterpret_cast<Status *>(a.g.status);
-                st->num_edges = (unsigned long long)carry;
-                st->required_capacity = (unsigned long long)carry;
-                if (carry > a.g.capacity) set_error(a.g.status, MG_ERR_CAPACITY, -1);
-                a.src_ptr[a.N] = carry;
-                a.g.edge_ptr[a.B] = carry;
-                for (int s = a.B - 1; s >= 0 && a.atom_ptr[s] == a.N; --s) a.g.edge_ptr[s] = carry;
-                w.queue[2] = 0;
-            }
-        }
+        if (lane_id() == 0) w.cnt[i] = count;
     }
     if (a.collect_stats && lane_id() == 0 && ncand) {
         Status *st = reinterpret_cast<Status *>(a.g.status);
@@ -574,23 +533,8 @@ __global__ void __launch_bounds__(WRITE_WARPS * 32) cutoff_write_kernel(BuildArg
     const unsigned lt = (1u << lane_id()) - 1u;
     for (int i = loop.first(); i < a.atom_hi; i = loop.next()) {
         const int s = w.atom_struct[i];
-        int64_t base, endp;
-        if (a.fused_scan) {
-            // src_ptr[i] = offset of i's tile + counts of the tile's earlier atoms
-            const int t0 = (i / ATOM_TILE) * ATOM_TILE;
-            long long pre = 0;
-            for (int q = t0 + lane_id(); q < i; q += 32) pre += w.cnt[q];
-            pre = warp_sum(pre);
-            base = w.atom_tile[i / ATOM_TILE] + pre;
-            endp = base + w.cnt[i];
-            if (lane_id() == 0) {
-                a.src_ptr[i] = base;
-                for (int q = s; q >= 0 && a.atom_ptr[q] == i; --q) g.edge_ptr[q] = base;  // structures starting at i
-            }
-        } else {
-            base = a.src_ptr[i];
-            endp = a.src_ptr[i + 1];
-        }
+        const int64_t base = a.src_ptr[i];
+        const int64_t endp = a.src_ptr[i + 1];
         if (endp > g.capacity || endp == base) continue;  // capacity error already reported
         const StructRec &R = w.recs[s];
         if (R.bad) continue;
@@ -688,6 +632,215 @@ cudaError_t launch_cutoff_write(const BuildArgs &a, const Work &w, cudaStream_t 
     } else {
         cutoff_write_kernel<1><<<blocks_for(atoms, threads), threads, 0, s>>>(a, w);
     }
+    return cudaGetLastError();
+}
+
+// ============================================================================ single-pass build
+
+// Tile status words of the decoupled look-back: value in the low 62 bits, flag on top.
+constexpr unsigned long long TILE_AGG = 1ull << 62;      // tile total published
+constexpr unsigned long long TILE_PREFIX = 2ull << 62;   // inclusive prefix published
+constexpr unsigned long long TILE_VALUE = (1ull << 62) - 1;
+constexpr int LOOKBACK_SPIN_LIMIT = 1 << 22;             // bounded wait per predecessor
+
+__device__ __forceinline__ unsigned long long load_flag(const unsigned long long *p) {
+    return *reinterpret_cast<const volatile unsigned long long *>(p);
+}
+
+// Exclusive prefix of tile `tile` from its predecessors' published words.  Every wait is
+// bounded: a predecessor that publishes nothing within the limit makes the build report
+// MG_ERR_TIMEOUT (and the prefix is then wrong) instead of hanging.
+__device__ long long tile_lookback(const unsigned long long *flags, int tile, mg_device_status_t *status) {
+    long long excl = 0;
+    int q = tile - 1, spins = 0;
+    while (q >= 0) {
+        const unsigned long long v = load_flag(&flags[q]);
+        const unsigned long long f = v & ~TILE_VALUE;
+        if (f == 0) {
+            if (++spins > LOOKBACK_SPIN_LIMIT) {
+                set_error(status, MG_ERR_TIMEOUT, -1);
+                break;
+            }
+            __nanosleep(32);
+            continue;
+        }
+        excl += (long long)(v & TILE_VALUE);
+        if (f == TILE_PREFIX) break;
+        --q;
+        spins = 0;
+    }
+    return excl;
+}
+
+constexpr int BUILD_WARPS = BUILD_TILE;
+constexpr int BUILD_CAP = 1024;  // edges of one source staged in shared memory
+
+// Cutoff graph in one pass.  Tiles of BUILD_WARPS consecutive source atoms are taken in
+// order (a ticket per block, so every tile a block waits on is already running); each
+// warp scans its source once and stages the edges' (j, t) keys in shared memory
+// (canonical order from the all-pairs enumeration, sorted for cell-list sources); the
+// tile's total is published, the tile's offset found by a decoupled look-back over the
+// predecessors; then the edges are written from shared memory.  A source with more than
+// BUILD_CAP edges (or an offset outside the packed key) is counted in the first scan
+// and emitted by a second, canonical all-pairs scan.  Writes src_ptr, edge_ptr, the
+// edge count and the capacity check too.
+__global__ void __launch_bounds__(BUILD_WARPS * 32) cutoff_build_kernel(BuildArgs a, Work w) {
+    __shared__ unsigned long long keys_all[BUILD_WARPS][BUILD_CAP];
+    __shared__ int s_tile;
+    __shared__ int s_cnt[BUILD_WARPS];
+    __shared__ long long s_prefix;
+    const int wid = threadIdx.x >> 5, lane = lane_id();
+    unsigned long long *keys = keys_all[wid];
+    const unsigned lt = (1u << lane) - 1u;
+    const mg_graph_t g = a.g;
+    const Cells cells{w.cell_start, w.cell_fx, w.cell_p};
+    unsigned long long *flags = w.tile_flags;
+    const int ntiles = gridDim.x;
+
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(&w.queue[3], 1u);
+    __syncthreads();
+    const int tile = s_tile;
+    const int i = a.atom_lo + tile * BUILD_WARPS + wid;
+    const bool have = i < a.atom_hi;
+    int s = 0;
+    int m = 0;
+    bool spill = false;  // edges not staged: emit through a second all-pairs scan
+    Source S;
+    float thr_lo = 0.f, thr_hi = 0.f, cut = 0.f;
+    double rr = 0.0;
+    unsigned long long nre = 0, ncand = 0;
+    if (have) {
+        s = w.atom_struct[i];
+        const StructRec &R = w.recs[s];
+        if (R.bad) {
+            if (lane == 0 && i == R.atom_begin) set_error(g.status, R.bad, s + a.struct_offset);
+        } else {
+            load_source(S, w.recs, s, a.frac, w.pos, i);
+            thr_lo = R.thr_lo;
+            thr_hi = R.thr_hi;
+            cut = R.cut;
+            rr = R.rr;
+            const bool cellp = S.nb[0] != 0;
+            bool range_bad = false;
+            for_each_candidate(S, a.frac, w.pos, cells, true, R.cut, [&](bool vc, float d2, bool self, int ow,
+                                                                          int t2, const RowRegs &rw) {
+                const bool cand = vc && !self;
+                bool in = cand && d2 < thr_lo;
+                const bool band = cand && !in && d2 <= thr_hi;
+                if (__any_sync(FULL, in || band)) {
+                    const int jj = __shfl_sync(FULL, rw.j, ow);
+                    const int t0 = __shfl_sync(FULL, rw.t0, ow);
+                    const int t1 = __shfl_sync(FULL, rw.t1, ow);
+                    if (band) {
+                        const int64_t jr = (int64_t)S.begin + jj;
+                        in = canon_d2(S.L, S.xi0, S.xi1, S.xi2, a.frac[3 * jr], a.frac[3 * jr + 1],
+                                      a.frac[3 * jr + 2], t0, t1, t2) < rr;
+                    }
+                    if (a.collect_stats) nre += __popc(__ballot_sync(FULL, band));
+                    const unsigned bal = __ballot_sync(FULL, in);
+                    if (in) {
+                        if (abs(t0) > OFFSET_KEY_LIM || abs(t1) > OFFSET_KEY_LIM || abs(t2) > OFFSET_KEY_LIM)
+                            range_bad = true;
+                        const int p = m + __popc(bal & lt);
+                        if (p < BUILD_CAP)
+                            keys[p] = ((unsigned long long)(unsigned)jj << 32) | pack_t(t0, t1, t2);
+                    }
+                    m += __popc(bal);
+                }
+                if (a.collect_stats) ncand += __popc(__ballot_sync(FULL, cand));
+            });
+            spill = m > BUILD_CAP || __any_sync(FULL, range_bad);
+            if (!spill && cellp && m > 1) {
+                int P = 64;
+                while (P < m) P <<= 1;
+                warp_smem_sort_u64(keys, m, P);
+            }
+            if (a.collect_stats && lane == 0 && ncand) {
+                Status *st = reinterpret_cast<Status *>(g.status);
+                atomicAdd(&st->rechecked, nre);
+                atomicAdd(&st->candidates, ncand);
+            }
+        }
+    }
+    if (lane == 0) s_cnt[wid] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long agg = 0;
+        for (int q = 0; q < BUILD_WARPS; ++q) agg += s_cnt[q];
+        long long prefix = 0;
+        if (tile == 0) {
+            atomicExch(&flags[0], TILE_PREFIX | (unsigned long long)agg);
+        } else {
+            atomicExch(&flags[tile], TILE_AGG | (unsigned long long)agg);
+            prefix = tile_lookback(flags, tile, g.status);
+            atomicExch(&flags[tile], TILE_PREFIX | (unsigned long long)(prefix + agg));
+        }
+        s_prefix = prefix;
+        if (tile == ntiles - 1) {  // the last tile knows the edge count
+            const long long tot = prefix + agg;
+            Status *st = reinterpret_cast<Status *>(g.status);
+            st->num_edges = (unsigned long long)tot;
+            st->required_capacity = (unsigned long long)tot;
+            if (tot > g.capacity) set_error(g.status, MG_ERR_CAPACITY, -1);
+            a.src_ptr[a.N] = tot;
+            g.edge_ptr[a.B] = tot;
+            for (int q = a.B - 1; q >= 0 && a.atom_ptr[q] == a.N; --q) g.edge_ptr[q] = tot;
+        }
+    }
+    __syncthreads();
+    if (!have) return;
+    int64_t base = s_prefix;
+    for (int q = 0; q < wid; ++q) base += s_cnt[q];
+    if (lane == 0) {
+        a.src_ptr[i] = base;
+        for (int q = s; q >= 0 && a.atom_ptr[q] == i; --q) g.edge_ptr[q] = base;  // structures starting at i
+    }
+    if (m == 0 || base + m > g.capacity) return;  // nothing to write, or the capacity error
+    if (!spill) {
+        for (int q = lane; q < m; q += 32) {
+            const unsigned long long key = keys[q];
+            int t0, t1, t2;
+            unpack_t((uint32_t)(key & 0xffffffffull), t0, t1, t2);
+            const int64_t jr = (int64_t)S.begin + (int)(key >> 32);
+            emit_edge(g, S, i, base + q, jr, a.frac[3 * jr], a.frac[3 * jr + 1], a.frac[3 * jr + 2], t0, t1, t2);
+        }
+    } else {
+        int64_t out = base;
+        const int64_t endp = base + m;
+        for_each_candidate(S, a.frac, w.pos, cells, false, cut,
+                           [&](bool vc, float d2, bool self, int ow, int t2, const RowRegs &rw) {
+            const bool cand = vc && !self;
+            bool in = cand && d2 < thr_lo;
+            const bool band = cand && !in && d2 <= thr_hi;
+            if (__any_sync(FULL, in || band)) {
+                const int jj = __shfl_sync(FULL, rw.j, ow);
+                const int t0 = __shfl_sync(FULL, rw.t0, ow);
+                const int t1 = __shfl_sync(FULL, rw.t1, ow);
+                const int64_t jr = (int64_t)S.begin + jj;
+                float xj0 = 0.f, xj1 = 0.f, xj2 = 0.f;
+                if (in || band) {
+                    xj0 = a.frac[3 * jr];
+                    xj1 = a.frac[3 * jr + 1];
+                    xj2 = a.frac[3 * jr + 2];
+                }
+                if (band) in = canon_d2(S.L, S.xi0, S.xi1, S.xi2, xj0, xj1, xj2, t0, t1, t2) < rr;
+                const unsigned bal = __ballot_sync(FULL, in);
+                if (in) {
+                    const int64_t e = out + __popc(bal & lt);
+                    if (e < endp) emit_edge(g, S, i, e, jr, xj0, xj1, xj2, t0, t1, t2);
+                }
+                out += __popc(bal);
+            }
+        });
+        if (lane == 0 && out != endp) set_error(g.status, MG_ERR_INTERNAL, s);
+    }
+}
+
+cudaError_t launch_cutoff_build(const BuildArgs &a, const Work &w, cudaStream_t s) {
+    const int atoms = a.atom_hi - a.atom_lo;
+    if (atoms <= 0) return cudaSuccess;
+    const int tiles = (atoms + BUILD_WARPS - 1) / BUILD_WARPS;
+    cutoff_build_kernel<<<tiles, BUILD_WARPS * 32, 0, s>>>(a, w);
     return cudaGetLastError();
 }
 

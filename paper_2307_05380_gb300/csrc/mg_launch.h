@@ -30,12 +30,12 @@ struct Work {
     float4 *cell_fx;          // [N] fractional coordinates of each slot, .w = local index bits
     float4 *cell_p;           // [N] FP32 Cartesian position of each slot (bin order)
     int32_t *atom_bin;        // [N] global bin of each atom (-1: all-pairs structure)
-    long long *atom_tile;     // [N/ATOM_TILE + 2] edges per tile of atoms, then tile offsets
+    unsigned long long *tile_flags;  // [N/BUILD_TILE + 2] look-back words of the one-pass build
     int64_t max_edges;
 };
 
 constexpr int SCAN_TILE = 4096;
-constexpr int ATOM_TILE = 256;   // atoms per tile of the fused count scan
+constexpr int BUILD_TILE = 4;    // source atoms per tile (one warp each) of the one-pass build
 
 struct PrepArgs {
     int B, N;
@@ -47,7 +47,7 @@ struct PrepArgs {
     float band_rel;
     mg_device_status_t *status;
     int struct_offset;         // global index of the first structure of this call
-    int zero_tiles;            // 1: clear the fused count scan's tile sums and counter
+    int zero_tiles;            // 1: clear the one-pass build's look-back words and ticket
     int init_status;           // 1: reset the status word (first kernel of a build)
     int64_t *src_ptr;          // KNN: written here (k per atom); may be NULL otherwise
     int64_t *edge_ptr;         // KNN: written here
@@ -81,11 +81,12 @@ struct BuildArgs {
     int knn_k;
     float band_rel;
     int atom_lo, atom_hi;      // atom row range to process (per-structure builds)
-    int fused_scan;            // 1: count kernel scans its own totals, write kernel derives
-                               //    src_ptr/edge_ptr (batched builds); 0: separate scan kernels
     int struct_offset;         // global index of local structure 0 (per-structure builds)
 };
 
+// One-pass cutoff build (batched): scan once, stage keys, look-back offsets, write.
+cudaError_t launch_cutoff_build(const BuildArgs &a, const Work &w, cudaStream_t s);
+// Two-pass form (per-structure builds): count, separate scan, write.
 cudaError_t launch_cutoff_count(const BuildArgs &a, const Work &w, cudaStream_t s);
 // Edge pointers, status and capacity check after the scan of counts.
 cudaError_t launch_cutoff_finalize(const BuildArgs &a, const Work &w, cudaStream_t s);
