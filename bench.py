@@ -44,8 +44,7 @@ WORKLOADS = {
 # Algorithmic work per unit of each stage (bytes or FP32 flops per edge, per atom).
 # Edge record: src 4 + dst 4 + offset 12 + vec 12 + len 4 = 36 B.
 STAGE_MODEL = {
-    ("cutoff", "write"): ("hbm", 36.0, "cut"),
-    ("cutoff", "count"): ("alu", 21.0, "cut"),
+    ("cutoff", "build"): ("hbm", 36.0, "cut"),
     ("knn", "knn"): ("hbm", 36.0, "knn"),
     ("fwd", "fwd"): ("hbm", 36.0, "cut"),
     ("bwd", "bwd_sym"): ("hbm", 68.0, "cut"),
@@ -56,7 +55,7 @@ STAGE_MODEL = {
 # Stages that are one kernel launch; the roofline reports the slowest of these (the
 # others bundle several launches: prep, the cell-list binning, the destination sort's
 # histogram / scan / scatter / segment sort).
-SINGLE_KERNEL_STAGES = {("cutoff", "count"), ("cutoff", "write"), ("knn", "knn"), ("fwd", "fwd"),
+SINGLE_KERNEL_STAGES = {("cutoff", "build"), ("knn", "knn"), ("fwd", "fwd"),
                         ("bwd", "bwd_sym"), ("bwd", "bwd_src"), ("bwd", "bwd_dst"), ("bwd", "bwd_lat")}
 
 

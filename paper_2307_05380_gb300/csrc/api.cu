@@ -278,7 +278,7 @@ mg_status_t enqueue_build(mg_context *ctx, int kind, const mg_batch_t *b, float 
         // one pass: scan, look-back offsets, write (also src_ptr, edge_ptr, edge count)
         if (launch_cutoff_build(ba, w, st)) return MG_ERR_CUDA;
         ++n;
-        mk.mark("write");
+        mk.mark("build");
     } else {
         if (launch_knn(ba, w, st)) return MG_ERR_CUDA;
         n += 1 + (ba.schedule == 2);

@@ -684,7 +684,8 @@ constexpr int BUILD_CAP = 1024;  // edges of one source staged in shared memory
 // BUILD_CAP edges (or an offset outside the packed key) is counted in the first scan
 // and emitted by a second, canonical all-pairs scan.  Writes src_ptr, edge_ptr, the
 // edge count and the capacity check too.
-__global__ void __launch_bounds__(BUILD_WARPS * 32) cutoff_build_kernel(BuildArgs a, Work w) {
+// At most 85 registers (6 blocks of 4 warps per SM), the measured best register budget.
+__global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_build_kernel(BuildArgs a, Work w) {
     __shared__ unsigned long long keys_all[BUILD_WARPS][BUILD_CAP];
     __shared__ int s_tile;
     __shared__ int s_cnt[BUILD_WARPS];

@@ -9,9 +9,12 @@
 //           by rho with the error band to spare, rho grows and the pass repeats (the
 //           covered-radius test plays the role of closest_distance(border, rho)).
 //   pass 2  the same scan again: images with FP32 d2 < tau - 2 delta are certainly
-//           among the k nearest; images within tau +- 2 delta are re-ranked by the
-//           canonical FP64 distance with the (d2, j, t) tie-break in a second register
-//           top-k; the k winners are sorted by (j, t) and written in canonical order.
+//           among the k nearest; images within tau +- 2 delta (the band) are staged in
+//           shared memory.  If the band holds exactly the slots left, all of it is
+//           taken; otherwise it is ranked by the canonical FP64 distance with the
+//           (d2, j, t) tie-break in a second register top-k (GB300's FP64 rate is low,
+//           so FP64 runs only when the order inside the band decides membership).  The
+//           k winners are sorted by (j, t) and written in canonical order.
 // delta bounds the FP32 error (fp32_d2_error) plus the requested band.
 #include "mg_device.cuh"
 #include "mg_enum.cuh"
@@ -132,12 +135,17 @@ struct KnnLoop {
 };
 
 constexpr int KNN_WARPS = 4;
+constexpr int BAND_CAP = 64;  // band candidates staged per source in shared memory
 
+// At most 85 registers (6 blocks of 4 warps per SM): measured faster than 128 registers
+// (fewer resident warps) and than 64 (more spills) on the bench workloads.
 template <int S, int SCHED>
-__global__ void __launch_bounds__(KNN_WARPS * 32) knn_kernel(BuildArgs a, Work w) {
+__global__ void __launch_bounds__(KNN_WARPS * 32, 6) knn_kernel(BuildArgs a, Work w) {
     __shared__ unsigned long long sel_all[KNN_WARPS][S * 32 > 64 ? S * 32 : 64];
+    __shared__ unsigned long long band_all[KNN_WARPS][BAND_CAP];
     const int wid = threadIdx.x >> 5, lane = lane_id();
     unsigned long long *sel = sel_all[wid];
+    unsigned long long *bl = band_all[wid];
     const int k = a.knn_k;
     const unsigned lt = (1u << lane) - 1u;
     const mg_graph_t g = a.g;
@@ -191,15 +199,13 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_kernel(BuildArgs a, Work w
             continue;
         }
 
-        // ---------------- pass 2: certain members, FP64 re-rank of the band
+        // ---------------- pass 2: certain members; the band is staged, then ranked only
+        // if it holds more candidates than the slots left (FP64 only in that case)
         const float lo_thr = tau - 2.0f * delta, hi_thr = tau + 2.0f * delta;
-        int m = 0;
+        int m = 0, nb = 0;
         bool range_bad = false;
-        TopK<XKey, S> ek;
-        ek.init();
-        XKey ethr = kinf(XKey{});
-        for_each_candidate(Src, a.frac, w.pos, cells, true, rho,[&](bool vc, float d2, bool self, int ow, int t2,
-                                                          const RowRegs &rw) {
+        for_each_candidate(Src, a.frac, w.pos, cells, true, rho, [&](bool vc, float d2, bool self, int ow, int t2,
+                                                                      const RowRegs &rw) {
             const bool c = vc && !self;
             const bool in = c && d2 < lo_thr;
             const bool band = c && !in && d2 <= hi_thr;
@@ -216,34 +222,76 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_kernel(BuildArgs a, Work w
                     if (p < k) sel[p] = jt;
                 }
                 m += __popc(bin);
-                XKey key = kinf(XKey{});
+                const unsigned bb = __ballot_sync(FULL, band);
                 if (band) {
-                    const int64_t jr = (int64_t)Src.begin + jj;
-                    const double d = canon_d2(Src.L, Src.xi0, Src.xi1, Src.xi2, a.frac[3 * jr], a.frac[3 * jr + 1],
-                                              a.frac[3 * jr + 2], t0, t1, t2);
-                    key = XKey{(unsigned long long)__double_as_longlong(d), jt};
+                    const int p = nb + __popc(bb & lt);
+                    if (p < BAND_CAP) bl[p] = jt;
                 }
-                const bool ins = band && kless(key, ethr);
-                if (a.collect_stats) nre += __popc(__ballot_sync(FULL, band));
-                if (__any_sync(FULL, ins)) {
-                    ek.insert(ins ? key : kinf(XKey{}));
-                    ethr = ek.kth(k);
-                }
+                nb += __popc(bb);
             }
         });
         if (__any_sync(FULL, range_bad)) {
             if (lane == 0) set_error(g.status, MG_ERR_OFFSET_RANGE, s);
             continue;
         }
-        if (m >= k) {  // cannot happen: at most k-1 FP32 distances lie below tau
+        if (m >= k || m + nb < k) {  // cannot happen: fewer than k FP32 distances lie below tau
             if (lane == 0) set_error(g.status, MG_ERR_INTERNAL, s);
             continue;
         }
         const int need = k - m;
+        __syncwarp();
+        if (nb == need) {  // every band member fills a remaining slot
+            for (int q = lane; q < nb; q += 32) sel[m + q] = bl[q];
+        } else {  // rank the band by (canonical FP64 d2, j, t)
+            TopK<XKey, S> ek;
+            ek.init();
+            if (a.collect_stats) nre += nb;
+            if (nb <= BAND_CAP) {
+                for (int b0 = 0; b0 < nb; b0 += 32) {
+                    const int q = b0 + lane;
+                    XKey key = kinf(XKey{});
+                    if (q < nb) {
+                        const unsigned long long jt = bl[q];
+                        int t0, t1, t2;
+                        unpack_t((uint32_t)(jt & 0xffffffffull), t0, t1, t2);
+                        const int64_t jr = (int64_t)Src.begin + (int)(jt >> 32);
+                        const double d = canon_d2(Src.L, Src.xi0, Src.xi1, Src.xi2, a.frac[3 * jr], a.frac[3 * jr + 1],
+                                                  a.frac[3 * jr + 2], t0, t1, t2);
+                        key = XKey{(unsigned long long)__double_as_longlong(d), jt};
+                    }
+                    ek.insert(key);
+                }
+            } else {  // the band did not fit in shared memory: stream it again with FP64 keys
+                XKey ethr = kinf(XKey{});
+                for_each_candidate(Src, a.frac, w.pos, cells, true, rho, [&](bool vc, float d2, bool self, int ow,
+                                                                              int t2, const RowRegs &rw) {
+                    const bool c = vc && !self;
+                    const bool band = c && d2 >= lo_thr && d2 <= hi_thr;
+                    if (__any_sync(FULL, band)) {
+                        const int jj = __shfl_sync(FULL, rw.j, ow);
+                        const int t0 = __shfl_sync(FULL, rw.t0, ow);
+                        const int t1 = __shfl_sync(FULL, rw.t1, ow);
+                        XKey key = kinf(XKey{});
+                        if (band) {
+                            const int64_t jr = (int64_t)Src.begin + jj;
+                            const double d = canon_d2(Src.L, Src.xi0, Src.xi1, Src.xi2, a.frac[3 * jr],
+                                                      a.frac[3 * jr + 1], a.frac[3 * jr + 2], t0, t1, t2);
+                            key = XKey{(unsigned long long)__double_as_longlong(d),
+                                       ((unsigned long long)(unsigned)jj << 32) | pack_t(t0, t1, t2)};
+                        }
+                        const bool ins = band && kless(key, ethr);
+                        if (__any_sync(FULL, ins)) {
+                            ek.insert(ins ? key : kinf(XKey{}));
+                            ethr = ek.kth(k);
+                        }
+                    }
+                });
+            }
 #pragma unroll
-        for (int q = 0; q < S; ++q) {
-            const int p = q * 32 + lane;
-            if (p < need) sel[m + p] = ek.a[q].jt;
+            for (int q = 0; q < S; ++q) {
+                const int p = q * 32 + lane;
+                if (p < need) sel[m + p] = ek.a[q].jt;
+            }
         }
         __syncwarp();
         // canonical (j, t) order of the k winners
