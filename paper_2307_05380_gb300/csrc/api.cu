@@ -251,7 +251,7 @@ mg_status_t enqueue_build(mg_context *ctx, int kind, const mg_batch_t *b, float 
     int64_t *src_ptr = g->src_ptr ? g->src_ptr : w.src_ptr;
     // prep also resets the status word and, for KNN, writes the k-per-atom pointers
     PrepArgs pa{B, N, b->lattice, b->frac, b->atom_ptr, cutoff, cutoff_ps, kind == MG_KIND_KNN ? k : 0,
-                o.band_rel, g->status, 0, kind == MG_KIND_CUTOFF ? 1 : 0, 1, src_ptr, g->edge_ptr};
+                o.band_rel, g->status, 0, kind == MG_KIND_CUTOFF ? 1 : 0, 1, src_ptr, g->edge_ptr, b->max_atoms};
     if (launch_prep(pa, w, st)) return MG_ERR_CUDA;
     ++n;
     mk.mark("prep");
@@ -556,7 +556,7 @@ mg_status_t mg_build_per_structure(mg_context_t ctx, const mg_batch_t *b, int32_
         Work w = w0;
         w.recs = w0.recs + s;  // the structure's record sits at local index 0
         PrepArgs pa{1, hi - lo, b->lattice + 9 * (size_t)s, b->frac, b->atom_ptr + s, cutoff, nullptr,
-                    kind == MG_KIND_KNN ? k : 0, o.band_rel, g->status, s, 0, 0, nullptr, nullptr};
+                    kind == MG_KIND_KNN ? k : 0, o.band_rel, g->status, s, 0, 0, nullptr, nullptr, hi - lo};
         if (launch_prep(pa, w, st)) return MG_ERR_CUDA;
         ++n;
         if (hi - lo >= CELL_MIN_ATOMS) {  // this structure may use a cell list

@@ -212,11 +212,24 @@ __global__ void __launch_bounds__(256) bwd_sym_kernel(EdgeVecArgs a, double *__r
     float M[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) M[q] = 0.f;
-    for (int64_t p = lo + lane; p < hi; p += 32) {
+    for (int64_t p0 = lo; p0 < hi; p0 += 32) {
+        const int64_t p = p0 + lane;
+        const bool valid = p < hi;
+        const int i = valid ? a.g.dst[p] : -1;
+        // lanes of one run (same target i, contiguous) share the run's two searches
+        const unsigned grp = __match_any_sync(FULL, i);
+        const int leader = __ffs(grp) - 1;
+        int64_t rhi = 0, sij = 0;
+        if (valid && lane == leader) {
+            int64_t e = p + 1;  // end of the run: a short probe, then a binary search
+            while (e < hi && e < p + 4 && a.g.dst[e] == i) ++e;
+            rhi = (e < hi && e == p + 4 && a.g.dst[e] == i) ? key_bound(a.g.dst, e, hi, i, true) : e;
+            sij = key_bound(a.g.dst, a.g.src_ptr[i], a.g.src_ptr[i + 1], j, false);
+        }
+        rhi = __shfl_sync(FULL, rhi, leader);
+        sij = __shfl_sync(FULL, sij, leader);
+        if (!valid) continue;
         const float3 g = edge_g(a, p);
-        const int i = a.g.dst[p];
-        const int64_t rhi = key_bound(a.g.dst, p, hi, i, true);  // end of p's run
-        const int64_t sij = key_bound(a.g.dst, a.g.src_ptr[i], a.g.src_ptr[i + 1], j, false);
         const float3 gr = edge_g(a, sij + (rhi - 1 - p));
         acc[0] += gr.x - g.x;
         acc[1] += gr.y - g.y;

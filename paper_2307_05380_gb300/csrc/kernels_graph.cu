@@ -1,12 +1,16 @@
 // Batched cutoff-graph construction (Def. 3, Sec. 2.1) on sm_103a:
-//   prep      one warp per structure: FP64 lattice inverse, interplanar spacings,
-//             FP32 Cartesian positions, FP32 error bound and re-test band;
-//   count     one warp per source atom: FP32 scan of the periodic images inside the
-//             interplanar box (Sec. 2.2's evaluated area), FP64 re-test in the band;
-//   scan      exclusive prefix of the counts (tile reduce, top scan, tile apply);
-//   finalize  per-structure edge pointers, edge count, capacity check;
-//   write     the same scan again, emitting (src, dst, t, vec, len) in canonical order;
-//   dst sort  edge ids ordered by (dst, src, t) for the deterministic backward pass.
+//   prep      a warp (or block) per structure: lattice cofactors in FP64, interplanar
+//             spacings, FP32 Cartesian positions, FP32 error bound and re-test band,
+//             cell-list shape; also resets the status word;
+//   bins      the fractional cell list of large structures (count, scan, scatter);
+//   build     one pass per source atom (one warp each): FP32 scan of the periodic
+//             images inside the interplanar box (Sec. 2.2's evaluated area) with an FP64
+//             re-test in the band, keys staged in shared memory, offsets by a bounded
+//             decoupled look-back, edges (src, dst, t, vec, len) written in canonical
+//             order;
+//   count/scan/finalize/write  the two-pass form used by the per-structure build;
+//   dst order edge ids ordered by (dst, src, t): from reverse runs for symmetric
+//             (cutoff) graphs, by a counting sort plus segment sorts otherwise.
 #include <cstdio>
 
 #include "mg_device.cuh"
@@ -17,11 +21,19 @@ namespace mg {
 
 // ============================================================================ prep
 
-__global__ void __launch_bounds__(128) prep_kernel(PrepArgs a, StructRec *__restrict__ recs,
-                                                    float4 *__restrict__ pos,
-                                                    int32_t *__restrict__ atom_struct,
-                                                    unsigned long long *__restrict__ tile_flags,
-                                                    unsigned int *__restrict__ queue) {
+// One group of GROUP threads per structure: a warp (small structures, four per block) or
+// a whole block (large structures).  The group converts its atoms to FP32 Cartesian
+// positions and finds max |x|; its first thread then derives the structure record.
+// FP64 is used for the lattice cofactors and determinant (cancellation-prone) and the
+// squared cutoff; the derived bounds are FP32, rounded up or inflated by 1e-5 so that
+// they stay bounds.
+template <int GROUP>
+__global__ void __launch_bounds__(GROUP == 32 ? 128 : GROUP) prep_kernel(PrepArgs a, StructRec *__restrict__ recs,
+                                                                        float4 *__restrict__ pos,
+                                                                        int32_t *__restrict__ atom_struct,
+                                                                        unsigned long long *__restrict__ tile_flags,
+                                                                        unsigned int *__restrict__ queue) {
+    __shared__ float red[GROUP == 32 ? 1 : 4 * (GROUP / 32)];
     if (a.zero_tiles) {  // the one-pass build's look-back words and tile ticket start at zero
         const int ntiles = (a.N + BUILD_TILE - 1) / BUILD_TILE + 1;
         for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x)
@@ -44,13 +56,13 @@ __global__ void __launch_bounds__(128) prep_kernel(PrepArgs a, StructRec *__rest
             st->required_capacity = (unsigned long long)a.N * a.knn_k;
         }
     }
-    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = lane_id();
+    const int s = GROUP == 32 ? (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) : (int)blockIdx.x;
+    const int t = GROUP == 32 ? lane_id() : (int)threadIdx.x;
     if (s >= a.B) return;
     const int begin = a.atom_ptr[s], end = a.atom_ptr[s + 1];
     if (a.knn_k > 0 && a.edge_ptr) {  // KNN pointers: k edges per atom
-        for (int r = begin + lane; r < end; r += 32) a.src_ptr[r] = (int64_t)r * a.knn_k;
-        if (lane == 0) {
+        for (int r = begin + t; r < end; r += GROUP) a.src_ptr[r] = (int64_t)r * a.knn_k;
+        if (t == 0) {
             a.edge_ptr[s] = (int64_t)begin * a.knn_k;
             if (s == a.B - 1) {
                 a.edge_ptr[a.B] = (int64_t)a.N * a.knn_k;
@@ -61,11 +73,10 @@ __global__ void __launch_bounds__(128) prep_kernel(PrepArgs a, StructRec *__rest
     float Lf[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) Lf[q] = a.lattice[9 * (int64_t)s + q];
-    float xm0 = 0.f, xm1 = 0.f, xm2 = 0.f;
-    int nonfinite = 0;
-    for (int r = begin + lane; r < end; r += 32) {
+    float xm0 = 0.f, xm1 = 0.f, xm2 = 0.f, nonfinite = 0.f;
+    for (int r = begin + t; r < end; r += GROUP) {
         const float x0 = a.frac[3 * (int64_t)r], x1 = a.frac[3 * (int64_t)r + 1], x2 = a.frac[3 * (int64_t)r + 2];
-        if (!isfinite(x0) || !isfinite(x1) || !isfinite(x2)) nonfinite = 1;
+        if (!isfinite(x0) || !isfinite(x1) || !isfinite(x2)) nonfinite = 1.f;
         const float3 p = cart(Lf, x0, x1, x2);
         pos[r] = make_float4(p.x, p.y, p.z, 0.f);
         atom_struct[r] = s;
@@ -76,8 +87,25 @@ __global__ void __launch_bounds__(128) prep_kernel(PrepArgs a, StructRec *__rest
     xm0 = warp_max(xm0);
     xm1 = warp_max(xm1);
     xm2 = warp_max(xm2);
-    nonfinite = __any_sync(FULL, nonfinite);
-    if (lane != 0) return;
+    nonfinite = warp_max(nonfinite);
+    if (GROUP > 32) {
+        const int wid = threadIdx.x >> 5;
+        if (lane_id() == 0) {
+            red[4 * wid + 0] = xm0;
+            red[4 * wid + 1] = xm1;
+            red[4 * wid + 2] = xm2;
+            red[4 * wid + 3] = nonfinite;
+        }
+        __syncthreads();
+        if (t == 0)
+            for (int q = 1; q < GROUP / 32; ++q) {
+                xm0 = fmaxf(xm0, red[4 * q + 0]);
+                xm1 = fmaxf(xm1, red[4 * q + 1]);
+                xm2 = fmaxf(xm2, red[4 * q + 2]);
+                nonfinite = fmaxf(nonfinite, red[4 * q + 3]);
+            }
+    }
+    if (t != 0) return;
 
     StructRec R;
     double L[9];
@@ -87,66 +115,55 @@ __global__ void __launch_bounds__(128) prep_kernel(PrepArgs a, StructRec *__rest
         L[q] = (double)Lf[q];
         if (!isfinite(Lf[q])) bad = MG_ERR_NONFINITE_INPUT;
     }
-    if (nonfinite) bad = MG_ERR_NONFINITE_INPUT;
-    // FP64 inverse by cofactors (row-vector convention: f = v L^-1)
+    if (nonfinite != 0.f) bad = MG_ERR_NONFINITE_INPUT;
+    // cofactors (row-vector convention: f = v L^-1, column k of L^-1 = cofactor row k / det)
     const double c00 = L[4] * L[8] - L[5] * L[7], c01 = L[5] * L[6] - L[3] * L[8], c02 = L[3] * L[7] - L[4] * L[6];
     const double c10 = L[2] * L[7] - L[1] * L[8], c11 = L[0] * L[8] - L[2] * L[6], c12 = L[1] * L[6] - L[0] * L[7];
     const double c20 = L[1] * L[5] - L[2] * L[4], c21 = L[2] * L[3] - L[0] * L[5], c22 = L[0] * L[4] - L[1] * L[3];
     const double det = L[0] * c00 + L[1] * c01 + L[2] * c02;
-    const double la = sqrt(L[0] * L[0] + L[1] * L[1] + L[2] * L[2]);
-    const double lb = sqrt(L[3] * L[3] + L[4] * L[4] + L[5] * L[5]);
-    const double lc = sqrt(L[6] * L[6] + L[7] * L[7] + L[8] * L[8]);
-    if (!bad && (!(fabs(det) > 1e-9 * la * lb * lc) || !isfinite(det))) bad = MG_ERR_SINGULAR_LATTICE;
-    // Linv[c][k] = cofactor[k][c] / det ; column k of Linv = (c_k0, c_k1, c_k2) / det
-    const double cof[3][3] = {{c00, c01, c02}, {c10, c11, c12}, {c20, c21, c22}};
-    const double xm[3] = {(double)xm0, (double)xm1, (double)xm2};
-    double invd[3];
+    const float la = sqrtf(Lf[0] * Lf[0] + Lf[1] * Lf[1] + Lf[2] * Lf[2]);
+    const float lb = sqrtf(Lf[3] * Lf[3] + Lf[4] * Lf[4] + Lf[5] * Lf[5]);
+    const float lc = sqrtf(Lf[6] * Lf[6] + Lf[7] * Lf[7] + Lf[8] * Lf[8]);
+    const float adet = fabsf((float)det);
+    if (!bad && (!(adet > 1e-9f * la * lb * lc) || !isfinite(adet))) bad = MG_ERR_SINGULAR_LATTICE;
+    const double cn2[3] = {c00 * c00 + c01 * c01 + c02 * c02, c10 * c10 + c11 * c11 + c12 * c12,
+                           c20 * c20 + c21 * c21 + c22 * c22};
+    const float xm[3] = {xm0, xm1, xm2};
+    float invd[3];
     for (int k = 0; k < 3; ++k) {
-        const double n2 = cof[k][0] * cof[k][0] + cof[k][1] * cof[k][1] + cof[k][2] * cof[k][2];
-        invd[k] = bad ? 1.0 : sqrt(n2) / fabs(det);
-        R.invd[k] = __double2float_ru(invd[k] * (1.0 + 1e-6));
+        // ||L^-1[:, k]|| = 1 / d_k, inflated to stay an upper bound after FP32 rounding
+        invd[k] = bad ? 1.0f : sqrtf((float)cn2[k]) / adet * (1.0f + 1e-5f);
+        R.invd[k] = invd[k];
     }
-    double c;
+    float c;
     const int n = end - begin;
     if (a.knn_k > 0) {
-        const double V = fabs(det);
-        c = 1.1 * cbrt(3.0 * (a.knn_k + 1) * V / (4.0 * 3.14159265358979 * (n > 0 ? n : 1)));
-        if (!(c > 0.0) || !isfinite(c)) c = 1.0;
+        c = 1.1f * cbrtf(3.0f * (a.knn_k + 1) * adet / (4.0f * 3.14159265f * (n > 0 ? n : 1)));
+        if (!(c > 0.f) || !isfinite(c)) c = 1.0f;
     } else {
-        c = a.cutoff_ps ? (double)a.cutoff_ps[s] : (double)a.cutoff;
-        if (!bad && (!(c > 0.0) || !isfinite(c))) bad = MG_ERR_INVALID_ARGUMENT;
+        c = a.cutoff_ps ? a.cutoff_ps[s] : a.cutoff;
+        if (!bad && (!(c > 0.f) || !isfinite(c))) bad = MG_ERR_INVALID_ARGUMENT;
     }
-    R.cut = (float)c;
+    R.cut = c;
     for (int cc = 0; cc < 3; ++cc) {
-        double P = 0.0, Lt = 0.0, C = 0.0;
+        float P = 0.f, Lt = 0.f, C = 0.f;
         for (int k = 0; k < 3; ++k) {
-            const double al = fabs(L[3 * k + cc]);
+            const float al = fabsf(Lf[3 * k + cc]);
             P += xm[k] * al;
-            Lt += (double)R.invd[k] * al;
-            C += (2.0 * xm[k] + 1.0) * al;
+            Lt += invd[k] * al;
+            C += (2.0f * xm[k] + 1.0f) * al;
         }
-        R.errP[cc] = __double2float_ru(P * (1.0 + 1e-6));
-        R.errL[cc] = __double2float_ru(Lt * (1.0 + 1e-6));
-        R.errC[cc] = __double2float_ru(C * (1.0 + 1e-6));
+        R.errP[cc] = P * (1.0f + 1e-5f);
+        R.errL[cc] = Lt * (1.0f + 1e-5f);
+        R.errC[cc] = C * (1.0f + 1e-5f);
     }
     R.L2norm2 = Lf[6] * Lf[6] + Lf[7] * Lf[7] + Lf[8] * Lf[8];
     R.L2norm = sqrtf(R.L2norm2);
-    const double cr = (double)R.cut;
-    R.rr = cr * cr;
-    // re-test band around the cutoff: FP32 error bound, widened to the requested band
-    {
-        const double u8 = 8.0 * 5.9604644775390625e-8;
-        double en2 = 0.0;
-        for (int cc = 0; cc < 3; ++cc) {
-            const double e = u8 * (2.0 * R.errP[cc] + cr * R.errL[cc] + R.errC[cc]);
-            en2 += e * e;
-        }
-        const double en = sqrt(en2) * 1.01;
-        const double dv = cr * 1.01 + en;
-        const double fp = 2.0 * (3.1 * 5.9604644775390625e-8 * dv * dv + 2.0 * dv * en + en * en);
-        const double band = fmax(fp, 2.0 * (double)a.band_rel * R.rr);
-        R.thr_lo = __double2float_rd(R.rr - band);
-        R.thr_hi = __double2float_ru(R.rr + band);
+    R.rr = (double)c * (double)c;
+    {   // re-test band around the cutoff: FP32 error bound, widened to the requested band
+        const float band = fmaxf(fp32_d2_error(R, c, c * c), 2.0f * a.band_rel * c * c) * (1.0f + 1e-5f);
+        R.thr_lo = __double2float_rd(R.rr - (double)band);
+        R.thr_hi = __double2float_ru(R.rr + (double)band);
     }
     R.atom_begin = begin;
     R.n_atoms = n;
@@ -159,15 +176,14 @@ __global__ void __launch_bounds__(128) prep_kernel(PrepArgs a, StructRec *__rest
     R.bin_base = begin + s + a.struct_offset;
     if (!bad && n >= CELL_MIN_ATOMS) {
         int nk[3];
-        double prod = 1.0;
+        float prod = 1.f;
         for (int k = 0; k < 3; ++k) {
-            const double dk = 1.0 / invd[k];
-            nk[k] = (int)fmin(fmax(floor(2.0 * dk / cr), 1.0), 1024.0);
+            nk[k] = (int)fminf(fmaxf(floorf(2.0f / (invd[k] * c)), 1.0f), 1024.0f);
             prod *= nk[k];
         }
         if (prod > n) {
-            const double f = cbrt((double)n / prod);
-            for (int k = 0; k < 3; ++k) nk[k] = max(1, (int)floor(nk[k] * f));
+            const float f = cbrtf((float)n / prod);
+            for (int k = 0; k < 3; ++k) nk[k] = max(1, (int)floorf(nk[k] * f));
         }
         while ((int64_t)nk[0] * nk[1] * nk[2] > n) {  // rounding left too many: trim the largest
             int kmax = 0;
@@ -175,9 +191,9 @@ __global__ void __launch_bounds__(128) prep_kernel(PrepArgs a, StructRec *__rest
                 if (nk[k] > nk[kmax]) kmax = k;
             --nk[kmax];
         }
-        double visited = 1.0;
-        for (int k = 0; k < 3; ++k) visited *= fmin(1.0, (2.0 * cr * invd[k] * nk[k] + 2.0) / nk[k]);
-        if (visited < 0.5)
+        float visited = 1.f;
+        for (int k = 0; k < 3; ++k) visited *= fminf(1.0f, (2.0f * c * invd[k] * nk[k] + 2.0f) / nk[k]);
+        if (visited < 0.5f)
             for (int k = 0; k < 3; ++k) R.nb[k] = nk[k];
     }
     recs[s] = R;  // a bad structure is reported by the kernel that scans its first atom
@@ -185,9 +201,12 @@ __global__ void __launch_bounds__(128) prep_kernel(PrepArgs a, StructRec *__rest
 
 cudaError_t launch_prep(const PrepArgs &a, const Work &w, cudaStream_t s) {
     if (a.B <= 0) return cudaSuccess;
-    const int threads = 128;
-    const int blocks = (a.B * 32 + threads - 1) / threads;
-    prep_kernel<<<blocks, threads, 0, s>>>(a, w.recs, w.pos, w.atom_struct, w.tile_flags, w.queue);
+    if (a.max_atoms > 0 && a.max_atoms <= 256) {  // a warp per structure
+        const int blocks = (a.B * 32 + 127) / 128;
+        prep_kernel<32><<<blocks, 128, 0, s>>>(a, w.recs, w.pos, w.atom_struct, w.tile_flags, w.queue);
+    } else {  // a block per structure
+        prep_kernel<512><<<a.B, 512, 0, s>>>(a, w.recs, w.pos, w.atom_struct, w.tile_flags, w.queue);
+    }
     return cudaGetLastError();
 }
 

@@ -51,6 +51,7 @@ struct PrepArgs {
     int init_status;           // 1: reset the status word (first kernel of a build)
     int64_t *src_ptr;          // KNN: written here (k per atom); may be NULL otherwise
     int64_t *edge_ptr;         // KNN: written here
+    int max_atoms;             // host-known bound on atoms per structure (0: unknown)
 };
 
 cudaError_t launch_prep(const PrepArgs &a, const Work &w, cudaStream_t s);
