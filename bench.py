@@ -74,6 +74,25 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def replica_seed(config: int, rank: int) -> int:
+    """Seed of rank `rank`'s batch: structures are independent units, so every rank builds
+    its own full-size batch (weak scaling, no collective on the data path)."""
+    import synth
+    return synth.BASE_SEED + config + 1000 * rank
+
+
+def reduce_over_ranks(units: float, ms: float, device) -> tuple:
+    """Whole-job aggregate over the process group: edges summed over ranks, time the
+    slowest rank's (the only cross-rank communication of the benchmark)."""
+    import torch
+    import torch.distributed as dist
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    m = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(m.item())
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2307_05380_gb300", "csrc")
@@ -231,7 +250,7 @@ def run_mine(args, rank, world, local_rank):
         dist.init_process_group("nccl")
     wl = WORKLOADS[args.config]
     # weak scaling: every rank builds its own seeded batch of the full workload size
-    b = synth.make_batch(args.config, seed=synth.BASE_SEED + args.config + 1000 * rank)
+    b = synth.make_batch(args.config, seed=replica_seed(args.config, rank))
     batch = mg.Batch(torch.from_numpy(b.frac).to(dev), torch.from_numpy(b.lattice).to(dev),
                      torch.from_numpy(b.atom_ptr).to(dev), max_atoms=b.max_atoms)
     # the cutoff graph is symmetric: its backward needs no destination order, so the
@@ -307,12 +326,7 @@ def run_mine(args, rank, world, local_rank):
     # whole-job aggregate: all ranks' edges over the slowest rank's time
     tot_units, max_ms = units * args.steps, total_ms
     if world > 1:
-        t = torch.tensor([float(tot_units), total_ms], dtype=torch.float64, device=dev)
-        u = t[:1].clone()
-        torch.distributed.all_reduce(u, op=torch.distributed.ReduceOp.SUM)
-        m = t[1:].clone()
-        torch.distributed.all_reduce(m, op=torch.distributed.ReduceOp.MAX)
-        tot_units, max_ms = float(u.item()), float(m.item())
+        tot_units, max_ms = reduce_over_ranks(tot_units, max_ms, dev)
     value = tot_units / (max_ms / 1e3)
 
     # e2e through the public API: pinned host inputs in, results out, every step
@@ -355,10 +369,8 @@ def run_mine(args, rank, world, local_rank):
         e2e_units += u_
     h2d = (frac_h.numel() * 4 + lat_h.numel() * 4 + ptr_h.numel() * 4)
     e2e_val = e2e_units / e2e_t
-    if world > 1:
-        t = torch.tensor([e2e_val], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
-        e2e_val = float(t.item())
+    if world > 1:  # e2e throughput of the replicas adds up
+        e2e_val, _ = reduce_over_ranks(e2e_val, 0.0, dev)
 
     # plain comparison: the same kernels, one launch sequence per structure
     per_structure = None

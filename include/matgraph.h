@@ -106,8 +106,12 @@ typedef struct {
                               (candidates within band_rel*c of c are re-tested in FP64,
                               widened further to the FP32 error bound when that is larger) */
     int32_t knn_keep_ties; /* 0: exactly k.  Other values are reserved (invalid argument) */
-    int32_t schedule;      /* 0 auto (tuned), 1 flat grid, 2 persistent work queue */
+    int32_t schedule;      /* 0 auto (tuned), 1 flat grid, 2 persistent work queue (KNN) */
     int32_t collect_stats; /* 1: count FP32 candidates and FP64 re-tests into status */
+    int32_t fault_tile;    /* -1.  Testing only: the one-pass cutoff build's tile with this
+                              index never publishes its offset, so the bounded waits of the
+                              tiles after it run out and the build reports MG_ERR_TIMEOUT
+                              (edges then wrong) instead of hanging */
 } mg_opts_t;
 
 #define MG_KIND_CUTOFF 1

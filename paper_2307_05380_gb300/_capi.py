@@ -35,7 +35,7 @@ class MgGraph(ctypes.Structure):
 
 class MgOpts(ctypes.Structure):
     _fields_ = [("band_rel", c_float), ("knn_keep_ties", c_int32), ("schedule", c_int32),
-                ("collect_stats", c_int32)]
+                ("collect_stats", c_int32), ("fault_tile", c_int32)]
 
 
 # exported symbols: (name, restype, argtypes)

@@ -193,6 +193,7 @@ mg_opts_t defaults(const mg_opts_t *o) {
     d.knn_keep_ties = 0;
     d.schedule = 0;
     d.collect_stats = 0;
+    d.fault_tile = -1;
     if (o) d = *o;
     return d;
 }
@@ -268,6 +269,7 @@ mg_status_t enqueue_build(mg_context *ctx, int kind, const mg_batch_t *b, float 
     ba.atom_ptr = b->atom_ptr;
     ba.schedule = pick_schedule(ctx, kind, b, o);
     ba.collect_stats = o.collect_stats;
+    ba.fault_tile = o.fault_tile;
     ba.g = *g;
     ba.src_ptr = src_ptr;
     ba.knn_k = k;
@@ -310,7 +312,7 @@ bool same_graph(const mg_graph_t &a, const mg_graph_t &b) {
 
 bool same_opts(const mg_opts_t &a, const mg_opts_t &b) {
     return a.band_rel == b.band_rel && a.knn_keep_ties == b.knn_keep_ties && a.schedule == b.schedule &&
-           a.collect_stats == b.collect_stats;
+           a.collect_stats == b.collect_stats && a.fault_tile == b.fault_tile;
 }
 
 mg_status_t check_build_args(mg_context *ctx, const mg_batch_t *b, const mg_opts_t &o, const mg_graph_t *g) {
@@ -571,6 +573,7 @@ mg_status_t mg_build_per_structure(mg_context_t ctx, const mg_batch_t *b, int32_
         ba.atom_ptr = b->atom_ptr;
         ba.schedule = 1;
         ba.collect_stats = o.collect_stats;
+        ba.fault_tile = -1;
         ba.g = *g;
         ba.src_ptr = src_ptr;
         ba.knn_k = k;
@@ -605,6 +608,7 @@ mg_status_t mg_build_per_structure(mg_context_t ctx, const mg_batch_t *b, int32_
     fa.atom_ptr = b->atom_ptr;
     fa.schedule = 1;
     fa.collect_stats = 0;
+    fa.fault_tile = -1;
     fa.g = *g;
     fa.src_ptr = src_ptr;
     fa.knn_k = k;

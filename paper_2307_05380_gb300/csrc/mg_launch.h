@@ -83,6 +83,7 @@ struct BuildArgs {
     float band_rel;
     int atom_lo, atom_hi;      // atom row range to process (per-structure builds)
     int struct_offset;         // global index of local structure 0 (per-structure builds)
+    int fault_tile;            // testing: a one-pass build tile that never publishes (-1: none)
 };
 
 // One-pass cutoff build (batched): scan once, stage keys, look-back offsets, write.

@@ -43,8 +43,10 @@ def _ptr(t: Optional[torch.Tensor]):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
-def make_opts(band_rel: float = 1e-5, schedule: int = 0, collect_stats: bool = False) -> MgOpts:
-    return MgOpts(float(band_rel), 0, int(schedule), int(bool(collect_stats)))
+def make_opts(band_rel: float = 1e-5, schedule: int = 0, collect_stats: bool = False,
+              fault_tile: int = -1) -> MgOpts:
+    """Build options (see mg_opts_t); fault_tile is a testing hook for the bounded waits."""
+    return MgOpts(float(band_rel), 0, int(schedule), int(bool(collect_stats)), int(fault_tile))
 
 
 class Batch:

@@ -295,6 +295,19 @@ def test_update_graph_replay_tracks_geometry():
         assert_vectors(cur, got)
 
 
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A tile of the one-pass build that never publishes its offset (testing hook): the
+    look-back waits of the tiles after it give up, the status reports MG_ERR_TIMEOUT, and
+    the next build on the same context is correct."""
+    b = synth.make_batch(1)
+    batch = to_device(b)
+    g = mg.cutoff_graph(batch, 5.0, opts=mg.make_opts(fault_tile=1), sync=False)
+    st = g.read_status()
+    assert st["code"] == 6, st  # MG_ERR_TIMEOUT
+    good = graph_arrays(mg.cutoff_graph(batch, 5.0))
+    assert_same_edges(good, oracle.cutoff(b.lattice, b.frac, b.atom_ptr, 5.0), "after timeout")
+
+
 def test_stats_counters():
     b = synth.make_batch(2, B=32)
     g = mg.cutoff_graph(to_device(b), 6.0, opts=mg.make_opts(collect_stats=True))
