@@ -138,8 +138,8 @@ Layout layout(int B, int N, int64_t max_edges) {
     L.cursor = take(sizeof(int32_t) * n);
     L.tile_sum = take(sizeof(long long) * tiles);
     L.src_ptr = take(sizeof(int64_t) * (n + 1));
-    L.gpart = take(sizeof(double) * 3 * n);
-    L.lpart = take(sizeof(double) * 9 * n);
+    L.gpart = take(sizeof(float2) * 3 * n);
+    L.lpart = take(sizeof(float2) * 9 * n);
     L.queue = take(16 * sizeof(unsigned int));
     L.bin_cnt = take(sizeof(int32_t) * nbins);
     L.bin_cursor = take(sizeof(int32_t) * nbins);
@@ -165,8 +165,8 @@ Work carve(void *ws, int B, int N, int64_t max_edges) {
     w.cursor = reinterpret_cast<int32_t *>(b + L.cursor);
     w.tile_sum = reinterpret_cast<long long *>(b + L.tile_sum);
     w.src_ptr = reinterpret_cast<int64_t *>(b + L.src_ptr);
-    w.gpart = reinterpret_cast<double *>(b + L.gpart);
-    w.lpart = reinterpret_cast<double *>(b + L.lpart);
+    w.gpart = reinterpret_cast<float2 *>(b + L.gpart);
+    w.lpart = reinterpret_cast<float2 *>(b + L.lpart);
     w.queue = reinterpret_cast<unsigned int *>(b + L.queue);
     w.bin_cnt = reinterpret_cast<int32_t *>(b + L.bin_cnt);
     w.bin_cursor = reinterpret_cast<int32_t *>(b + L.bin_cursor);

@@ -6,7 +6,7 @@
 //             float-float evaluation, rounded once) and len.
 //   bwd_src   one warp per atom over its out-edges: g_e = dvec_e + dlen_e vec_e / len_e,
 //             the sum of g over out-edges and the per-atom lattice partial
-//             sum_e (x_j - x_i + t)^T g_e (FP32 lane sums, FP64 warp reduction).
+//             sum_e (x_j - x_i + t)^T g_e (FP32 lane sums, compensated warp reduction).
 //   bwd_dst   one warp per atom over its in-edges in (dst, src, t) order (perm_dst):
 //             grad_frac[j] = (sum_in g - sum_out g) L^T.
 //   bwd_lat   one warp per structure: grad_lattice = sum of the atoms' partials in
@@ -76,20 +76,80 @@ __device__ __forceinline__ float3 edge_g(const EdgeVecArgs &a, int64_t e) {
     return g;
 }
 
-__device__ __forceinline__ double warp_sum_d(double v) {
+// Compensated warp sum of one FP32 value per lane: a float-float pair (hi, lo) whose
+// sum carries the total to about 2^-44 relative, in a fixed butterfly order.  TwoSum is
+// exact and symmetric in its operands, so every lane ends with the same pair.  (GB300
+// issues FP64 at a small fraction of its FP32 rate: the reductions stay on FP32 pipes.)
+__device__ __forceinline__ float2 warp_sum_ff(float v) {
+    float hi = v, lo = 0.f;
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    return v;
+    for (int o = 16; o >= 1; o >>= 1) {
+        const float ho = __shfl_xor_sync(FULL, hi, o);
+        const float lo2 = __shfl_xor_sync(FULL, lo, o);
+        float s, e;
+        two_sum(hi, ho, s, e);
+        hi = s;
+        lo = __fadd_rn(__fadd_rn(lo, lo2), e);
+    }
+    return make_float2(hi, lo);
 }
 
-__global__ void __launch_bounds__(256) bwd_src_kernel(EdgeVecArgs a, double *__restrict__ gpart,
-                                                      double *__restrict__ lpart) {
+// (a_hi + a_lo) + (b_hi + b_lo) as a float-float pair.
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+    float s, e;
+    two_sum(a.x, b.x, s, e);
+    return make_float2(s, __fadd_rn(__fadd_rn(a.y, b.y), e));
+}
+
+__device__ __forceinline__ float2 ff_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// (sum_c g_c L[k][c]) for a float-float gradient: FP32 terms, error within a few
+// roundings of the contributions' magnitude.
+__device__ __forceinline__ float ff_times_LT(const float2 g[3], const float *L, int k) {
+    float h = __fmul_rn(g[0].x, L[3 * k + 0]);
+    h = __fmaf_rn(g[1].x, L[3 * k + 1], h);
+    h = __fmaf_rn(g[2].x, L[3 * k + 2], h);
+    h = __fmaf_rn(g[0].y, L[3 * k + 0], h);
+    h = __fmaf_rn(g[1].y, L[3 * k + 1], h);
+    return __fmaf_rn(g[2].y, L[3 * k + 2], h);
+}
+
+// Lattice partial of one edge: M[k][c] += df_k g_c with df = x_j - x_i + t carried
+// exactly, then rounded once.
+__device__ __forceinline__ void add_lattice_term(float M[9], const float xs[3], const float xd[3], const int t[3],
+                                                 float3 g) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float s1, e1, s2, e2;
+        two_sum(xd[k], -xs[k], s1, e1);
+        two_sum(s1, (float)t[k], s2, e2);
+        const float df = __fadd_rn(s2, __fadd_rn(e2, e1));
+        M[3 * k + 0] = __fmaf_rn(df, g.x, M[3 * k + 0]);
+        M[3 * k + 1] = __fmaf_rn(df, g.y, M[3 * k + 1]);
+        M[3 * k + 2] = __fmaf_rn(df, g.z, M[3 * k + 2]);
+    }
+}
+
+// Per-atom lattice partial (9 float-float pairs) from the lanes' FP32 sums.
+__device__ __forceinline__ void store_lattice_partial(float2 *__restrict__ lpart, int64_t atom, const float M[9]) {
+    const int lane = lane_id();
+    float2 r = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const float2 t = warp_sum_ff(M[q]);
+        if (lane == q) r = t;
+    }
+    if (lane < 9) lpart[9 * atom + lane] = r;
+}
+
+__global__ void __launch_bounds__(256) bwd_src_kernel(EdgeVecArgs a, float2 *__restrict__ gpart,
+                                                      float2 *__restrict__ lpart) {
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = lane_id();
     if (i >= a.N) return;
     const int64_t E = a.g.edge_ptr[a.B];
     const int64_t lo = a.g.src_ptr[i], hi = (E > a.g.capacity) ? lo : a.g.src_ptr[i + 1];
-    const float xi0 = a.frac[3 * (int64_t)i], xi1 = a.frac[3 * (int64_t)i + 1], xi2 = a.frac[3 * (int64_t)i + 2];
+    const float xi[3] = {a.frac[3 * (int64_t)i], a.frac[3 * (int64_t)i + 1], a.frac[3 * (int64_t)i + 2]};
     float gs[3] = {0.f, 0.f, 0.f};
     float M[9];
 #pragma unroll
@@ -99,42 +159,20 @@ __global__ void __launch_bounds__(256) bwd_src_kernel(EdgeVecArgs a, double *__r
         const int64_t j = a.g.dst[e];
         const int t[3] = {a.g.offset[3 * e], a.g.offset[3 * e + 1], a.g.offset[3 * e + 2]};
         const float xj[3] = {a.frac[3 * j], a.frac[3 * j + 1], a.frac[3 * j + 2]};
-        const float xi[3] = {xi0, xi1, xi2};
         gs[0] += g.x;
         gs[1] += g.y;
         gs[2] += g.z;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            // df_k = x_j - x_i + t, carried exactly then rounded once
-            float s1, e1, s2, e2;
-            two_sum(xj[k], -xi[k], s1, e1);
-            two_sum(s1, (float)t[k], s2, e2);
-            const float df = __fadd_rn(s2, __fadd_rn(e2, e1));
-            M[3 * k + 0] = __fmaf_rn(df, g.x, M[3 * k + 0]);
-            M[3 * k + 1] = __fmaf_rn(df, g.y, M[3 * k + 1]);
-            M[3 * k + 2] = __fmaf_rn(df, g.z, M[3 * k + 2]);
-        }
+        add_lattice_term(M, xi, xj, t, g);
     }
-    double r[12];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) r[q] = warp_sum_d((double)gs[q]);
-#pragma unroll
-    for (int q = 0; q < 9; ++q) r[3 + q] = warp_sum_d((double)M[q]);
-    if (lane == 0) {
-        gpart[3 * (int64_t)i + 0] = r[0];
-        gpart[3 * (int64_t)i + 1] = r[1];
-        gpart[3 * (int64_t)i + 2] = r[2];
+    for (int q = 0; q < 3; ++q) {
+        const float2 t = warp_sum_ff(gs[q]);
+        if (lane == 0) gpart[3 * (int64_t)i + q] = t;
     }
-    if (lane < 9) {
-        double v = r[3];
-#pragma unroll
-        for (int q = 1; q < 9; ++q)
-            if (lane == q) v = r[3 + q];
-        lpart[9 * (int64_t)i + lane] = v;
-    }
+    store_lattice_partial(lpart, i, M);
 }
 
-__global__ void __launch_bounds__(256) bwd_dst_kernel(EdgeVecArgs a, const double *__restrict__ gpart) {
+__global__ void __launch_bounds__(256) bwd_dst_kernel(EdgeVecArgs a, const float2 *__restrict__ gpart) {
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = lane_id();
     if (j >= a.N) return;
@@ -148,39 +186,34 @@ __global__ void __launch_bounds__(256) bwd_dst_kernel(EdgeVecArgs a, const doubl
         gs[1] += g.y;
         gs[2] += g.z;
     }
-    double tot[3];
+    float2 tot[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) tot[q] = warp_sum_d((double)gs[q]) - gpart[3 * (int64_t)j + q];
+    for (int q = 0; q < 3; ++q) tot[q] = ff_add(warp_sum_ff(gs[q]), ff_neg(gpart[3 * (int64_t)j + q]));
     if (lane < 3) {
         const int s = structure_of(a.atom_ptr, a.B, j);
-        const float *L = a.lattice + 9 * (int64_t)s;
-        // (g L^T)_k = sum_c g_c L[k][c]
-        const double h = tot[0] * (double)L[3 * lane + 0] + tot[1] * (double)L[3 * lane + 1] +
-                         tot[2] * (double)L[3 * lane + 2];
-        a.grad_frac[3 * (int64_t)j + lane] = (float)h;
+        a.grad_frac[3 * (int64_t)j + lane] = ff_times_LT(tot, a.lattice + 9 * (int64_t)s, lane);
     }
 }
 
-__global__ void __launch_bounds__(256) bwd_lat_kernel(EdgeVecArgs a, const double *__restrict__ lpart) {
+__global__ void __launch_bounds__(256) bwd_lat_kernel(EdgeVecArgs a, const float2 *__restrict__ lpart) {
     const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = lane_id();
     if (s >= a.B) return;
     const int lo = a.atom_ptr[s], hi = a.atom_ptr[s + 1];
-    double acc[9];
+    float2 acc[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) acc[q] = 0.0;
+    for (int q = 0; q < 9; ++q) acc[q] = make_float2(0.f, 0.f);
     for (int r = lo + lane; r < hi; r += 32)
 #pragma unroll
-        for (int q = 0; q < 9; ++q) acc[q] += lpart[9 * (int64_t)r + q];
+        for (int q = 0; q < 9; ++q) acc[q] = ff_add(acc[q], lpart[9 * (int64_t)r + q]);
+    float out = 0.f;
 #pragma unroll
-    for (int q = 0; q < 9; ++q) acc[q] = warp_sum_d(acc[q]);
-    if (lane < 9) {
-        double v = acc[0];
-#pragma unroll
-        for (int q = 1; q < 9; ++q)
-            if (lane == q) v = acc[q];
-        a.grad_lattice[9 * (int64_t)s + lane] = (float)v;
+    for (int q = 0; q < 9; ++q) {
+        const float2 h = warp_sum_ff(acc[q].x);
+        const float2 l = warp_sum_ff(acc[q].y);
+        if (lane == q) out = __fadd_rn(h.x, __fadd_rn(h.y, __fadd_rn(l.x, l.y)));
     }
+    if (lane < 9) a.grad_lattice[9 * (int64_t)s + lane] = out;
 }
 
 // First position in [lo, hi) of the sorted keys with key >= v (or > v when upper).
@@ -201,7 +234,7 @@ __device__ __forceinline__ int64_t key_bound(const int32_t *__restrict__ keys, i
 // the opposite offset order; s_ij its start, [rlo, rhi) the run of p in j's segment).
 // grad_frac[j] = sum_p (g_rev(p) - g_p) L^T; the lattice partial sums (x_i - x_j + t)^T g_p.
 // Fixed per-lane order and a fixed warp reduction: deterministic, no destination order.
-__global__ void __launch_bounds__(256) bwd_sym_kernel(EdgeVecArgs a, double *__restrict__ lpart) {
+__global__ void __launch_bounds__(256) bwd_sym_kernel(EdgeVecArgs a, float2 *__restrict__ lpart) {
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = lane_id();
     if (j >= a.N) return;
@@ -236,36 +269,16 @@ __global__ void __launch_bounds__(256) bwd_sym_kernel(EdgeVecArgs a, double *__r
         acc[2] += gr.z - g.z;
         const int t[3] = {a.g.offset[3 * p], a.g.offset[3 * p + 1], a.g.offset[3 * p + 2]};
         const float xi[3] = {a.frac[3 * (int64_t)i], a.frac[3 * (int64_t)i + 1], a.frac[3 * (int64_t)i + 2]};
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            float s1, e1, s2, e2;
-            two_sum(xi[k], -xj[k], s1, e1);
-            two_sum(s1, (float)t[k], s2, e2);
-            const float df = __fadd_rn(s2, __fadd_rn(e2, e1));
-            M[3 * k + 0] = __fmaf_rn(df, g.x, M[3 * k + 0]);
-            M[3 * k + 1] = __fmaf_rn(df, g.y, M[3 * k + 1]);
-            M[3 * k + 2] = __fmaf_rn(df, g.z, M[3 * k + 2]);
-        }
+        add_lattice_term(M, xj, xi, t, g);
     }
-    double r[12];
+    float2 tot[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) r[q] = warp_sum_d((double)acc[q]);
-#pragma unroll
-    for (int q = 0; q < 9; ++q) r[3 + q] = warp_sum_d((double)M[q]);
+    for (int q = 0; q < 3; ++q) tot[q] = warp_sum_ff(acc[q]);
     if (lane < 3) {
         const int s = structure_of(a.atom_ptr, a.B, j);
-        const float *L = a.lattice + 9 * (int64_t)s;
-        // (g L^T)_k = sum_c g_c L[k][c]
-        const double h = r[0] * (double)L[3 * lane + 0] + r[1] * (double)L[3 * lane + 1] + r[2] * (double)L[3 * lane + 2];
-        a.grad_frac[3 * (int64_t)j + lane] = (float)h;
+        a.grad_frac[3 * (int64_t)j + lane] = ff_times_LT(tot, a.lattice + 9 * (int64_t)s, lane);
     }
-    if (lane < 9) {
-        double v = r[3];
-#pragma unroll
-        for (int q = 1; q < 9; ++q)
-            if (lane == q) v = r[3 + q];
-        lpart[9 * (int64_t)j + lane] = v;
-    }
+    store_lattice_partial(lpart, j, M);
 }
 
 cudaError_t launch_bwd_sym(const EdgeVecArgs &a, const Work &w, cudaStream_t s) {

@@ -20,8 +20,8 @@ struct Work {
     int32_t *cursor;          // [N] scatter cursors
     long long *tile_sum;      // [n_tiles + 1] scan partials
     int64_t *src_ptr;         // [N+1] used when the graph has none
-    double *gpart;            // [N][3] source-side gradient partials
-    double *lpart;            // [N][9] per-atom lattice-gradient partials
+    float2 *gpart;            // [N][3] source-side gradient partials (float-float)
+    float2 *lpart;            // [N][9] per-atom lattice-gradient partials (float-float)
     int32_t *sort_tmp;        // [max_edges] scratch for long destination segments
     unsigned int *queue;      // [4] work-queue counters
     int32_t *bin_cnt;         // [N+B] atoms per cell-list bin
@@ -35,7 +35,7 @@ struct Work {
 };
 
 constexpr int SCAN_TILE = 4096;
-constexpr int BUILD_TILE = 4;    // source atoms per tile (one warp each) of the one-pass build
+constexpr int BUILD_TILE = 4;    // source atoms (one warp each) per look-back tile of the one-pass build
 
 struct PrepArgs {
     int B, N;
