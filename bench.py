@@ -47,7 +47,7 @@ STAGE_MODEL = {
     ("cutoff", "build"): ("hbm", 36.0, "cut"),
     ("knn", "knn"): ("hbm", 36.0, "knn"),
     ("fwd", "fwd"): ("hbm", 36.0, "cut"),
-    ("bwd", "bwd_sym"): ("hbm", 68.0, "cut"),
+    ("bwd", "bwd_sym"): ("hbm", 36.0, "cut"),
     ("bwd", "bwd_src"): ("hbm", 36.0, "cut"),
     ("bwd", "bwd_dst"): ("hbm", 24.0, "cut"),
     ("bwd", "bwd_lat"): ("hbm", 0.0, "cut"),
