@@ -11,6 +11,10 @@ What it computes (paper, Sec. 2.1):
   over an oversized, per-pair-centred box of offsets (see ``oracle.c``).
 * :func:`knn` -- the KNN special case (Sec. 2.1 after Def. 3; Algorithm 1's output):
   exactly k edges per atom, ties broken by (d2, j, t).
+* :func:`cutoff_atoms` -- Def. 3 with one cutoff c_i per atom (the source's radius decides).
+* :func:`knn` with ``keep_ties`` -- Alg. 2's filter: every image at distance <= the k-th.
+* :func:`symmetrize` -- the symmetric closure of a graph (tool list after Alg. 2).
+* :func:`triplets` -- Gamma_2 of Def. 3: pairs of edges sharing a source.
 * :func:`edge_vectors`, :func:`edge_grad` -- ``vec = (x_j - x_i + t) L``, ``len = |vec|``
   and the analytic gradient of a loss through them, edge set held fixed (Sec. 1 and
   Sec. 4: graphs updated inside a generative model's forward pass).
@@ -62,8 +66,10 @@ def _load():
         lib.oracle_cutoff.restype = ctypes.c_int
         lib.oracle_cutoff.argtypes = [ctypes.c_int, P, P, P, P, ctypes.c_int, P, ctypes.c_int64, P]
         lib.oracle_knn.restype = ctypes.c_int
-        lib.oracle_knn.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int, ctypes.c_int, P,
+        lib.oracle_knn.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
                                    ctypes.c_int64, P]
+        lib.oracle_cutoff_atoms.restype = ctypes.c_int
+        lib.oracle_cutoff_atoms.argtypes = [ctypes.c_int, P, P, P, P, ctypes.c_int, P, ctypes.c_int64, P]
         lib.oracle_edge_vectors.restype = ctypes.c_int
         lib.oracle_edge_vectors.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int64, P, P, P, P, P]
         lib.oracle_edge_grad.restype = ctypes.c_int
@@ -121,8 +127,31 @@ def cutoff(lattice, frac, atom_ptr, r, sources=None, extra: int = 0):
         lib.oracle_buf_free(buf)
 
 
-def knn(lattice, frac, atom_ptr, k: int, sources=None, extra: int = 0):
-    """KNN multigraph: exactly k edges per source atom, ties by (d2, j, t).
+def cutoff_atoms(lattice, frac, atom_ptr, radii, sources=None, extra: int = 0):
+    """Cutoff multigraph with one cutoff per atom (Def. 3 in full): (i, j, t) is an edge
+    when |(x_j - x_i + t) L| < c_i, the source's radius.  ``radii`` holds c_i for every
+    global atom row.  Returns dict(src, dst, offset, d2) in canonical order."""
+    lib = _load()
+    lat, fr, ptr = _geom(lattice, frac, atom_ptr)
+    c = np.ascontiguousarray(np.asarray(radii, np.float64).reshape(-1))
+    if c.shape[0] != fr.shape[0]:
+        raise ValueError("one radius per atom")
+    src, ns = _sources(sources)
+    buf = lib.oracle_buf_new()
+    try:
+        rc = lib.oracle_cutoff_atoms(lat.shape[0], ptr.ctypes.data, lat.ctypes.data, fr.ctypes.data,
+                                     c.ctypes.data, int(extra), None if src is None else src.ctypes.data, ns,
+                                     buf)
+        if rc:
+            raise RuntimeError(f"oracle_cutoff_atoms: {_ERRORS.get(rc, rc)}")
+        return _collect(lib, buf)
+    finally:
+        lib.oracle_buf_free(buf)
+
+
+def knn(lattice, frac, atom_ptr, k: int, sources=None, extra: int = 0, keep_ties: bool = False):
+    """KNN multigraph: exactly k edges per source atom, ties by (d2, j, t); with
+    ``keep_ties`` every image whose d2 is <= the k-th one (Alg. 2's final filter).
 
     Returns dict(src, dst, offset, d2) in canonical order."""
     lib = _load()
@@ -131,7 +160,7 @@ def knn(lattice, frac, atom_ptr, k: int, sources=None, extra: int = 0):
     buf = lib.oracle_buf_new()
     try:
         rc = lib.oracle_knn(lat.shape[0], ptr.ctypes.data, lat.ctypes.data, fr.ctypes.data, int(k),
-                            int(extra), None if src is None else src.ctypes.data, ns, buf)
+                            int(bool(keep_ties)), int(extra), None if src is None else src.ctypes.data, ns, buf)
         if rc:
             raise RuntimeError(f"oracle_knn: {_ERRORS.get(rc, rc)}")
         return _collect(lib, buf)
@@ -196,3 +225,38 @@ def pointers(src, atom_ptr):
     np.add.at(src_ptr, src + 1, 1)
     src_ptr = np.cumsum(src_ptr)
     return src_ptr[atom_ptr], src_ptr
+
+
+def symmetrize(src, dst, offset):
+    """Symmetric closure of a multigraph (the paper's tool list after Alg. 2): the input
+    edges together with every reversed edge (j, i, -t), each distinct edge once.
+    Returns dict(src, dst, offset) in canonical order (src, dst, t0, t1, t2)."""
+    s = np.asarray(src, np.int64).reshape(-1)
+    d = np.asarray(dst, np.int64).reshape(-1)
+    t = np.asarray(offset, np.int64).reshape(-1, 3)
+    edges = set()
+    for q in range(s.shape[0]):
+        e = (int(s[q]), int(d[q]), int(t[q, 0]), int(t[q, 1]), int(t[q, 2]))
+        edges.add(e)
+        edges.add((e[1], e[0], -e[2], -e[3], -e[4]))
+    out = np.array(sorted(edges), dtype=np.int64).reshape(-1, 5)
+    return dict(src=out[:, 0].astype(np.int32), dst=out[:, 1].astype(np.int32),
+                offset=out[:, 2:5].astype(np.int32))
+
+
+def triplets(src, include_self: bool = True):
+    """Gamma_2 of Def. 3 over an edge list in canonical order: every ordered pair of edge
+    ids (e, e') whose edges share a source; (e, e) is a member of the definition as
+    written and is dropped when ``include_self`` is false.  Returns dict(a, b) sorted by
+    (a, b)."""
+    s = np.asarray(src, np.int64).reshape(-1)
+    by_source = {}
+    for e in range(s.shape[0]):
+        by_source.setdefault(int(s[e]), []).append(e)
+    a, b = [], []
+    for e in range(s.shape[0]):
+        for f in by_source[int(s[e])]:
+            if include_self or e != f:
+                a.append(e)
+                b.append(f)
+    return dict(a=np.asarray(a, np.int64), b=np.asarray(b, np.int64))

@@ -16,7 +16,9 @@
  *           wrapped, so t is relative to the x given.
  *   Sec. 2.1 (after Def. 3) the KNN graph is the special case where c_i is the distance
  *           of the k-th nearest image of atom i.  Reading: exactly k edges per atom, ties
- *           broken by (d2, j, t) ascending, lexicographically, with t signed.
+ *           broken by (d2, j, t) ascending, lexicographically, with t signed.  With
+ *           keep_ties, Alg. 2's filter instead: every image whose d2 is <= the k-th d2.
+ *   Def. 3  with one cutoff per atom (oracle_cutoff_atoms): the source's own c_i decides.
  *
  * The distance that decides membership and ranking is the canonical FP64 one, written
  * out below (canon_d2): every operation rounded to nearest, no fused multiply-add
@@ -202,6 +204,33 @@ int oracle_cutoff(int B, const int32_t *atom_ptr, const double *lattice, const d
     return rc;
 }
 
+/* Cutoff graph with one radius per atom (Def. 3 in full: the condition of edge (i, j, t)
+ * uses the source's own c_i, so the graph need not be symmetric).  radius [N] holds
+ * c_i for every global atom row; other arguments and return codes as oracle_cutoff. */
+int oracle_cutoff_atoms(int B, const int32_t *atom_ptr, const double *lattice, const double *frac,
+                        const double *radius, int extra, const int32_t *sources, int64_t n_sources,
+                        void *buf) {
+    obuf_t *out = (obuf_t *)buf;
+    int32_t N = atom_ptr[B];
+    int32_t *owner = (int32_t *)malloc(sizeof(int32_t) * (N > 0 ? N : 1));
+    if (!owner) return -1;
+    atom_structure(B, atom_ptr, owner);
+    int64_t count = sources ? n_sources : N;
+    int rc = 0;
+    for (int64_t q = 0; q < count && rc == 0; ++q) {
+        int32_t a = sources ? sources[q] : (int32_t)q;
+        if (a < 0 || a >= N) { rc = -4; break; }
+        int s = owner[a];
+        const double *L = lattice + 9 * s;
+        const double *x = frac + 3 * (int64_t)atom_ptr[s];
+        int n = atom_ptr[s + 1] - atom_ptr[s];
+        if (!valid_structure(L, x, n) || !(radius[a] > 0.0) || !isfinite(radius[a])) { rc = -2; break; }
+        rc = cutoff_atom(L, x, n, a - atom_ptr[s], radius[a], extra, atom_ptr[s], out);
+    }
+    free(owner);
+    return rc;
+}
+
 /* ---------------------------------------------------------------- KNN graph */
 
 typedef struct { double d2; int32_t j; int t[3]; } cand_t;
@@ -231,7 +260,7 @@ static int jt_cmp(const void *pa, const void *pb) {
  *   2. with D the k-th d2, any image with d2 <= D lies within ceil(sqrt(D) ||L^-1||_F) + 1
  *      of the centre; if that exceeds Bx, enlarge Bx and repeat.
  * The k kept are appended in canonical order (j, t). */
-static int knn_atom(const double L[9], const double *x, int n, int i, int kk, int extra,
+static int knn_atom(const double L[9], const double *x, int n, int i, int kk, int extra, int keep_ties,
                     int32_t row0, obuf_t *out) {
     double Li[9];
     if (inverse3(L, Li) == 0.0) return -2;
@@ -265,6 +294,39 @@ static int knn_atom(const double L[9], const double *x, int n, int i, int kk, in
         if (need > Bx) { Bx = need; continue; }
         break;
     }
+    if (keep_ties) {
+        /* Alg. 2's filter: every image with d2 <= D, the k-th d2 (the box holds them all) */
+        double D = best[kk - 1].d2;
+        free(best);
+        int cap = kk, m = 0;
+        cand_t *all = (cand_t *)malloc(sizeof(cand_t) * (size_t)cap);
+        if (!all) return -1;
+        for (int j = 0; j < n; ++j) {
+            int c[3];
+            for (int k = 0; k < 3; ++k) c[k] = -(int)llround(x[3 * j + k] - x[3 * i + k]);
+            cand_t cd;
+            cd.j = j;
+            for (cd.t[0] = c[0] - Bx; cd.t[0] <= c[0] + Bx; ++cd.t[0])
+                for (cd.t[1] = c[1] - Bx; cd.t[1] <= c[1] + Bx; ++cd.t[1])
+                    for (cd.t[2] = c[2] - Bx; cd.t[2] <= c[2] + Bx; ++cd.t[2]) {
+                        if (j == i && cd.t[0] == 0 && cd.t[1] == 0 && cd.t[2] == 0) continue;
+                        cd.d2 = canon_d2(L, x + 3 * i, x + 3 * j, cd.t, NULL);
+                        if (!(cd.d2 <= D)) continue;
+                        if (m == cap) {
+                            cand_t *na = (cand_t *)realloc(all, sizeof(cand_t) * (size_t)(2 * cap));
+                            if (!na) { free(all); return -1; }
+                            all = na;
+                            cap *= 2;
+                        }
+                        all[m++] = cd;
+                    }
+        }
+        qsort(all, (size_t)m, sizeof(cand_t), jt_cmp);
+        int rc = 0;
+        for (int q = 0; q < m && rc == 0; ++q) rc = push(out, row0 + i, row0 + all[q].j, all[q].t, all[q].d2);
+        free(all);
+        return rc;
+    }
     qsort(best, (size_t)kk, sizeof(cand_t), jt_cmp);
     int rc = 0;
     for (int q = 0; q < kk && rc == 0; ++q) rc = push(out, row0 + i, row0 + best[q].j, best[q].t, best[q].d2);
@@ -272,10 +334,11 @@ static int knn_atom(const double L[9], const double *x, int n, int i, int kk, in
     return rc;
 }
 
-/* KNN graph of a batch: exactly k edges per source atom, canonical order.  Same
+/* KNN graph of a batch: exactly k edges per source atom, canonical order (keep_ties 0),
+ * or every image at distance <= the k-th one (keep_ties 1, Alg. 2's filter).  Same
  * arguments and return codes as oracle_cutoff, with k in place of the cutoffs. */
 int oracle_knn(int B, const int32_t *atom_ptr, const double *lattice, const double *frac, int k,
-               int extra, const int32_t *sources, int64_t n_sources, void *buf) {
+               int keep_ties, int extra, const int32_t *sources, int64_t n_sources, void *buf) {
     obuf_t *out = (obuf_t *)buf;
     if (k <= 0) return -4;
     int32_t N = atom_ptr[B];
@@ -292,7 +355,7 @@ int oracle_knn(int B, const int32_t *atom_ptr, const double *lattice, const doub
         const double *x = frac + 3 * (int64_t)atom_ptr[s];
         int n = atom_ptr[s + 1] - atom_ptr[s];
         if (!valid_structure(L, x, n)) { rc = -2; break; }
-        rc = knn_atom(L, x, n, a - atom_ptr[s], k, extra, atom_ptr[s], out);
+        rc = knn_atom(L, x, n, a - atom_ptr[s], k, extra, keep_ties, atom_ptr[s], out);
     }
     free(owner);
     return rc;
