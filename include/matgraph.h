@@ -105,7 +105,10 @@ typedef struct {
     float band_rel;        /* 1e-5: FP64 re-test band, relative to the cutoff distance
                               (candidates within band_rel*c of c are re-tested in FP64,
                               widened further to the FP32 error bound when that is larger) */
-    int32_t knn_keep_ties; /* 0: exactly k.  Other values are reserved (invalid argument) */
+    int32_t knn_keep_ties; /* 0: exactly k edges per atom.  1: Alg. 2's final filter, every
+                              image whose canonical d2 is <= the k-th one (ties at the k-th
+                              distance all kept, so >= k edges per atom; the capacity then
+                              works as for a cutoff graph).  Other values: invalid argument */
     int32_t schedule;      /* 0 auto (tuned), 1 flat grid, 2 persistent work queue (KNN) */
     int32_t collect_stats; /* 1: count FP32 candidates and FP64 re-tests into status */
     int32_t fault_tile;    /* -1.  Testing only: the one-pass cutoff build's tile with this
@@ -138,9 +141,22 @@ mg_status_t mg_cutoff_graph(mg_context_t ctx, const mg_batch_t *batch, float cut
                             mg_graph_t *graph, void *workspace, size_t workspace_bytes,
                             void *stream);
 
+/* Cutoff multigraph with one cutoff per atom (Def. 3 in full): every (i, j, t) with
+ * |v| < c_i, the SOURCE atom's radius (so (i, j, t) and (j, i, -t) need not both be
+ * edges), (i, i, 0) excluded; the FP64 test is d2 < (double)c_i * (double)c_i.
+ * cutoff_atom: device [N], every value finite and > 0 (else the status word reports
+ * MG_ERR_INVALID_ARGUMENT for the structure).  Outputs, capacity handling and order as
+ * mg_cutoff_graph; the graph is not symmetric, so its backward needs perm_dst. */
+mg_status_t mg_cutoff_graph_atoms(mg_context_t ctx, const mg_batch_t *batch, const float *cutoff_atom,
+                                  const mg_opts_t *opts, mg_graph_t *graph, void *workspace,
+                                  size_t workspace_bytes, void *stream);
+
 /* KNN multigraph (Alg. 1 output): exactly k edges per atom, k * N in total, so the
  * capacity needed is known up front.  Search radii start from the number density and
- * grow until the k-th distance is covered (Alg. 1's loop).  Same outputs as above. */
+ * grow until the k-th distance is covered (Alg. 1's loop).  Same outputs as above.
+ * With opts->knn_keep_ties = 1 (Alg. 2's filter, d <= d^k_i) the k-th canonical distance
+ * of every atom is found first and every image at most that far is emitted: >= k edges
+ * per atom, capacity and MG_ERR_CAPACITY as for mg_cutoff_graph. */
 mg_status_t mg_knn_graph(mg_context_t ctx, const mg_batch_t *batch, int32_t k,
                          const mg_opts_t *opts, mg_graph_t *graph, void *workspace,
                          size_t workspace_bytes, void *stream);
@@ -172,14 +188,52 @@ mg_status_t mg_edge_vectors_fwd(mg_context_t ctx, const mg_batch_t *batch, const
  *   g_e = grad_vec_e + grad_len_e * vec_e / len_e   (len_e > 0)
  *   grad_frac[j] = sum_{e: dst=j} g_e L^T - sum_{e: src=j} g_e L^T
  *   grad_lattice[s] = sum_{e in s} (x_j - x_i + t)^T g_e          (3x3)
- * Deterministic: segmented sums in canonical order (src segments, then dst segments
- * through perm_dst), no floating-point atomics.  grad_vec or grad_len may be NULL (zero);
- * vec/len are the forward outputs.  Needs src_ptr, perm_dst and dst_ptr.  Outputs
- * (device float [N][3] and [B][3][3]) are overwritten. */
+ * Deterministic: fixed-order compensated (float-float) sums, no floating-point atomics.
+ * A graph last built on this context by mg_cutoff_graph (one radius per structure) or
+ * mg_symmetrize is symmetric: the in-edge matching out-edge (j, i, t) is its reverse (i, j, -t), found in
+ * i's source segment, so only src_ptr is needed.  Every other graph is summed over src
+ * segments and over dst segments through perm_dst, so it needs src_ptr, perm_dst and
+ * dst_ptr (else MG_ERR_INVALID_ARGUMENT).  grad_vec or grad_len may be NULL (zero);
+ * vec/len are the forward outputs.  Outputs (device float [N][3] and [B][3][3]) are
+ * overwritten. */
 mg_status_t mg_edge_vectors_bwd(mg_context_t ctx, const mg_batch_t *batch, const mg_graph_t *graph,
                                 const float *grad_vec, const float *grad_len, const float *vec,
                                 const float *len, float *grad_frac, float *grad_lattice,
                                 void *workspace, size_t workspace_bytes, void *stream);
+
+/* Triplet buffers (device memory owned by the caller). */
+typedef struct {
+    int64_t capacity;           /* triplets the arrays below can hold */
+    int32_t *edge_a;            /* [capacity] first edge id e of each triplet, or NULL
+                                   (then implied by trip_ptr) */
+    int32_t *edge_b;            /* [capacity] second edge id e' */
+    int64_t *trip_ptr;          /* [E+1] triplets with first edge e: trip_ptr[e] ..
+                                   trip_ptr[e+1]-1, or NULL */
+    mg_device_status_t *status; /* num_edges = triplet count; MG_ERR_CAPACITY with
+                                   required_capacity when capacity is too small */
+} mg_triplets_t;
+
+/* Triplets of a built graph: Gamma_2 of Def. 3, the ordered pairs (e, e') of edges with
+ * the same source (the paper's tool list after Alg. 2), as ids into the graph's edge
+ * arrays.  include_self = 1 keeps (e, e) as the definition does; 0 drops it.  Order:
+ * (e, e') ascending, so source by source a deg x deg block (deg x (deg-1) without the
+ * diagonal).  Needs graph->src_ptr and at most INT32_MAX edges; reads only src_ptr.
+ * The count is sum_i deg_i * (deg_i - 1 + include_self); nothing is written past
+ * `capacity` (the status word then reports MG_ERR_CAPACITY and the exact count). */
+mg_status_t mg_triplets(mg_context_t ctx, const mg_batch_t *batch, const mg_graph_t *graph,
+                        int32_t include_self, mg_triplets_t *out, void *workspace,
+                        size_t workspace_bytes, void *stream);
+
+/* Symmetric closure of a graph (the paper's tool list after Alg. 2): every edge of `in`
+ * plus every reversed edge (j, i, -t), each distinct edge once, in canonical order.
+ * `in` must hold distinct edges in canonical order with src_ptr, perm_dst and dst_ptr
+ * (any graph this library built with a destination order).  `out` gets src, dst,
+ * offset, vec/len (if not NULL, from the batch's geometry), src_ptr (required),
+ * edge_ptr, and perm_dst/dst_ptr (if not NULL); capacity as for mg_cutoff_graph.  The
+ * result is recorded as symmetric, so mg_edge_vectors_bwd needs no perm_dst for it.
+ * The workspace must cover `in`'s capacity in edges (mg_workspace_size). */
+mg_status_t mg_symmetrize(mg_context_t ctx, const mg_batch_t *batch, const mg_graph_t *in,
+                          mg_graph_t *out, void *workspace, size_t workspace_bytes, void *stream);
 
 /* Time the available schedules for this batch shape on the caller's buffers and keep
  * the fastest per size class in the context (synchronises; results are identical for

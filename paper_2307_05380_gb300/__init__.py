@@ -6,10 +6,10 @@ Python here marshals arguments only; importing works without a GPU, while every 
 that computes needs the CUDA library (no CPU fallback).
 """
 from .graph import (Batch, EdgeVectors, Graph, autotune, build_per_structure, context, cutoff_graph,
-                    edge_vectors, edge_vectors_bwd, edge_vectors_fwd, knn_graph, last_launch_count, make_opts,
-                    profile_enable, rebuild, stage_times, update_graph)
+                    cutoff_graph_atoms, edge_vectors, edge_vectors_bwd, edge_vectors_fwd, knn_graph,
+                    last_launch_count, make_opts, profile_enable, rebuild, stage_times, update_graph)
 from ._build import build as build_library
 
-__all__ = ["Batch", "Graph", "EdgeVectors", "cutoff_graph", "knn_graph", "update_graph", "rebuild",
-           "build_per_structure", "edge_vectors", "edge_vectors_fwd", "edge_vectors_bwd", "autotune",
+__all__ = ["Batch", "Graph", "EdgeVectors", "cutoff_graph", "cutoff_graph_atoms", "knn_graph", "update_graph",
+           "rebuild", "build_per_structure", "edge_vectors", "edge_vectors_fwd", "edge_vectors_bwd", "autotune",
            "context", "last_launch_count", "make_opts", "build_library", "profile_enable", "stage_times"]

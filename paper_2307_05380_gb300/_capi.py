@@ -16,6 +16,7 @@ c_int32, c_int64, c_float, c_void_p, c_size_t = (ctypes.c_int32, ctypes.c_int64,
 MG_OK = 0
 MG_KIND_CUTOFF = 1
 MG_KIND_KNN = 2
+KIND_CUTOFF_ATOMS = 3  # binding-side tag: a cutoff graph with per-atom radii
 STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID_ARGUMENT", 2: "MG_ERR_NONFINITE_INPUT",
                 3: "MG_ERR_SINGULAR_LATTICE", 4: "MG_ERR_CAPACITY", 5: "MG_ERR_OFFSET_RANGE",
                 6: "MG_ERR_TIMEOUT", 7: "MG_ERR_CUDA", 8: "MG_ERR_WORKSPACE", 9: "MG_ERR_NOT_BUILT",
@@ -46,6 +47,8 @@ SIGNATURES = [
     ("mg_workspace_size", c_int32, [c_void_p, ctypes.POINTER(MgBatch), c_int64, ctypes.POINTER(c_size_t)]),
     ("mg_cutoff_graph", c_int32, [c_void_p, ctypes.POINTER(MgBatch), c_float, c_void_p, ctypes.POINTER(MgOpts),
                                   ctypes.POINTER(MgGraph), c_void_p, c_size_t, c_void_p]),
+    ("mg_cutoff_graph_atoms", c_int32, [c_void_p, ctypes.POINTER(MgBatch), c_void_p, ctypes.POINTER(MgOpts),
+                                        ctypes.POINTER(MgGraph), c_void_p, c_size_t, c_void_p]),
     ("mg_knn_graph", c_int32, [c_void_p, ctypes.POINTER(MgBatch), c_int32, ctypes.POINTER(MgOpts),
                                ctypes.POINTER(MgGraph), c_void_p, c_size_t, c_void_p]),
     ("mg_update_graph", c_int32, [c_void_p, ctypes.POINTER(MgBatch), ctypes.POINTER(MgGraph), c_void_p, c_size_t,

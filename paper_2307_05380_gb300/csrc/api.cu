@@ -49,6 +49,7 @@ struct Plan {
     int kind = 0;
     float cutoff = 0.f;
     const float *cutoff_ps = nullptr;
+    const float *cutoff_atom = nullptr;
     int k = 0;
     mg_opts_t opts{};
     mg_batch_t batch{};
@@ -68,6 +69,7 @@ struct mg_context {
     Prof *last_prof[4] = {};     // events of the last call of each kind
     std::mutex mu;
     std::map<const void *, Plan> plans;      // keyed by graph->src
+    std::map<const void *, mg_graph_t> sym;  // symmetric closures written here, keyed by src
     int tuned[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};  // [kind-1][size class] -> schedule
     int64_t last_launches = 0;
 };
@@ -75,6 +77,7 @@ struct mg_context {
 namespace {
 
 constexpr size_t ALIGN = 256;
+constexpr int KIND_CUTOFF_ATOMS = 3;  // plans only: a cutoff graph with per-atom radii
 
 // Stage marks: with profiling on, record the next event of `prof` (default: the
 // context's set for `which`) on the stream.
@@ -115,7 +118,7 @@ size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
     size_t recs, pos, atom_struct, cnt, cursor, tile_sum, src_ptr, gpart, lpart, queue, bin_cnt, bin_cursor,
-        cell_start, cell_fx, cell_p, atom_bin, tile_flags, sort_tmp, total;
+        cell_start, cell_fx, cell_p, atom_bin, tile_flags, rr_atom, sort_tmp, total;
 };
 
 // Workspace regions, 256-byte aligned; the edge-sized sort scratch comes last so that
@@ -148,6 +151,7 @@ Layout layout(int B, int N, int64_t max_edges) {
     L.cell_p = take(sizeof(float4) * n);
     L.atom_bin = take(sizeof(int32_t) * n);
     L.tile_flags = take(sizeof(unsigned long long) * (n / BUILD_TILE + 2));
+    L.rr_atom = take(sizeof(double) * n);
     L.sort_tmp = off;
     off += sizeof(int32_t) * (size_t)(max_edges > 0 ? max_edges : 0);
     L.total = align_up(off);
@@ -175,6 +179,7 @@ Work carve(void *ws, int B, int N, int64_t max_edges) {
     w.cell_p = reinterpret_cast<float4 *>(b + L.cell_p);
     w.atom_bin = reinterpret_cast<int32_t *>(b + L.atom_bin);
     w.tile_flags = reinterpret_cast<unsigned long long *>(b + L.tile_flags);
+    w.rr_atom = reinterpret_cast<double *>(b + L.rr_atom);
     w.sort_tmp = reinterpret_cast<int32_t *>(b + L.sort_tmp);
     w.max_edges = max_edges;
     return w;
@@ -225,7 +230,7 @@ int size_class(const mg_batch_t *b) {
 
 int pick_schedule(mg_context *ctx, int kind, const mg_batch_t *b, const mg_opts_t &o) {
     if (o.schedule == 1 || o.schedule == 2) return o.schedule;
-    const int t = ctx->tuned[kind - 1][size_class(b)];
+    const int t = ctx->tuned[kind == MG_KIND_KNN ? 1 : 0][size_class(b)];
     return t ? t : 1;
 }
 
@@ -240,19 +245,22 @@ __global__ void status_init_kernel(mg_device_status_t *st) {
 
 // The batched build's launch sequence (no host synchronisation).
 mg_status_t enqueue_build(mg_context *ctx, int kind, const mg_batch_t *b, float cutoff, const float *cutoff_ps,
-                          int k, const mg_opts_t &o, const mg_graph_t *g, void *ws, size_t ws_bytes,
-                          cudaStream_t st, int *launches, Prof *prof = nullptr) {
+                          const float *cutoff_atom, int k, const mg_opts_t &o, const mg_graph_t *g, void *ws,
+                          size_t ws_bytes, cudaStream_t st, int *launches, Prof *prof = nullptr) {
     const int B = b->num_structures, N = b->total_atoms;
     const int64_t me = ws_max_edges(B, N, ws_bytes);
     if (!ws || me < 0) return MG_ERR_WORKSPACE;
     if (g->perm_dst && me < g->capacity) return MG_ERR_WORKSPACE;  // destination sort scratch
     const Work w = carve(ws, B, N, me);
     int n = 0;
-    Marker mk(ctx, kind == MG_KIND_CUTOFF ? MG_PROF_CUTOFF : MG_PROF_KNN, st, prof);
+    const bool knn = kind == MG_KIND_KNN;
+    const bool ties = knn && o.knn_keep_ties;  // edges come from the one-pass build
+    Marker mk(ctx, knn ? MG_PROF_KNN : MG_PROF_CUTOFF, st, prof);
     int64_t *src_ptr = g->src_ptr ? g->src_ptr : w.src_ptr;
-    // prep also resets the status word and, for KNN, writes the k-per-atom pointers
-    PrepArgs pa{B, N, b->lattice, b->frac, b->atom_ptr, cutoff, cutoff_ps, kind == MG_KIND_KNN ? k : 0,
-                o.band_rel, g->status, 0, kind == MG_KIND_CUTOFF ? 1 : 0, 1, src_ptr, g->edge_ptr, b->max_atoms};
+    // prep also resets the status word and, for exact-k KNN, writes the k-per-atom pointers
+    PrepArgs pa{B, N, b->lattice, b->frac, b->atom_ptr, cutoff, cutoff_ps, knn ? k : 0, o.band_rel, g->status,
+                0, (!knn || ties) ? 1 : 0, 1, src_ptr, (knn && !ties) ? g->edge_ptr : nullptr, b->max_atoms};
+    pa.cutoff_atom = kind == KIND_CUTOFF_ATOMS ? cutoff_atom : nullptr;
     if (launch_prep(pa, w, st)) return MG_ERR_CUDA;
     ++n;
     mk.mark("prep");
@@ -276,8 +284,21 @@ mg_status_t enqueue_build(mg_context *ctx, int kind, const mg_batch_t *b, float 
     ba.band_rel = o.band_rel;
     ba.atom_lo = 0;
     ba.atom_hi = N;
-    if (kind == MG_KIND_CUTOFF) {
+    if (!knn) {
         // one pass: scan, look-back offsets, write (also src_ptr, edge_ptr, edge count)
+        if (kind == KIND_CUTOFF_ATOMS) ba.cut_atom = cutoff_atom;
+        if (launch_cutoff_build(ba, w, st)) return MG_ERR_CUDA;
+        ++n;
+        mk.mark("build");
+    } else if (ties) {
+        // the k-th canonical distance of every atom, then every image at most that far
+        ba.knn_dk = w.rr_atom;
+        if (launch_knn(ba, w, st)) return MG_ERR_CUDA;
+        n += 1 + (ba.schedule == 2);
+        mk.mark("knn");
+        ba.knn_dk = nullptr;
+        ba.rr_atom = w.rr_atom;
+        ba.inclusive = 1;
         if (launch_cutoff_build(ba, w, st)) return MG_ERR_CUDA;
         ++n;
         mk.mark("build");
@@ -321,29 +342,33 @@ mg_status_t check_build_args(mg_context *ctx, const mg_batch_t *b, const mg_opts
     if (r) return r;
     r = check_graph(g, b);
     if (r) return r;
-    if (o.knn_keep_ties != 0 || !(o.band_rel >= 0.f) || o.schedule < 0 || o.schedule > 2)
+    if (o.knn_keep_ties < 0 || o.knn_keep_ties > 1 || !(o.band_rel >= 0.f) || o.schedule < 0 || o.schedule > 2)
         return MG_ERR_INVALID_ARGUMENT;
     return MG_OK;
 }
 
 mg_status_t build_and_record(mg_context *ctx, int kind, const mg_batch_t *b, float cutoff, const float *cutoff_ps,
-                             int k, const mg_opts_t *opts, mg_graph_t *g, void *ws, size_t ws_bytes, void *stream) {
+                             const float *cutoff_atom, int k, const mg_opts_t *opts, mg_graph_t *g, void *ws,
+                             size_t ws_bytes, void *stream) {
     const mg_opts_t o = defaults(opts);
     mg_status_t r = check_build_args(ctx, b, o, g);
     if (r) return r;
     if (kind == MG_KIND_CUTOFF && !cutoff_ps && !(cutoff > 0.f)) return MG_ERR_INVALID_ARGUMENT;
+    if (kind == KIND_CUTOFF_ATOMS && !cutoff_atom && b->total_atoms > 0) return MG_ERR_INVALID_ARGUMENT;
     if (kind == MG_KIND_KNN) {
         if (k <= 0 || k > KNN_MAX_K) return MG_ERR_INVALID_ARGUMENT;
-        if ((int64_t)k * b->total_atoms > g->capacity) return MG_ERR_CAPACITY;
+        if (!o.knn_keep_ties && (int64_t)k * b->total_atoms > g->capacity) return MG_ERR_CAPACITY;
     }
     int launches = 0;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    r = enqueue_build(ctx, kind, b, cutoff, cutoff_ps, k, o, g, ws, ws_bytes, st, &launches);
+    r = enqueue_build(ctx, kind, b, cutoff, cutoff_ps, cutoff_atom, k, o, g, ws, ws_bytes, st, &launches);
     if (r) return r;
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->last_launches = launches;
+    ctx->sym.erase((const void *)g->src);
     Plan &p = ctx->plans[(const void *)g->src];
-    const bool same = p.kind == kind && p.cutoff == cutoff && p.cutoff_ps == cutoff_ps && p.k == k &&
+    const bool same = p.kind == kind && p.cutoff == cutoff && p.cutoff_ps == cutoff_ps &&
+                      p.cutoff_atom == cutoff_atom && p.k == k &&
                       same_opts(p.opts, o) && same_batch(p.batch, *b) && same_graph(p.graph, *g) && p.ws == ws &&
                       p.ws_bytes == ws_bytes;
     if (!same) {
@@ -355,6 +380,7 @@ mg_status_t build_and_record(mg_context *ctx, int kind, const mg_batch_t *b, flo
         p.kind = kind;
         p.cutoff = cutoff;
         p.cutoff_ps = cutoff_ps;
+        p.cutoff_atom = cutoff_atom;
         p.k = k;
         p.opts = o;
         p.batch = *b;
@@ -449,12 +475,19 @@ mg_status_t mg_workspace_size(mg_context_t ctx, const mg_batch_t *batch, int64_t
 
 mg_status_t mg_cutoff_graph(mg_context_t ctx, const mg_batch_t *batch, float cutoff, const float *cutoff_ps,
                             const mg_opts_t *opts, mg_graph_t *graph, void *ws, size_t ws_bytes, void *stream) {
-    return build_and_record(ctx, MG_KIND_CUTOFF, batch, cutoff, cutoff_ps, 0, opts, graph, ws, ws_bytes, stream);
+    return build_and_record(ctx, MG_KIND_CUTOFF, batch, cutoff, cutoff_ps, nullptr, 0, opts, graph, ws, ws_bytes,
+                            stream);
+}
+
+mg_status_t mg_cutoff_graph_atoms(mg_context_t ctx, const mg_batch_t *batch, const float *cutoff_atom,
+                                  const mg_opts_t *opts, mg_graph_t *graph, void *ws, size_t ws_bytes, void *stream) {
+    return build_and_record(ctx, KIND_CUTOFF_ATOMS, batch, 0.f, nullptr, cutoff_atom, 0, opts, graph, ws, ws_bytes,
+                            stream);
 }
 
 mg_status_t mg_knn_graph(mg_context_t ctx, const mg_batch_t *batch, int32_t k, const mg_opts_t *opts,
                          mg_graph_t *graph, void *ws, size_t ws_bytes, void *stream) {
-    return build_and_record(ctx, MG_KIND_KNN, batch, 0.f, nullptr, k, opts, graph, ws, ws_bytes, stream);
+    return build_and_record(ctx, MG_KIND_KNN, batch, 0.f, nullptr, nullptr, k, opts, graph, ws, ws_bytes, stream);
 }
 
 mg_status_t mg_update_graph(mg_context_t ctx, const mg_batch_t *batch, mg_graph_t *graph, void *ws, size_t ws_bytes,
@@ -474,7 +507,8 @@ mg_status_t mg_update_graph(mg_context_t ctx, const mg_batch_t *batch, mg_graph_
     if (st == nullptr || cap != cudaStreamCaptureStatusNone) {
         // legacy stream or a capture already in progress: enqueue the launches directly
         int n = 0;
-        r = enqueue_build(ctx, p.kind, batch, p.cutoff, p.cutoff_ps, p.k, p.opts, graph, ws, ws_bytes, st, &n);
+        r = enqueue_build(ctx, p.kind, batch, p.cutoff, p.cutoff_ps, p.cutoff_atom, p.k, p.opts, graph, ws,
+                          ws_bytes, st, &n);
         ctx->last_launches = n;
         return r;
     }
@@ -489,8 +523,8 @@ mg_status_t mg_update_graph(mg_context_t ctx, const mg_batch_t *batch, mg_graph_
         cudaGraph_t cg = nullptr;
         if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MG_ERR_CUDA;
         int n = 0;
-        r = enqueue_build(ctx, p.kind, batch, p.cutoff, p.cutoff_ps, p.k, p.opts, graph, ws, ws_bytes, st, &n,
-                          prof);
+        r = enqueue_build(ctx, p.kind, batch, p.cutoff, p.cutoff_ps, p.cutoff_atom, p.k, p.opts, graph, ws,
+                          ws_bytes, st, &n, prof);
         const cudaError_t ce = cudaStreamEndCapture(st, &cg);
         if (r) {
             if (cg) cudaGraphDestroy(cg);
@@ -539,6 +573,7 @@ mg_status_t mg_build_per_structure(mg_context_t ctx, const mg_batch_t *b, int32_
     mg_status_t r = check_build_args(ctx, b, o, g);
     if (r) return r;
     if (!atom_ptr_host || (kind != MG_KIND_CUTOFF && kind != MG_KIND_KNN)) return MG_ERR_INVALID_ARGUMENT;
+    if (o.knn_keep_ties) return MG_ERR_INVALID_ARGUMENT;  // the comparison build has exact-k KNN only
     if (kind == MG_KIND_CUTOFF && !(cutoff > 0.f)) return MG_ERR_INVALID_ARGUMENT;
     if (kind == MG_KIND_KNN && (k <= 0 || k > KNN_MAX_K)) return MG_ERR_INVALID_ARGUMENT;
     if (kind == MG_KIND_KNN && (int64_t)k * b->total_atoms > g->capacity) return MG_ERR_CAPACITY;
@@ -667,14 +702,18 @@ mg_status_t mg_edge_vectors_bwd(mg_context_t ctx, const mg_batch_t *b, const mg_
     if (!g || !g->src_ptr || !g->edge_ptr || !g->dst || !g->offset || !grad_frac || !grad_lattice)
         return MG_ERR_INVALID_ARGUMENT;
     if (grad_len && (!vec || !len)) return MG_ERR_INVALID_ARGUMENT;
-    // A cutoff graph built on this context is symmetric: its in-edges are found as the
-    // reverses of out-edges and no destination order is needed.  Other graphs need one.
+    // A cutoff graph built on this context with one radius per structure is symmetric:
+    // its in-edges are found as the reverses of out-edges and no destination order is
+    // needed.  Other graphs (KNN, per-atom radii, foreign edge lists) need one.
     bool symmetric = false;
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
         auto it = ctx->plans.find((const void *)g->src);
-        symmetric = it != ctx->plans.end() && it->second.kind == MG_KIND_CUTOFF && it->second.cutoff_ps == nullptr &&
-                    same_graph(it->second.graph, *g);
+        symmetric = it != ctx->plans.end() && it->second.kind == MG_KIND_CUTOFF && same_graph(it->second.graph, *g);
+        if (!symmetric) {
+            auto sit = ctx->sym.find((const void *)g->src);
+            symmetric = sit != ctx->sym.end() && same_graph(sit->second, *g);
+        }
     }
     if (!symmetric && (!g->perm_dst || !g->dst_ptr)) return MG_ERR_INVALID_ARGUMENT;
     const int B = b->num_structures, N = b->total_atoms;
@@ -715,6 +754,61 @@ mg_status_t mg_edge_vectors_bwd(mg_context_t ctx, const mg_batch_t *b, const mg_
     return MG_OK;
 }
 
+mg_status_t mg_triplets(mg_context_t ctx, const mg_batch_t *b, const mg_graph_t *g, int32_t include_self,
+                        mg_triplets_t *out, void *ws, size_t ws_bytes, void *stream) {
+    if (!ctx || !out || !out->status || !out->edge_b || out->capacity < 0 || (include_self != 0 && include_self != 1))
+        return MG_ERR_INVALID_ARGUMENT;
+    mg_status_t r = check_batch(b);
+    if (r) return r;
+    if (!g || !g->src_ptr || g->capacity > (int64_t)INT_MAX) return MG_ERR_INVALID_ARGUMENT;
+    const int B = b->num_structures, N = b->total_atoms;
+    const int64_t me = ws_max_edges(B, N, ws_bytes);
+    if (!ws || me < 0) return MG_ERR_WORKSPACE;
+    const Work w = carve(ws, B, N, me);
+    TripArgs ta{N, g->src_ptr, include_self ? 0 : 1, out->capacity, out->edge_a, out->edge_b, out->trip_ptr,
+                out->status};
+    int n = 0;
+    if (launch_triplets(ta, w, static_cast<cudaStream_t>(stream), &n)) return MG_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->last_launches = n;
+    return MG_OK;
+}
+
+mg_status_t mg_symmetrize(mg_context_t ctx, const mg_batch_t *b, const mg_graph_t *in, mg_graph_t *out, void *ws,
+                          size_t ws_bytes, void *stream) {
+    if (!ctx) return MG_ERR_INVALID_ARGUMENT;
+    mg_status_t r = check_batch(b);
+    if (r) return r;
+    if (!in || !in->src_ptr || !in->perm_dst || !in->dst_ptr || !in->src || !in->dst || !in->offset)
+        return MG_ERR_INVALID_ARGUMENT;
+    r = check_graph(out, b);
+    if (r) return r;
+    if (!out->src_ptr || out->src == in->src || out->capacity > (int64_t)INT_MAX) return MG_ERR_INVALID_ARGUMENT;
+    const int B = b->num_structures, N = b->total_atoms;
+    const int64_t me = ws_max_edges(B, N, ws_bytes);
+    if (!ws || me < 0) return MG_ERR_WORKSPACE;
+    if (me < in->capacity) return MG_ERR_WORKSPACE;  // per-edge twin counts of the input
+    const Work w = carve(ws, B, N, me);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SymArgs sa{B, N, b->lattice, b->frac, b->atom_ptr, *in, *out};
+    int n = 0;
+    if (launch_symmetrize(sa, w, st, &n)) return MG_ERR_CUDA;
+    if (out->perm_dst) {  // symmetric: destination order from reverse runs
+        BuildArgs ba;
+        ba.B = B;
+        ba.N = N;
+        ba.g = *out;
+        ba.src_ptr = out->src_ptr;
+        if (launch_dst_perm_symmetric(ba, w, st)) return MG_ERR_CUDA;
+        ++n;
+    }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->last_launches = n;
+    ctx->plans.erase((const void *)out->src);  // no longer the graph of a recorded build
+    ctx->sym[(const void *)out->src] = *out;
+    return MG_OK;
+}
+
 mg_status_t mg_cutoff_graph_noalloc(mg_context_t ctx, const mg_batch_t *b, float cutoff, const mg_opts_t *opts,
                                     mg_graph_t *g, void *stream) {
     // Same launch sequence as mg_cutoff_graph, with the fixed scratch array as workspace.
@@ -730,7 +824,7 @@ mg_status_t mg_cutoff_graph_noalloc(mg_context_t ctx, const mg_batch_t *b, float
     r = noalloc_scratch(&scratch);
     if (r) return r;
     int launches = 0;
-    r = enqueue_build(ctx, MG_KIND_CUTOFF, b, cutoff, nullptr, 0, o, g, scratch, need,
+    r = enqueue_build(ctx, MG_KIND_CUTOFF, b, cutoff, nullptr, nullptr, 0, o, g, scratch, need,
                       static_cast<cudaStream_t>(stream), &launches);
     if (r) return r;
     std::lock_guard<std::mutex> lk(ctx->mu);

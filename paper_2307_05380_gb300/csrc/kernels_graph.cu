@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(GROUP == 32 ? 128 : GROUP) prep_kernel(PrepArg
                                                                         int32_t *__restrict__ atom_struct,
                                                                         unsigned long long *__restrict__ tile_flags,
                                                                         unsigned int *__restrict__ queue) {
-    __shared__ float red[GROUP == 32 ? 1 : 4 * (GROUP / 32)];
+    __shared__ float red[GROUP == 32 ? 1 : 6 * (GROUP / 32)];
     if (a.zero_tiles) {  // the one-pass build's look-back words and tile ticket start at zero
         const int ntiles = (a.N + BUILD_TILE - 1) / BUILD_TILE + 1;
         for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x)
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(GROUP == 32 ? 128 : GROUP) prep_kernel(PrepArg
     float Lf[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) Lf[q] = a.lattice[9 * (int64_t)s + q];
-    float xm0 = 0.f, xm1 = 0.f, xm2 = 0.f, nonfinite = 0.f;
+    float xm0 = 0.f, xm1 = 0.f, xm2 = 0.f, nonfinite = 0.f, cmax = 0.f, cbad = 0.f;
     for (int r = begin + t; r < end; r += GROUP) {
         const float x0 = a.frac[3 * (int64_t)r], x1 = a.frac[3 * (int64_t)r + 1], x2 = a.frac[3 * (int64_t)r + 2];
         if (!isfinite(x0) || !isfinite(x1) || !isfinite(x2)) nonfinite = 1.f;
@@ -83,26 +83,37 @@ __global__ void __launch_bounds__(GROUP == 32 ? 128 : GROUP) prep_kernel(PrepArg
         xm0 = fmaxf(xm0, fabsf(x0));
         xm1 = fmaxf(xm1, fabsf(x1));
         xm2 = fmaxf(xm2, fabsf(x2));
+        if (a.cutoff_atom) {  // per-atom radii: the structure reaches as far as the largest
+            const float ca = a.cutoff_atom[r];
+            if (!(ca > 0.f) || !isfinite(ca)) cbad = 1.f;
+            else cmax = fmaxf(cmax, ca);
+        }
     }
     xm0 = warp_max(xm0);
     xm1 = warp_max(xm1);
     xm2 = warp_max(xm2);
     nonfinite = warp_max(nonfinite);
+    cmax = warp_max(cmax);
+    cbad = warp_max(cbad);
     if (GROUP > 32) {
         const int wid = threadIdx.x >> 5;
         if (lane_id() == 0) {
-            red[4 * wid + 0] = xm0;
-            red[4 * wid + 1] = xm1;
-            red[4 * wid + 2] = xm2;
-            red[4 * wid + 3] = nonfinite;
+            red[6 * wid + 0] = xm0;
+            red[6 * wid + 1] = xm1;
+            red[6 * wid + 2] = xm2;
+            red[6 * wid + 3] = nonfinite;
+            red[6 * wid + 4] = cmax;
+            red[6 * wid + 5] = cbad;
         }
         __syncthreads();
         if (t == 0)
             for (int q = 1; q < GROUP / 32; ++q) {
-                xm0 = fmaxf(xm0, red[4 * q + 0]);
-                xm1 = fmaxf(xm1, red[4 * q + 1]);
-                xm2 = fmaxf(xm2, red[4 * q + 2]);
-                nonfinite = fmaxf(nonfinite, red[4 * q + 3]);
+                xm0 = fmaxf(xm0, red[6 * q + 0]);
+                xm1 = fmaxf(xm1, red[6 * q + 1]);
+                xm2 = fmaxf(xm2, red[6 * q + 2]);
+                nonfinite = fmaxf(nonfinite, red[6 * q + 3]);
+                cmax = fmaxf(cmax, red[6 * q + 4]);
+                cbad = fmaxf(cbad, red[6 * q + 5]);
             }
     }
     if (t != 0) return;
@@ -140,6 +151,9 @@ __global__ void __launch_bounds__(GROUP == 32 ? 128 : GROUP) prep_kernel(PrepArg
     if (a.knn_k > 0) {
         c = 1.1f * cbrtf(3.0f * (a.knn_k + 1) * adet / (4.0f * 3.14159265f * (n > 0 ? n : 1)));
         if (!(c > 0.f) || !isfinite(c)) c = 1.0f;
+    } else if (a.cutoff_atom) {
+        c = n > 0 ? cmax : 1.0f;
+        if (!bad && cbad != 0.f) bad = MG_ERR_INVALID_ARGUMENT;
     } else {
         c = a.cutoff_ps ? a.cutoff_ps[s] : a.cutoff;
         if (!bad && (!(c > 0.f) || !isfinite(c))) bad = MG_ERR_INVALID_ARGUMENT;
@@ -160,11 +174,7 @@ __global__ void __launch_bounds__(GROUP == 32 ? 128 : GROUP) prep_kernel(PrepArg
     R.L2norm2 = Lf[6] * Lf[6] + Lf[7] * Lf[7] + Lf[8] * Lf[8];
     R.L2norm = sqrtf(R.L2norm2);
     R.rr = (double)c * (double)c;
-    {   // re-test band around the cutoff: FP32 error bound, widened to the requested band
-        const float band = fmaxf(fp32_d2_error(R, c, c * c), 2.0f * a.band_rel * c * c) * (1.0f + 1e-5f);
-        R.thr_lo = __double2float_rd(R.rr - (double)band);
-        R.thr_hi = __double2float_ru(R.rr + (double)band);
-    }
+    band_thresholds(R, c, R.rr, a.band_rel, R.thr_lo, R.thr_hi);  // re-test band around the cutoff
     R.atom_begin = begin;
     R.n_atoms = n;
     R.bad = bad;
@@ -702,8 +712,11 @@ constexpr int BUILD_CAP = 1024;  // edges of one source staged in shared memory
 // predecessors; then the edges are written from shared memory.  A source with more than
 // BUILD_CAP edges (or an offset outside the packed key) is counted in the first scan
 // and emitted by a second, canonical all-pairs scan.  Writes src_ptr, edge_ptr, the
-// edge count and the capacity check too.
+// edge count and the capacity check too.  The radius is the structure's cutoff, or per
+// source: c_i (Def. 3 with per-atom cutoffs) or an FP64 squared radius with an inclusive
+// test (Alg. 2's filter, d <= d^k_i, for keep-ties KNN graphs).
 // At most 85 registers (6 blocks of 4 warps per SM), the measured best register budget.
+template <bool PERSRC>
 __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_build_kernel(BuildArgs a, Work w) {
     __shared__ unsigned long long keys_all[BUILD_WARPS][BUILD_CAP];
     __shared__ int s_tile;
@@ -740,10 +753,20 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_build_kernel(Build
             thr_hi = R.thr_hi;
             cut = R.cut;
             rr = R.rr;
+            if (PERSRC && a.cut_atom) {  // the source's own radius c_i (Def. 3)
+                cut = a.cut_atom[i];
+                rr = (double)cut * (double)cut;
+                band_thresholds(R, cut, rr, a.band_rel, thr_lo, thr_hi);
+            } else if (PERSRC && a.rr_atom) {  // a squared radius given in FP64 (keep-ties KNN)
+                rr = a.rr_atom[i];
+                cut = __double2float_ru(sqrt(rr)) * (1.0f + 1e-6f);
+                band_thresholds(R, cut, rr, a.band_rel, thr_lo, thr_hi);
+            }
             const bool cellp = S.nb[0] != 0;
+            const bool incl = PERSRC && a.inclusive != 0;
             bool range_bad = false;
-            for_each_candidate(S, a.frac, w.pos, cells, true, R.cut, [&](bool vc, float d2, bool self, int ow,
-                                                                          int t2, const RowRegs &rw) {
+            for_each_candidate(S, a.frac, w.pos, cells, true, cut, [&](bool vc, float d2, bool self, int ow,
+                                                                        int t2, const RowRegs &rw) {
                 const bool cand = vc && !self;
                 bool in = cand && d2 < thr_lo;
                 const bool band = cand && !in && d2 <= thr_hi;
@@ -753,8 +776,9 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_build_kernel(Build
                     const int t1 = __shfl_sync(FULL, rw.t1, ow);
                     if (band) {
                         const int64_t jr = (int64_t)S.begin + jj;
-                        in = canon_d2(S.L, S.xi0, S.xi1, S.xi2, a.frac[3 * jr], a.frac[3 * jr + 1],
-                                      a.frac[3 * jr + 2], t0, t1, t2) < rr;
+                        const double d = canon_d2(S.L, S.xi0, S.xi1, S.xi2, a.frac[3 * jr], a.frac[3 * jr + 1],
+                                                  a.frac[3 * jr + 2], t0, t1, t2);
+                        in = incl ? d <= rr : d < rr;
                     }
                     if (a.collect_stats) nre += __popc(__ballot_sync(FULL, band));
                     const unsigned bal = __ballot_sync(FULL, in);
@@ -845,7 +869,10 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_build_kernel(Build
                     xj1 = a.frac[3 * jr + 1];
                     xj2 = a.frac[3 * jr + 2];
                 }
-                if (band) in = canon_d2(S.L, S.xi0, S.xi1, S.xi2, xj0, xj1, xj2, t0, t1, t2) < rr;
+                if (band) {
+                    const double d = canon_d2(S.L, S.xi0, S.xi1, S.xi2, xj0, xj1, xj2, t0, t1, t2);
+                    in = (PERSRC && a.inclusive) ? d <= rr : d < rr;
+                }
                 const unsigned bal = __ballot_sync(FULL, in);
                 if (in) {
                     const int64_t e = out + __popc(bal & lt);
@@ -862,7 +889,10 @@ cudaError_t launch_cutoff_build(const BuildArgs &a, const Work &w, cudaStream_t 
     const int atoms = a.atom_hi - a.atom_lo;
     if (atoms <= 0) return cudaSuccess;
     const int tiles = (atoms + BUILD_WARPS - 1) / BUILD_WARPS;
-    cutoff_build_kernel<<<tiles, BUILD_WARPS * 32, 0, s>>>(a, w);
+    if (a.cut_atom || a.rr_atom)
+        cutoff_build_kernel<true><<<tiles, BUILD_WARPS * 32, 0, s>>>(a, w);
+    else
+        cutoff_build_kernel<false><<<tiles, BUILD_WARPS * 32, 0, s>>>(a, w);
     return cudaGetLastError();
 }
 

@@ -15,6 +15,8 @@
 //           (d2, j, t) tie-break in a second register top-k (GB300's FP64 rate is low,
 //           so FP64 runs only when the order inside the band decides membership).  The
 //           k winners are sorted by (j, t) and written in canonical order.
+//           Keep-ties mode (Alg. 2's filter d <= d^k_i) writes only the k-th canonical
+//           d2 of each atom; the one-pass cutoff build then emits every image that close.
 // delta bounds the FP32 error (fp32_d2_error) plus the requested band.
 #include "mg_device.cuh"
 #include "mg_enum.cuh"
@@ -240,8 +242,28 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 6) knn_kernel(BuildArgs a, Wor
         }
         const int need = k - m;
         __syncwarp();
-        if (nb == need) {  // every band member fills a remaining slot
+        // the k-th canonical d2 (keep-ties mode): the largest selected band member, since
+        // every certain member lies below tau - delta and the k-th distance does not
+        unsigned long long dk_bits = 0;
+        if (nb == need && nb <= BAND_CAP) {  // every band member fills a remaining slot
             for (int q = lane; q < nb; q += 32) sel[m + q] = bl[q];
+            if (a.knn_dk) {
+                for (int q = lane; q < nb; q += 32) {
+                    const unsigned long long jt = bl[q];
+                    int t0, t1, t2;
+                    unpack_t((uint32_t)(jt & 0xffffffffull), t0, t1, t2);
+                    const int64_t jr = (int64_t)Src.begin + (int)(jt >> 32);
+                    const double d = canon_d2(Src.L, Src.xi0, Src.xi1, Src.xi2, a.frac[3 * jr], a.frac[3 * jr + 1],
+                                              a.frac[3 * jr + 2], t0, t1, t2);
+                    const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
+                    dk_bits = bits > dk_bits ? bits : dk_bits;  // non-negative: bits order like values
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long y = __shfl_xor_sync(FULL, dk_bits, o);
+                    dk_bits = y > dk_bits ? y : dk_bits;
+                }
+            }
         } else {  // rank the band by (canonical FP64 d2, j, t)
             TopK<XKey, S> ek;
             ek.init();
@@ -292,8 +314,13 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 6) knn_kernel(BuildArgs a, Wor
                 const int p = q * 32 + lane;
                 if (p < need) sel[m + p] = ek.a[q].jt;
             }
+            if (a.knn_dk) dk_bits = ek.kth(need).d;
         }
         __syncwarp();
+        if (a.knn_dk) {  // keep-ties mode: the radius only; a cutoff pass emits the edges
+            if (lane == 0) a.knn_dk[i] = __longlong_as_double((long long)dk_bits);
+            continue;
+        }
         // canonical (j, t) order of the k winners
         if (k <= 32) {
             unsigned long long v = lane < k ? sel[lane] : ~0ull;

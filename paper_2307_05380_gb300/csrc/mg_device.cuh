@@ -237,4 +237,15 @@ __device__ __forceinline__ float fp32_d2_error(const StructRec &R, float rho, fl
     return 2.0f * (3.1f * 5.9604645e-8f * dv * dv + 2.0f * dv * en + en * en) + 1e-30f;
 }
 
+// Re-test thresholds around the squared radius rr (FP64) of radius rho: FP32 d2 below
+// lo is certainly inside, above hi certainly outside, in between the FP64 test decides.
+// The band is the FP32 error bound, widened to 2 band_rel rho^2 when that is larger.
+__device__ __forceinline__ void band_thresholds(const StructRec &R, float rho, double rr, float band_rel,
+                                                float &lo, float &hi) {
+    const float r2 = rho * rho;
+    const float band = fmaxf(fp32_d2_error(R, rho, r2), 2.0f * band_rel * r2) * (1.0f + 1e-5f);
+    lo = __double2float_rd(rr - (double)band);
+    hi = __double2float_ru(rr + (double)band);
+}
+
 }  // namespace mg

@@ -31,6 +31,7 @@ struct Work {
     float4 *cell_p;           // [N] FP32 Cartesian position of each slot (bin order)
     int32_t *atom_bin;        // [N] global bin of each atom (-1: all-pairs structure)
     unsigned long long *tile_flags;  // [N/BUILD_TILE + 2] look-back words of the one-pass build
+    double *rr_atom;          // [N] per-source squared radius (keep-ties KNN: the k-th distance)
     int64_t max_edges;
 };
 
@@ -52,6 +53,7 @@ struct PrepArgs {
     int64_t *src_ptr;          // KNN: written here (k per atom); may be NULL otherwise
     int64_t *edge_ptr;         // KNN: written here
     int max_atoms;             // host-known bound on atoms per structure (0: unknown)
+    const float *cutoff_atom = nullptr;  // per-atom radii [N]: the structure's reach is their maximum
 };
 
 cudaError_t launch_prep(const PrepArgs &a, const Work &w, cudaStream_t s);
@@ -84,6 +86,11 @@ struct BuildArgs {
     int atom_lo, atom_hi;      // atom row range to process (per-structure builds)
     int struct_offset;         // global index of local structure 0 (per-structure builds)
     int fault_tile;            // testing: a one-pass build tile that never publishes (-1: none)
+    // per-source radius of the one-pass build (default: the structure's cutoff)
+    const float *cut_atom = nullptr;   // [N] radius c_i; edge iff d2 < c_i^2
+    const double *rr_atom = nullptr;   // [N] squared radius in FP64 (keep-ties KNN)
+    int inclusive = 0;                 // 1: edge iff d2 <= rr (Alg. 2's filter)
+    double *knn_dk = nullptr;          // KNN: write the k-th canonical d2 per atom, no edges
 };
 
 // One-pass cutoff build (batched): scan once, stage keys, look-back offsets, write.
@@ -114,6 +121,27 @@ cudaError_t launch_bwd_sym(const EdgeVecArgs &a, const Work &w, cudaStream_t s);
 cudaError_t launch_bwd_src(const EdgeVecArgs &a, const Work &w, cudaStream_t s);
 cudaError_t launch_bwd_dst(const EdgeVecArgs &a, const Work &w, cudaStream_t s);
 cudaError_t launch_bwd_lat(const EdgeVecArgs &a, const Work &w, cudaStream_t s);
+
+// Triplets (Gamma_2): ordered pairs of edges with a common source, as edge ids.
+struct TripArgs {
+    int N;
+    const int64_t *src_ptr;    // [N+1] CSR by source of the graph
+    int excl;                  // 1: leave out (e, e)
+    int64_t capacity;
+    int32_t *edge_a, *edge_b;  // [capacity]; edge_a may be NULL
+    int64_t *trip_ptr;         // [E+1] CSR by first edge, or NULL
+    mg_device_status_t *status;
+};
+cudaError_t launch_triplets(const TripArgs &a, const Work &w, cudaStream_t s, int *launches);
+
+// Symmetric closure of a graph (needs its destination order).
+struct SymArgs {
+    int B, N;
+    const float *lattice, *frac;
+    const int32_t *atom_ptr;
+    mg_graph_t in, out;
+};
+cudaError_t launch_symmetrize(const SymArgs &a, const Work &w, cudaStream_t s, int *launches);
 
 int num_sms();
 

@@ -44,9 +44,9 @@ def _ptr(t: Optional[torch.Tensor]):
 
 
 def make_opts(band_rel: float = 1e-5, schedule: int = 0, collect_stats: bool = False,
-              fault_tile: int = -1) -> MgOpts:
+              fault_tile: int = -1, keep_ties: bool = False) -> MgOpts:
     """Build options (see mg_opts_t); fault_tile is a testing hook for the bounded waits."""
-    return MgOpts(float(band_rel), 0, int(schedule), int(bool(collect_stats)), int(fault_tile))
+    return MgOpts(float(band_rel), int(bool(keep_ties)), int(schedule), int(bool(collect_stats)), int(fault_tile))
 
 
 class Batch:
@@ -115,6 +115,7 @@ class Graph:
     status: torch.Tensor
     ws: torch.Tensor
     opts: MgOpts
+    radii: Optional[torch.Tensor] = None  # per-atom cutoffs (KIND_CUTOFF_ATOMS)
     num_edges: int = -1
     last_status: dict = field(default_factory=dict)
     _c: Optional[MgGraph] = None
@@ -185,6 +186,10 @@ def _launch_build(g: Graph, per_structure: bool = False, atom_ptr_host=None):
         rc = lib.mg_cutoff_graph(ctx, ctypes.byref(g.batch.c), float(g.cutoff), None, ctypes.byref(g.opts),
                                  ctypes.byref(g.c), _ptr(g.ws), g.ws.numel(), st)
         _capi.check(rc, "mg_cutoff_graph")
+    elif g.kind == _capi.KIND_CUTOFF_ATOMS:
+        rc = lib.mg_cutoff_graph_atoms(ctx, ctypes.byref(g.batch.c), _ptr(g.radii), ctypes.byref(g.opts),
+                                       ctypes.byref(g.c), _ptr(g.ws), g.ws.numel(), st)
+        _capi.check(rc, "mg_cutoff_graph_atoms")
     else:
         rc = lib.mg_knn_graph(ctx, ctypes.byref(g.batch.c), int(g.k), ctypes.byref(g.opts), ctypes.byref(g.c),
                               _ptr(g.ws), g.ws.numel(), st)
@@ -201,21 +206,25 @@ def _finish(g: Graph, sync: bool) -> Graph:
     return g
 
 
-def _build(kind, batch: Batch, cutoff, k, capacity, with_vectors, with_perm, opts, sync, per_structure=False):
+def _build(kind, batch: Batch, cutoff, k, capacity, with_vectors, with_perm, opts, sync, per_structure=False,
+           radii=None):
     if opts is None:
         opts = make_opts()
     atom_ptr_host = batch.atom_ptr.cpu().tolist() if per_structure else None
-    if kind == _capi.MG_KIND_KNN:
+    exact_k = kind == _capi.MG_KIND_KNN and not opts.knn_keep_ties
+    if exact_k:
         capacity = int(k) * batch.N
     elif capacity is None:
-        capacity = 64 * batch.N + 1024
+        capacity = (2 * int(k) * batch.N + 1024) if kind == _capi.MG_KIND_KNN else 64 * batch.N + 1024
     g = _alloc_graph(kind, batch, cutoff, k, capacity, with_vectors, with_perm, opts)
+    g.radii = radii
     _launch_build(g, per_structure, atom_ptr_host)
     if not sync:
         return g
     st = g.read_status()
-    if st["code"] == 4 and kind == _capi.MG_KIND_CUTOFF:  # MG_ERR_CAPACITY: exact size known now
+    if st["code"] == 4 and not exact_k:  # MG_ERR_CAPACITY: exact size known now
         g = _alloc_graph(kind, batch, cutoff, k, st["required_capacity"], with_vectors, with_perm, opts)
+        g.radii = radii
         _launch_build(g, per_structure, atom_ptr_host)
     return _finish(g, True)
 
@@ -227,9 +236,25 @@ def cutoff_graph(batch: Batch, cutoff: float, *, capacity: Optional[int] = None,
     return _build(_capi.MG_KIND_CUTOFF, batch, cutoff, 0, capacity, with_vectors, with_perm, opts, sync)
 
 
+def cutoff_graph_atoms(batch: Batch, radii: torch.Tensor, *, capacity: Optional[int] = None,
+                       with_vectors: bool = True, with_perm: bool = True, opts: Optional[MgOpts] = None,
+                       sync: bool = True) -> Graph:
+    """Cutoff multigraph with one cutoff per atom (Def. 3 in full): every (i, j, t) with
+    |(x_j - x_i + t) L| < radii[i], (i, i, 0) excluded.  radii: float32 [N] on the device."""
+    if radii.dtype != torch.float32 or radii.device != batch.device or radii.numel() != batch.N:
+        raise ValueError("radii must be float32 [N] on the batch's device")
+    radii = radii.contiguous()
+    return _build(_capi.KIND_CUTOFF_ATOMS, batch, 0.0, 0, capacity, with_vectors, with_perm, opts, sync,
+                  radii=radii)
+
+
 def knn_graph(batch: Batch, k: int, *, with_vectors: bool = True, with_perm: bool = True,
-              opts: Optional[MgOpts] = None, sync: bool = True) -> Graph:
-    """KNN multigraph: exactly k edges per atom, ties by (distance, j, t)."""
+              opts: Optional[MgOpts] = None, sync: bool = True, keep_ties: bool = False) -> Graph:
+    """KNN multigraph: exactly k edges per atom, ties by (distance, j, t); with keep_ties
+    every image at most as far as the k-th (Alg. 2's filter, >= k edges per atom)."""
+    if keep_ties:
+        opts = opts or make_opts()
+        opts = MgOpts(opts.band_rel, 1, opts.schedule, opts.collect_stats, opts.fault_tile)
     return _build(_capi.MG_KIND_KNN, batch, 0.0, k, None, with_vectors, with_perm, opts, sync)
 
 

@@ -57,3 +57,40 @@ def pointers_ok(got, b):
     edge_ptr, src_ptr = oracle.pointers(got["src"], b.atom_ptr)
     np.testing.assert_array_equal(got["edge_ptr"], edge_ptr)
     np.testing.assert_array_equal(got["src_ptr"], src_ptr)
+
+
+def grad_check(b, g, w, sigma=1.5):
+    """Autograd through the library's edge vectors for a Gaussian edge loss, against the
+    oracle's analytic gradient within a condition-aware bound (1e-5 of the summed
+    magnitudes of the contributions).  Returns the two gradients."""
+    import torch
+
+    import paper_2307_05380_gb300 as mg
+    batch = g.batch
+    frac = batch.frac.clone().requires_grad_(True)
+    lat = batch.lattice.clone().requires_grad_(True)
+    vec, ln = mg.edge_vectors(frac, lat, g)
+    wt = torch.from_numpy(w).to(batch.device)
+    loss = (wt * torch.exp(-ln ** 2 / (2 * sigma ** 2))).sum()
+    loss.backward()
+    got = graph_arrays(g)
+    ov, ol = oracle.edge_vectors(b.lattice, b.frac, b.atom_ptr, got["src"], got["dst"], got["offset"])
+    _, dlen = oracle.gaussian_loss_grads(ov, ol, w, sigma)
+    gf, gL = oracle.edge_grad(b.lattice, b.frac, b.atom_ptr, got["src"], got["dst"], got["offset"], None, dlen)
+    # condition-aware bound: 1e-5 of the summed magnitudes of the contributions
+    gabs = np.abs(dlen)[:, None] * np.ones((1, 3))
+    scale_f = np.zeros_like(gf)
+    Lt = np.abs(b.lattice.astype(np.float64))
+    atom_s = np.repeat(np.arange(b.num_structures), np.diff(b.atom_ptr))
+    # |g_e| L^T magnitudes per edge and component (|dLoss/dlen| bounds |g_e| componentwise)
+    h = np.einsum("ec,ekc->ek", gabs, Lt[atom_s[got["src"]]])
+    np.add.at(scale_f, got["src"], h)
+    np.add.at(scale_f, got["dst"], h)
+    err_f = np.abs(frac.grad.cpu().numpy() - gf)
+    assert np.all(err_f <= 1e-5 * scale_f + 1e-12), err_f.max()
+    df = (b.frac[got["dst"]].astype(np.float64) - b.frac[got["src"]] + got["offset"])
+    scale_L = np.zeros((b.num_structures, 3, 3))
+    np.add.at(scale_L, atom_s[got["src"]], np.abs(df)[:, :, None] * gabs[:, None, :])
+    err_L = np.abs(lat.grad.cpu().numpy() - gL)
+    assert np.all(err_L <= 1e-5 * scale_L + 1e-12), err_L.max()
+    return frac.grad.clone(), lat.grad.clone()

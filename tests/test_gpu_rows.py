@@ -1,0 +1,173 @@
+"""GPU parity for the rows after the hot path: per-atom cutoffs and keep-ties KNN graphs
+(Def. 3 in full; Alg. 2's filter), against the FP64 oracle through the C-ABI library.
+
+Edge sets bit-exact in canonical order; vec/len within 1e-6 relative; destination order
+and gradients as for the constant-cutoff graph.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import (assert_perm_dst, assert_same_edges, assert_vectors, grad_check, graph_arrays, pointers_ok,
+                     to_device)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2307_05380_gb300 as mg  # noqa: E402
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "next_rows.json")))
+
+
+def radii_for(b, seed, lo, hi):
+    """Seeded per-atom radii, uniform in [lo, hi)."""
+    return np.random.default_rng(seed).uniform(lo, hi, b.total_atoms).astype(np.float32)
+
+
+def atoms_parity(b, radii, **kw):
+    batch = to_device(b)
+    g = mg.cutoff_graph_atoms(batch, torch.from_numpy(radii).cuda(), **kw)
+    got = graph_arrays(g)
+    want = oracle.cutoff_atoms(b.lattice, b.frac, b.atom_ptr, radii.astype(np.float64))
+    assert_same_edges(got, want, "per-atom cutoff")
+    pointers_ok(got, b)
+    if g.vec is not None:
+        assert_vectors(b, got)
+    if g.perm_dst is not None:
+        assert_perm_dst(got, b.total_atoms)
+    return g, got
+
+
+def ties_parity(b, k, **kw):
+    g = mg.knn_graph(to_device(b), k, keep_ties=True, **kw)
+    got = graph_arrays(g)
+    want = oracle.knn(b.lattice, b.frac, b.atom_ptr, k, keep_ties=True)
+    assert_same_edges(got, want, f"keep-ties knn k={k}")
+    pointers_ok(got, b)
+    if g.vec is not None:
+        assert_vectors(b, got)
+    if g.perm_dst is not None:
+        assert_perm_dst(got, b.total_atoms)
+    return g, got
+
+
+# ------------------------------------------------------------------ per-atom cutoffs
+
+def test_per_atom_cutoff_closed_forms_on_gpu():
+    d = GOLD["per_atom_cutoff_sc_pair"]
+    b = synth.crystal(d["lattice"], d["frac"])
+    for radii, degs in d["cases"]:  # radius 1.0 sits exactly on a shell: strict inequality
+        g = mg.cutoff_graph_atoms(to_device(b), torch.tensor(radii, dtype=torch.float32, device="cuda"))
+        got = graph_arrays(g)
+        assert np.bincount(got["src"], minlength=2).tolist() == degs
+
+
+@pytest.mark.parametrize("cfg,lo,hi", [(1, 2.0, 6.0), (2, 3.0, 7.0), (4, 2.5, 6.0)])
+def test_per_atom_cutoff_full_batches(cfg, lo, hi):
+    b = synth.make_batch(cfg, B=None if cfg == 1 else 96)
+    atoms_parity(b, radii_for(b, cfg, lo, hi))
+
+
+def test_per_atom_cutoff_cell_list_sources():
+    """Two supercells (cell-list path, thousands of atoms) against the oracle on a sample
+    of sources: every edge of each sampled source, in canonical order."""
+    b = synth.make_batch(5).subset([0, 1])
+    radii = radii_for(b, 5, 5.0, 8.0)
+    g = mg.cutoff_graph_atoms(to_device(b), torch.from_numpy(radii).cuda(), with_perm=False)
+    got = graph_arrays(g)
+    rng = np.random.default_rng(5)
+    srcs = np.sort(rng.choice(b.total_atoms, 64, replace=False)).astype(np.int32)
+    want = oracle.cutoff_atoms(b.lattice, b.frac, b.atom_ptr, radii.astype(np.float64), sources=srcs)
+    sel = np.concatenate([np.arange(got["src_ptr"][s], got["src_ptr"][s + 1]) for s in srcs])
+    part = {k: got[k][sel] for k in ("src", "dst", "offset", "vec", "len")}
+    assert_same_edges(part, want, "cell-list sources")
+    assert_vectors(b, part)
+    assert got["src_ptr"][-1] == g.num_edges
+
+
+def test_per_atom_cutoff_equal_radii_is_the_constant_cutoff_graph():
+    b = synth.make_batch(2, B=64)
+    batch = to_device(b)
+    ga = mg.cutoff_graph_atoms(batch, torch.full((b.total_atoms,), 6.0, device="cuda"))
+    gc = mg.cutoff_graph(batch, 6.0)
+    a, c = graph_arrays(ga), graph_arrays(gc)
+    for key in ("src", "dst", "offset", "vec", "len", "edge_ptr", "src_ptr", "perm_dst", "dst_ptr"):
+        np.testing.assert_array_equal(a[key], c[key], err_msg=key)
+
+
+def test_per_atom_cutoff_gradients_through_destination_order():
+    b = synth.make_batch(4, B=48)
+    g, _ = atoms_parity(b, radii_for(b, 44, 3.0, 6.0))
+    w = synth.normal(4, 2, g.num_edges)
+    g1 = grad_check(b, g, w)
+    g2 = grad_check(b, g, w)
+    assert torch.equal(g1[0], g2[0]) and torch.equal(g1[1], g2[1])
+
+
+def test_per_atom_cutoff_bad_radius_reported():
+    b = synth.make_batch(1)
+    radii = np.full(b.total_atoms, 4.0, np.float32)
+    radii[int(b.atom_ptr[3]) + 1] = -1.0
+    batch = to_device(b)
+    with pytest.raises(RuntimeError, match="INVALID_ARGUMENT"):
+        mg.cutoff_graph_atoms(batch, torch.from_numpy(radii).cuda())
+    radii[int(b.atom_ptr[3]) + 1] = float("nan")
+    with pytest.raises(RuntimeError, match="structure 3"):
+        mg.cutoff_graph_atoms(batch, torch.from_numpy(radii).cuda())
+
+
+def test_per_atom_cutoff_update_replay():
+    b = synth.make_batch(4, B=32)
+    batch = to_device(b)
+    radii = torch.from_numpy(radii_for(b, 9, 3.0, 5.0)).cuda()
+    g = mg.cutoff_graph_atoms(batch, radii, capacity=200 * b.total_atoms)
+    moved = synth.perturb(b, 9, 1)
+    batch.frac.copy_(torch.from_numpy(moved.frac).cuda())
+    batch.lattice.copy_(torch.from_numpy(moved.lattice).cuda())
+    for _ in range(2):
+        mg.update_graph(g)
+        got = graph_arrays(g)
+        want = oracle.cutoff_atoms(moved.lattice, moved.frac, moved.atom_ptr,
+                                   radii.cpu().numpy().astype(np.float64))
+        assert_same_edges(got, want, "per-atom replay")
+
+
+# ------------------------------------------------------------------ keep-ties KNN
+
+@pytest.mark.parametrize("name", ["knn_keep_ties_sc", "knn_keep_ties_fcc", "knn_keep_ties_bcc"])
+def test_keep_ties_closed_forms_on_gpu(name):
+    d = GOLD[name]
+    L = np.asarray(d.get("lattice_over_a", np.eye(3)), float) * 3.0
+    b = synth.crystal(L, [[0, 0, 0]])
+    for k, m in d["cases"]:
+        g, got = ties_parity(b, k)
+        assert g.num_edges == m, (name, k)
+
+
+def test_keep_ties_perfect_supercell_many_ties():
+    L = np.eye(3) * 2.0
+    x = [[a, b_, c] for a in (0, .5) for b_ in (0, .5) for c in (0, .5)]
+    b = synth.concat([synth.crystal(L, x), synth.crystal(np.diag([3.0, 3.0, 4.0]), [[0, 0, 0], [.5, .5, .5]])])
+    for k in (1, 6, 7, 19, 33, 100):
+        ties_parity(b, k)
+
+
+@pytest.mark.parametrize("cfg,k", [(1, 12), (2, 16), (3, 8)])
+def test_keep_ties_batches(cfg, k):
+    b = synth.make_batch(cfg, B=None if cfg == 1 else 96)
+    g, got = ties_parity(b, k)
+    # with generic coordinates the only ties are an atom's own images t and -t
+    assert g.num_edges >= k * b.total_atoms
+
+
+def test_keep_ties_gradients():
+    b = synth.make_batch(2, B=32)
+    g, _ = ties_parity(b, 16)
+    grad_check(b, g, synth.normal(6, 1, g.num_edges))
