@@ -2,16 +2,18 @@
 """Benchmark of the batched periodic-graph hot path on GB300.
 
 One step = the whole path over one batch: the cutoff multigraph build (prep,
-interplanar-box FP32 scan with FP64 re-test, count / scan / write, destination sort),
-the KNN build (adaptive radius, register top-k, FP64 re-rank) and the edge-vector
-forward and backward passes on the cutoff graph.  Both builds replay their captured
-CUDA-graph plans (mg_update_graph).  Units are edges built per step (cutoff + KNN).
+interplanar-box FP32 scan with FP64 re-test, one-pass write with a decoupled look-back),
+the KNN build (adaptive radius, register top-k, FP64 re-rank, destination order) and the
+edge-vector forward and backward passes on the cutoff graph.  Both builds replay their
+captured CUDA-graph plans (mg_update_graph).  Units are edges built per step (cutoff +
+KNN).
 
 Default workload: 256 synthetic structures with 1..64 atoms (log-uniform), lengths
 U[2.5,12] A, angles U[50,130] deg, 0.9 A separation; cutoff 6 A, k = 16.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
-Prints one JSON line (rank 0).
+Prints one JSON line (rank 0).  With --sweep: the batch-size sweep of the KNN k = 32
+build (Table 2's shape), one JSON line per batch size.
 """
 from __future__ import annotations
 
@@ -67,6 +69,7 @@ def parse_args():
     p.add_argument("--impl", default="mine", choices=["mine", "reference"])
     p.add_argument("--config", type=int, default=2, choices=sorted(WORKLOADS))
     p.add_argument("--no-baselines", action="store_true", help="skip the CPU oracle and per-structure legs")
+    p.add_argument("--sweep", action="store_true", help="batch-size sweep of the KNN k=32 build")
     return p.parse_args()
 
 
@@ -457,11 +460,64 @@ def run_mine(args, rank, world, local_rank):
     return 0
 
 
+SWEEP_BATCHES = (32, 64, 128, 256, 512)
+SWEEP_K = 32
+DATASET_STRUCTURES = 119701  # structures of the paper's filtered dataset (Sec. 3)
+
+
+def run_sweep(args, local_rank):
+    """Time of one KNN k=32 build per batch size (plan replay, L2 flushed between
+    batches) and the device memory it holds (workspace + graph buffers), on batches of
+    the default workload's recipe; the dataset column scales the batch time to the
+    paper's structure count (Table 2's columns, synthetic stand-in)."""
+    import torch
+
+    import paper_2307_05380_gb300 as mg
+    import synth
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    steps = max(5, min(args.steps, 200))
+    for B in SWEEP_BATCHES:
+        b = synth.make_batch(2, B=B)
+        batch = mg.Batch(torch.from_numpy(b.frac).to(dev), torch.from_numpy(b.lattice).to(dev),
+                         torch.from_numpy(b.atom_ptr).to(dev), max_atoms=b.max_atoms)
+        g = mg.knn_graph(batch, SWEEP_K, with_perm=False)
+        held = g.ws.numel() + sum(t.numel() * t.element_size() for t in
+                                  (g.src, g.dst, g.offset, g.vec, g.len, g.edge_ptr, g.src_ptr, g.status))
+        for _ in range(max(3, args.warmup)):
+            mg.update_graph(g, sync=False)
+        ms = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(steps):
+            flush.zero_()
+            e0.record(stream)
+            mg.update_graph(g, sync=False)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = g.read_status()
+        assert st["code"] == 0, st
+        t = statistics.median(ms)
+        print(json.dumps({"sweep": f"knn k={SWEEP_K} batch size", "batch": B, "atoms": b.total_atoms,
+                          "edges": g.num_edges, "ms_per_batch": t, "structures_per_s": B / t * 1e3,
+                          "edges_per_s": g.num_edges / t * 1e3, "device_bytes": int(held),
+                          "dataset_s": DATASET_STRUCTURES / B * t / 1e3, "steps": steps,
+                          "timing": "CUDA events around each plan replay, median; L2 flushed between batches"}),
+              flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     rank, world, local_rank = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank)
+    if args.sweep:
+        return run_sweep(args, local_rank) if rank == 0 else 0
     return run_mine(args, rank, world, local_rank)
 
 

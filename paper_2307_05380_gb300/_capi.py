@@ -34,6 +34,11 @@ class MgGraph(ctypes.Structure):
                 ("perm_dst", c_void_p), ("dst_ptr", c_void_p), ("status", c_void_p)]
 
 
+class MgTriplets(ctypes.Structure):
+    _fields_ = [("capacity", c_int64), ("edge_a", c_void_p), ("edge_b", c_void_p), ("trip_ptr", c_void_p),
+                ("status", c_void_p)]
+
+
 class MgOpts(ctypes.Structure):
     _fields_ = [("band_rel", c_float), ("knn_keep_ties", c_int32), ("schedule", c_int32),
                 ("collect_stats", c_int32), ("fault_tile", c_int32)]
@@ -66,6 +71,10 @@ SIGNATURES = [
     ("mg_last_launch_count", c_int64, [c_void_p]),
     ("mg_cutoff_graph_noalloc", c_int32, [c_void_p, ctypes.POINTER(MgBatch), c_float, ctypes.POINTER(MgOpts),
                                           ctypes.POINTER(MgGraph), c_void_p]),
+    ("mg_triplets", c_int32, [c_void_p, ctypes.POINTER(MgBatch), ctypes.POINTER(MgGraph), c_int32,
+                              ctypes.POINTER(MgTriplets), c_void_p, c_size_t, c_void_p]),
+    ("mg_symmetrize", c_int32, [c_void_p, ctypes.POINTER(MgBatch), ctypes.POINTER(MgGraph),
+                                ctypes.POINTER(MgGraph), c_void_p, c_size_t, c_void_p]),
     ("mg_profile_enable", c_int32, [c_void_p, c_int32]),
     ("mg_stage_times", c_int32, [c_void_p, c_int32, c_int32, ctypes.POINTER(ctypes.c_char_p),
                                  ctypes.POINTER(c_float)]),

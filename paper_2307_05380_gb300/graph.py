@@ -14,7 +14,7 @@ from typing import Optional
 import torch
 
 from . import _capi
-from ._capi import MgBatch, MgGraph, MgOpts
+from ._capi import MgBatch, MgGraph, MgOpts, MgTriplets
 
 _CTX: dict = {}
 
@@ -323,6 +323,79 @@ def autotune(batch: Batch, kind: str, cutoff: float = 0.0, k: int = 0, capacity=
     rc = _capi.load().mg_autotune(context(batch.device), ctypes.byref(batch.c), kd, float(cutoff), int(k),
                                   ctypes.byref(g.c), _ptr(g.ws), g.ws.numel(), _stream(batch.device))
     _capi.check(rc, "mg_autotune")
+
+
+# ---------------------------------------------------------------------------- graph operations
+
+@dataclass
+class Triplets:
+    """Gamma_2 of a graph: triplet q pairs edge edge_a[q] with edge edge_b[q] (same source);
+    the triplets whose first edge is e are trip_ptr[e] .. trip_ptr[e+1]-1."""
+    count: int
+    edge_a: Optional[torch.Tensor]
+    edge_b: torch.Tensor
+    trip_ptr: torch.Tensor
+
+
+def triplets(g: Graph, include_self: bool = True, with_edge_a: bool = True,
+             capacity: Optional[int] = None) -> Triplets:
+    """Ordered pairs (e, e') of edges with a common source (Def. 3's Gamma_2), as edge ids
+    in canonical order; include_self keeps (e, e).  Synchronises to size the output."""
+    batch = g.batch
+    dev = batch.device
+    if g.num_edges < 0:
+        raise RuntimeError("graph has no synchronised build")
+    E = g.num_edges
+    lib = _capi.load()
+    ctx = context(dev)
+    st = _stream(dev)
+    status = torch.zeros(5, dtype=torch.int64, device=dev)
+    trip_ptr = torch.empty(E + 1, dtype=torch.int64, device=dev)
+    nbytes = ctypes.c_size_t(0)
+    _capi.check(lib.mg_workspace_size(ctx, ctypes.byref(batch.c), 0, ctypes.byref(nbytes)), "mg_workspace_size")
+    ws = torch.empty(int(nbytes.value), dtype=torch.uint8, device=dev)
+    if capacity is None:  # sum of squared degrees >= E^2 / N
+        capacity = int(1.25 * E * E / max(batch.N, 1)) + 1024
+    for _ in range(2):
+        a = torch.empty(capacity, dtype=torch.int32, device=dev) if with_edge_a else None
+        b = torch.empty(capacity, dtype=torch.int32, device=dev)
+        out = MgTriplets(int(capacity), _ptr(a), b.data_ptr(), trip_ptr.data_ptr(), status.data_ptr())
+        _capi.check(lib.mg_triplets(ctx, ctypes.byref(batch.c), ctypes.byref(g.c), int(bool(include_self)),
+                                    ctypes.byref(out), ws.data_ptr(), ws.numel(), st), "mg_triplets")
+        raw = status.cpu()
+        code = int(raw[0].item() & 0xFFFFFFFF)
+        T = int(raw[1])
+        if code == 4:  # MG_ERR_CAPACITY: the exact count is known now
+            capacity = max(T, 1)
+            continue
+        if code:
+            raise RuntimeError(f"mg_triplets failed: {_capi.status_name(code)}")
+        return Triplets(T, a[:T] if a is not None else None, b[:T], trip_ptr)
+    raise RuntimeError("mg_triplets: capacity retry failed")
+
+
+def symmetrize(g: Graph, *, with_vectors: bool = True, with_perm: bool = True,
+               capacity: Optional[int] = None) -> Graph:
+    """Symmetric closure of a graph built with a destination order (tool list after
+    Alg. 2): its edges plus every reversed edge (j, i, -t), each once, canonical order."""
+    if g.perm_dst is None or g.num_edges < 0:
+        raise ValueError("symmetrize needs a synchronised graph built with with_perm=True")
+    batch = g.batch
+    lib = _capi.load()
+    ctx = context(batch.device)
+    st = _stream(batch.device)
+    cap = capacity or max(2 * g.num_edges, 1)
+    for _ in range(2):
+        out = _alloc_graph(g.kind, batch, g.cutoff, g.k, cap, with_vectors, with_perm, g.opts,
+                           ws_edges=max(g.capacity, cap))
+        _capi.check(lib.mg_symmetrize(ctx, ctypes.byref(batch.c), ctypes.byref(g.c), ctypes.byref(out.c),
+                                      _ptr(out.ws), out.ws.numel(), st), "mg_symmetrize")
+        s = out.read_status()
+        if s["code"] == 4:
+            cap = s["required_capacity"]
+            continue
+        return _finish(out, True)
+    raise RuntimeError("mg_symmetrize: capacity retry failed")
 
 
 # ---------------------------------------------------------------------------- edge vectors

@@ -4,6 +4,7 @@
 Edge sets bit-exact in canonical order; vec/len within 1e-6 relative; destination order
 and gradients as for the constant-cutoff graph.
 """
+import dataclasses
 import json
 import os
 
@@ -171,3 +172,123 @@ def test_keep_ties_gradients():
     b = synth.make_batch(2, B=32)
     g, _ = ties_parity(b, 16)
     grad_check(b, g, synth.normal(6, 1, g.num_edges))
+
+
+# ------------------------------------------------------------------ triplets (Gamma_2)
+
+def _oracle_triplets_check(got_g, tr, include_self):
+    want = oracle.triplets(got_g["src"], include_self=include_self)
+    assert tr.count == want["a"].shape[0]
+    np.testing.assert_array_equal(tr.edge_b.cpu().numpy(), want["b"])
+    if tr.edge_a is not None:
+        np.testing.assert_array_equal(tr.edge_a.cpu().numpy(), want["a"])
+    ptr = np.searchsorted(want["a"], np.arange(got_g["src"].shape[0] + 1))
+    np.testing.assert_array_equal(tr.trip_ptr.cpu().numpy(), ptr)
+
+
+def test_triplets_closed_form_on_gpu():
+    d = GOLD["triplets_sc"]
+    b = synth.crystal(np.eye(3), [[0, 0, 0]])
+    g = mg.cutoff_graph(to_device(b), d["cutoff"])
+    assert mg.triplets(g).count == d["with_self"]
+    assert mg.triplets(g, include_self=False).count == d["without_self"]
+
+
+@pytest.mark.parametrize("include_self", [True, False])
+def test_triplets_config1_cutoff_and_config2_knn(include_self):
+    b1 = synth.make_batch(1)
+    g1 = mg.cutoff_graph(to_device(b1), 5.0)
+    _oracle_triplets_check(graph_arrays(g1), mg.triplets(g1, include_self=include_self), include_self)
+    b2 = synth.make_batch(2, B=64)
+    g2 = mg.knn_graph(to_device(b2), 16)
+    tr = mg.triplets(g2, include_self=include_self, with_edge_a=include_self)
+    _oracle_triplets_check(graph_arrays(g2), tr, include_self)
+
+
+def test_triplets_full_size_sampled():
+    """The bench workload's cutoff graph (tens of millions of triplets): the count is
+    the sum of squared degrees and sampled triplets follow from the definition."""
+    b = synth.make_batch(2)
+    g = mg.cutoff_graph(to_device(b), 6.0, with_perm=False)
+    got = graph_arrays(g)
+    tr = mg.triplets(g, capacity=1024)  # forces the capacity retry
+    deg = np.diff(got["src_ptr"]).astype(np.int64)
+    assert tr.count == int(np.sum(deg * deg))
+    rng = np.random.default_rng(7)
+    q = np.sort(rng.choice(tr.count, 4096, replace=False))
+    a = tr.edge_a.cpu().numpy()[q]
+    bb = tr.edge_b.cpu().numpy()[q]
+    np.testing.assert_array_equal(got["src"][a], got["src"][bb])  # same source
+    tp = tr.trip_ptr.cpu().numpy()
+    e = np.searchsorted(tp, q, side="right") - 1
+    np.testing.assert_array_equal(a, e)
+    lo = got["src_ptr"][got["src"][e]]
+    np.testing.assert_array_equal(bb, lo + (q - tp[e]))
+
+
+# ------------------------------------------------------------------ symmetric closure
+
+def sym_parity(b, g):
+    s = mg.symmetrize(g)
+    got_in = graph_arrays(g)
+    got = graph_arrays(s)
+    want = oracle.symmetrize(got_in["src"], got_in["dst"], got_in["offset"])
+    assert_same_edges(got, want, "symmetric closure")
+    pointers_ok(got, b)
+    assert_vectors(b, got)
+    assert_perm_dst(got, b.total_atoms)
+    return s, got
+
+
+def test_symmetrize_closed_form_on_gpu():
+    b = synth.crystal(np.eye(3), [[0, 0, 0]])
+    g = mg.knn_graph(to_device(b), 8)
+    s, got = sym_parity(b, g)
+    assert got["offset"].tolist() == GOLD["symmetrize_sc_k8"]["offsets"]
+
+
+@pytest.mark.parametrize("cfg,k", [(1, 12), (2, 16), (3, 32)])
+def test_symmetrize_knn_graphs(cfg, k):
+    b = synth.make_batch(cfg, B=None if cfg == 1 else 128)
+    sym_parity(b, mg.knn_graph(to_device(b), k))
+
+
+def test_symmetrize_cutoff_graph_is_identity_and_per_atom_closure():
+    b = synth.make_batch(2, B=64)
+    batch = to_device(b)
+    g = mg.cutoff_graph(batch, 6.0)
+    s, got = sym_parity(b, g)
+    ref = graph_arrays(g)
+    for key in ("src", "dst", "offset", "edge_ptr", "src_ptr"):
+        np.testing.assert_array_equal(got[key], ref[key], err_msg=key)
+    ga = mg.cutoff_graph_atoms(batch, torch.from_numpy(radii_for(b, 3, 3.0, 7.0)).cuda())
+    sym_parity(b, ga)
+
+
+def test_symmetrize_keep_ties_graph():
+    L = np.eye(3) * 2.0
+    x = [[a, b_, c] for a in (0, .5) for b_ in (0, .5) for c in (0, .5)]
+    b = synth.concat([synth.crystal(L, x), synth.make_batch(1, B=4)])
+    sym_parity(b, mg.knn_graph(to_device(b), 7, keep_ties=True))
+
+
+def test_symmetrized_graph_backward_uses_reverse_edges():
+    """The closure is recorded as symmetric: its backward (reverse-edge path) against the
+    oracle gradient, and equal to the destination-order path on the same edges."""
+    b = synth.make_batch(2, B=48)
+    batch = to_device(b)
+    s, _ = sym_parity(b, mg.knn_graph(batch, 16))
+    w = synth.normal(8, 0, s.num_edges)
+    grad_check(b, s, w)
+    gl = torch.from_numpy(w).cuda()
+    v, ln = mg.edge_vectors_fwd(s)
+    f1, L1 = mg.edge_vectors_bwd(s, batch, None, gl, v, ln)
+    assert mg.last_launch_count() == 2  # symmetric path: bwd_sym + bwd_lat
+    # the same edges in other buffers are not recorded as symmetric: destination order
+    c = dataclasses.replace(s, src=s.src.clone(), dst=s.dst.clone(), offset=s.offset.clone(),
+                            edge_ptr=s.edge_ptr.clone(), src_ptr=s.src_ptr.clone(), perm_dst=s.perm_dst.clone(),
+                            dst_ptr=s.dst_ptr.clone(), _c=None)
+    f2, L2 = mg.edge_vectors_bwd(c, batch, None, gl, v, ln)
+    assert mg.last_launch_count() == 3  # bwd_src + bwd_dst + bwd_lat
+    torch.testing.assert_close(f1, f2, rtol=1e-5, atol=1e-5 * float(f2.abs().max()))
+    torch.testing.assert_close(L1, L2, rtol=1e-5, atol=1e-5 * float(L2.abs().max()))
