@@ -70,6 +70,8 @@ def parse_args():
     p.add_argument("--config", type=int, default=2, choices=sorted(WORKLOADS))
     p.add_argument("--no-baselines", action="store_true", help="skip the CPU oracle and per-structure legs")
     p.add_argument("--sweep", action="store_true", help="batch-size sweep of the KNN k=32 build")
+    p.add_argument("--rows", action="store_true",
+                   help="per-atom cutoff, keep-ties KNN, symmetric closure and triplets on --config")
     return p.parse_args()
 
 
@@ -511,6 +513,97 @@ def run_sweep(args, local_rank):
     return 0
 
 
+def run_rows(args, local_rank):
+    """Throughput and HBM roofline of the operations after the hot path, one JSON line
+    each, on the --config workload: per-atom cutoff build (radii U[0.75 c, c]), keep-ties
+    KNN build, symmetric closure of the KNN graph, triplets of the cutoff graph.  Builds
+    replay their plans; closure and triplets call the C-ABI on preallocated buffers.  L2
+    is flushed between iterations; CUDA events around each call, median."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    import paper_2307_05380_gb300 as mg
+    import synth
+    from paper_2307_05380_gb300 import _capi
+    from paper_2307_05380_gb300.graph import MgTriplets, _stream, context
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    hbm_peak, _, peak_src = measured_peaks()
+    wl = WORKLOADS[args.config]
+    b = synth.make_batch(args.config)
+    batch = mg.Batch(torch.from_numpy(b.frac).to(dev), torch.from_numpy(b.lattice).to(dev),
+                     torch.from_numpy(b.atom_ptr).to(dev), max_atoms=b.max_atoms)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    steps = max(5, min(args.steps, 100))
+    lib = _capi.load()
+    ctx = context(dev)
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        ms = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(steps):
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    def line(op, units, unit_name, ms, bytes_per_unit, note):
+        gbs = units * bytes_per_unit / ms / 1e6
+        print(json.dumps({"row": op, "workload": wl["name"], "units": int(units), "unit": unit_name,
+                          "ms": ms, "units_per_s": units / ms * 1e3,
+                          "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                                       "frac": gbs / hbm_peak, "peak_source": peak_src,
+                                       "work_per_unit": note}, "steps": steps}), flush=True)
+
+    radii = np.random.default_rng(args.config).uniform(0.75 * wl["cutoff"], wl["cutoff"], b.total_atoms)
+    g_atoms = mg.cutoff_graph_atoms(batch, torch.from_numpy(radii.astype(np.float32)).to(dev), with_perm=False)
+    ms = timed(lambda: mg.update_graph(g_atoms, sync=False))
+    assert g_atoms.read_status()["code"] == 0
+    line("cutoff graph, per-atom radii", g_atoms.num_edges, "edges", ms, 36.0, "36 B written per edge")
+
+    g_ties = mg.knn_graph(batch, wl["k"], keep_ties=True, with_perm=False)
+    ms = timed(lambda: mg.update_graph(g_ties, sync=False))
+    assert g_ties.read_status()["code"] == 0
+    line(f"knn graph k={wl['k']}, keep ties", g_ties.num_edges, "edges", ms, 36.0, "36 B written per edge")
+
+    g_knn = mg.knn_graph(batch, wl["k"])
+    sym = mg.symmetrize(g_knn)
+    E_in = g_knn.num_edges
+    ms = timed(lambda: _capi.check(lib.mg_symmetrize(ctx, ctypes.byref(batch.c), ctypes.byref(g_knn.c),
+                                                     ctypes.byref(sym.c), sym.ws.data_ptr(), sym.ws.numel(),
+                                                     _stream(dev)), "mg_symmetrize"))
+    assert sym.read_status()["code"] == 0
+    line(f"symmetric closure of the knn graph k={wl['k']}", sym.num_edges, "edges", ms,
+         40.0 + 24.0 * E_in / sym.num_edges,
+         "40 B written per output edge (36 + perm_dst 4) + 24 B read per input edge (dst, offset, perm, src)")
+
+    g_cut = mg.cutoff_graph(batch, wl["cutoff"], with_perm=False)
+    tr = mg.triplets(g_cut)
+    T = tr.count
+    status = torch.zeros(5, dtype=torch.int64, device=dev)
+    nbytes = ctypes.c_size_t(0)
+    lib.mg_workspace_size(ctx, ctypes.byref(batch.c), 0, ctypes.byref(nbytes))
+    ws = torch.empty(int(nbytes.value), dtype=torch.uint8, device=dev)
+    out = MgTriplets(T, tr.edge_a.data_ptr(), tr.edge_b.data_ptr(), tr.trip_ptr.data_ptr(), status.data_ptr())
+    ms = timed(lambda: _capi.check(lib.mg_triplets(ctx, ctypes.byref(batch.c), ctypes.byref(g_cut.c), 1,
+                                                   ctypes.byref(out), ws.data_ptr(), ws.numel(), _stream(dev)),
+                                   "mg_triplets"))
+    assert int(status.cpu()[1]) == T
+    line("triplets of the cutoff graph", T, "triplets", ms, 8.0 + 8.0 * g_cut.num_edges / T,
+         "8 B written per triplet (two edge ids) + 8 B per edge (trip_ptr)")
+    return 0
+
+
 def main():
     args = parse_args()
     rank, world, local_rank = dist_env()
@@ -518,6 +611,8 @@ def main():
         return run_reference(args, rank)
     if args.sweep:
         return run_sweep(args, local_rank) if rank == 0 else 0
+    if args.rows:
+        return run_rows(args, local_rank) if rank == 0 else 0
     return run_mine(args, rank, world, local_rank)
 
 
