@@ -70,6 +70,7 @@ struct mg_context {
     std::mutex mu;
     std::map<const void *, Plan> plans;      // keyed by graph->src
     std::map<const void *, mg_graph_t> sym;  // symmetric closures written here, keyed by src
+    std::map<const void *, const void *> pair_owner;  // workspace -> graph (src) whose pair table it holds
     int tuned[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};  // [kind-1][size class] -> schedule
     int64_t last_launches = 0;
 };
@@ -118,7 +119,7 @@ size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
     size_t recs, pos, atom_struct, cnt, cursor, tile_sum, src_ptr, gpart, lpart, queue, bin_cnt, bin_cursor,
-        cell_start, cell_fx, cell_p, atom_bin, tile_flags, rr_atom, sort_tmp, total;
+        cell_start, cell_fx, cell_p, atom_bin, tile_flags, rr_atom, pair_lo, pair_hi, pair_ok, sort_tmp, total;
 };
 
 // Workspace regions, 256-byte aligned; the edge-sized sort scratch comes last so that
@@ -152,6 +153,9 @@ Layout layout(int B, int N, int64_t max_edges) {
     L.atom_bin = take(sizeof(int32_t) * n);
     L.tile_flags = take(sizeof(unsigned long long) * (n / BUILD_TILE + 2));
     L.rr_atom = take(sizeof(double) * n);
+    L.pair_lo = take(sizeof(uint16_t) * n * PAIR_MAX);
+    L.pair_hi = take(sizeof(uint16_t) * n * PAIR_MAX);
+    L.pair_ok = take(sizeof(int32_t) * (size_t)(B > 0 ? B : 1));
     L.sort_tmp = off;
     off += sizeof(int32_t) * (size_t)(max_edges > 0 ? max_edges : 0);
     L.total = align_up(off);
@@ -180,6 +184,9 @@ Work carve(void *ws, int B, int N, int64_t max_edges) {
     w.atom_bin = reinterpret_cast<int32_t *>(b + L.atom_bin);
     w.tile_flags = reinterpret_cast<unsigned long long *>(b + L.tile_flags);
     w.rr_atom = reinterpret_cast<double *>(b + L.rr_atom);
+    w.pair_lo = reinterpret_cast<uint16_t *>(b + L.pair_lo);
+    w.pair_hi = reinterpret_cast<uint16_t *>(b + L.pair_hi);
+    w.pair_ok = reinterpret_cast<int32_t *>(b + L.pair_ok);
     w.sort_tmp = reinterpret_cast<int32_t *>(b + L.sort_tmp);
     w.max_edges = max_edges;
     return w;
@@ -261,6 +268,8 @@ mg_status_t enqueue_build(mg_context *ctx, int kind, const mg_batch_t *b, float 
     PrepArgs pa{B, N, b->lattice, b->frac, b->atom_ptr, cutoff, cutoff_ps, knn ? k : 0, o.band_rel, g->status,
                 0, (!knn || ties) ? 1 : 0, 1, src_ptr, (knn && !ties) ? g->edge_ptr : nullptr, b->max_atoms};
     pa.cutoff_atom = kind == KIND_CUTOFF_ATOMS ? cutoff_atom : nullptr;
+    const bool pairs = kind == MG_KIND_CUTOFF;  // symmetric: record the pair table for the backward
+    pa.pair_ok = pairs ? w.pair_ok : nullptr;
     if (launch_prep(pa, w, st)) return MG_ERR_CUDA;
     ++n;
     mk.mark("prep");
@@ -287,6 +296,7 @@ mg_status_t enqueue_build(mg_context *ctx, int kind, const mg_batch_t *b, float 
     if (!knn) {
         // one pass: scan, look-back offsets, write (also src_ptr, edge_ptr, edge count)
         if (kind == KIND_CUTOFF_ATOMS) ba.cut_atom = cutoff_atom;
+        ba.write_pairs = pairs ? 1 : 0;
         if (launch_cutoff_build(ba, w, st)) return MG_ERR_CUDA;
         ++n;
         mk.mark("build");
@@ -366,6 +376,10 @@ mg_status_t build_and_record(mg_context *ctx, int kind, const mg_batch_t *b, flo
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->last_launches = launches;
     ctx->sym.erase((const void *)g->src);
+    if (kind == MG_KIND_CUTOFF)  // this build wrote the workspace's pair table
+        ctx->pair_owner[ws] = (const void *)g->src;
+    else
+        ctx->pair_owner.erase(ws);
     Plan &p = ctx->plans[(const void *)g->src];
     const bool same = p.kind == kind && p.cutoff == cutoff && p.cutoff_ps == cutoff_ps &&
                       p.cutoff_atom == cutoff_atom && p.k == k &&
@@ -510,6 +524,10 @@ mg_status_t mg_update_graph(mg_context_t ctx, const mg_batch_t *batch, mg_graph_
         r = enqueue_build(ctx, p.kind, batch, p.cutoff, p.cutoff_ps, p.cutoff_atom, p.k, p.opts, graph, ws,
                           ws_bytes, st, &n);
         ctx->last_launches = n;
+        if (p.kind == MG_KIND_CUTOFF)
+            ctx->pair_owner[ws] = (const void *)graph->src;
+        else
+            ctx->pair_owner.erase(ws);
         return r;
     }
     const int which = p.kind == MG_KIND_KNN ? MG_PROF_KNN : MG_PROF_CUTOFF;
@@ -541,6 +559,10 @@ mg_status_t mg_update_graph(mg_context_t ctx, const mg_batch_t *batch, mg_graph_
     }
     if (cudaGraphLaunch(p.exec, st) != cudaSuccess) return MG_ERR_CUDA;
     ctx->last_launches = p.launches;
+    if (p.kind == MG_KIND_CUTOFF)
+        ctx->pair_owner[ws] = (const void *)graph->src;
+    else
+        ctx->pair_owner.erase(ws);
     if (p.prof.valid) ctx->last_prof[which] = &p.prof;  // the replay re-records the plan's events
     return MG_OK;
 }
@@ -667,6 +689,7 @@ mg_status_t mg_build_per_structure(mg_context_t ctx, const mg_batch_t *b, int32_
     if (cudaGetLastError() != cudaSuccess) return MG_ERR_CUDA;
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->last_launches = n;
+    ctx->pair_owner.erase(ws);  // the per-structure build records no pair table
     return MG_OK;
 }
 
@@ -705,12 +728,18 @@ mg_status_t mg_edge_vectors_bwd(mg_context_t ctx, const mg_batch_t *b, const mg_
     // A cutoff graph built on this context with one radius per structure is symmetric:
     // its in-edges are found as the reverses of out-edges and no destination order is
     // needed.  Other graphs (KNN, per-atom radii, foreign edge lists) need one.
-    bool symmetric = false;
+    // The pair table in the workspace serves it when the last build that used this
+    // workspace was this graph's own.
+    bool symmetric = false, pairs = false;
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
         auto it = ctx->plans.find((const void *)g->src);
         symmetric = it != ctx->plans.end() && it->second.kind == MG_KIND_CUTOFF && same_graph(it->second.graph, *g);
-        if (!symmetric) {
+        if (symmetric) {
+            auto po = ctx->pair_owner.find(ws);
+            pairs = po != ctx->pair_owner.end() && po->second == (const void *)g->src && it->second.ws == ws &&
+                    it->second.ws_bytes == ws_bytes;
+        } else {
             auto sit = ctx->sym.find((const void *)g->src);
             symmetric = sit != ctx->sym.end() && same_graph(sit->second, *g);
         }
@@ -723,6 +752,7 @@ mg_status_t mg_edge_vectors_bwd(mg_context_t ctx, const mg_batch_t *b, const mg_
     EdgeVecArgs a{};
     a.B = B;
     a.N = N;
+    a.max_atoms = b->max_atoms;
     a.lattice = b->lattice;
     a.frac = b->frac;
     a.atom_ptr = b->atom_ptr;
@@ -733,6 +763,12 @@ mg_status_t mg_edge_vectors_bwd(mg_context_t ctx, const mg_batch_t *b, const mg_
     a.len = len;
     a.grad_frac = grad_frac;
     a.grad_lattice = grad_lattice;
+    if (pairs) {
+        a.pair_lo = w.pair_lo;
+        a.pair_hi = w.pair_hi;
+        a.pair_ok = w.pair_ok;
+        a.atom_struct = w.atom_struct;
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Marker mk(ctx, MG_PROF_BWD, st);
     int n = 0;

@@ -216,6 +216,36 @@ __global__ void __launch_bounds__(256) bwd_lat_kernel(EdgeVecArgs a, const float
     if (lane < 9) a.grad_lattice[9 * (int64_t)s + lane] = out;
 }
 
+// Large structures: a block of LAT_WARPS warps per structure, warp w taking every
+// LAT_WARPS-th chunk of 32 atoms; the warps' float-float partials are combined in warp
+// order through shared memory (a fixed order: deterministic).
+constexpr int LAT_WARPS = 8;
+__global__ void __launch_bounds__(LAT_WARPS * 32) bwd_lat_block_kernel(EdgeVecArgs a,
+                                                                     const float2 *__restrict__ lpart) {
+    __shared__ float2 part[LAT_WARPS][9];
+    const int s = blockIdx.x;
+    const int lane = lane_id(), wid = threadIdx.x >> 5;
+    const int lo = a.atom_ptr[s], hi = a.atom_ptr[s + 1];
+    float2 acc[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q] = make_float2(0.f, 0.f);
+    for (int r = lo + 32 * wid + lane; r < hi; r += 32 * LAT_WARPS)
+#pragma unroll
+        for (int q = 0; q < 9; ++q) acc[q] = ff_add(acc[q], lpart[9 * (int64_t)r + q]);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const float2 h = warp_sum_ff(acc[q].x);
+        const float2 l = warp_sum_ff(acc[q].y);
+        if (lane == q) part[wid][q] = ff_add(h, l);
+    }
+    __syncthreads();
+    if (wid == 0 && lane < 9) {
+        float2 t = part[0][lane];
+        for (int w = 1; w < LAT_WARPS; ++w) t = ff_add(t, part[w][lane]);
+        a.grad_lattice[9 * (int64_t)s + lane] = __fadd_rn(t.x, t.y);
+    }
+}
+
 // First position in [lo, hi) of the sorted keys with key >= v (or > v when upper).
 __device__ __forceinline__ int64_t key_bound(const int32_t *__restrict__ keys, int64_t lo, int64_t hi, int v,
                                              bool upper) {
@@ -232,15 +262,30 @@ __device__ __forceinline__ int64_t key_bound(const int32_t *__restrict__ keys, i
 // of j matching out-edge p = (j, i, t) is its reverse (i, j, -t), which sits in i's
 // segment at s_ij + (rhi - 1 - p) (the run of i's edges to j holds the reversed run in
 // the opposite offset order; s_ij its start, [rlo, rhi) the run of p in j's segment).
+// PAIRS 0: the runs come from binary searches done once per run by its first lane;
+// PAIRS 1: from the build's pair table where the structure has one, else searches;
+// PAIRS 2: every structure has a table (two loads per edge).
+// The reverse edge's vector and length are those of p negated (the forward evaluates
+// both edges with sign-symmetric float-float arithmetic), so only its incoming
+// gradients are gathered.
 // grad_frac[j] = sum_p (g_rev(p) - g_p) L^T; the lattice partial sums (x_i - x_j + t)^T g_p.
 // Fixed per-lane order and a fixed warp reduction: deterministic, no destination order.
-__global__ void __launch_bounds__(256) bwd_sym_kernel(EdgeVecArgs a, float2 *__restrict__ lpart) {
+template <int PAIRS>
+__global__ void __launch_bounds__(256, 5) bwd_sym_kernel(EdgeVecArgs a, float2 *__restrict__ lpart) {
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = lane_id();
     if (j >= a.N) return;
     const int64_t E = a.g.edge_ptr[a.B];
     const int64_t lo = a.g.src_ptr[j], hi = (E > a.g.capacity) ? lo : a.g.src_ptr[j + 1];
     const float xj[3] = {a.frac[3 * (int64_t)j], a.frac[3 * (int64_t)j + 1], a.frac[3 * (int64_t)j + 2]};
+    int sj = -1, begin = 0;  // structure of j when its pair table is usable
+    if (PAIRS) {
+        const int s = a.atom_struct[j];
+        if (PAIRS == 2 || a.pair_ok[s]) {
+            sj = s;
+            begin = a.atom_ptr[s];
+        }
+    }
     float acc[3] = {0.f, 0.f, 0.f};
     float M[9];
 #pragma unroll
@@ -249,21 +294,48 @@ __global__ void __launch_bounds__(256) bwd_sym_kernel(EdgeVecArgs a, float2 *__r
         const int64_t p = p0 + lane;
         const bool valid = p < hi;
         const int i = valid ? a.g.dst[p] : -1;
-        // lanes of one run (same target i, contiguous) share the run's two searches
-        const unsigned grp = __match_any_sync(FULL, i);
-        const int leader = __ffs(grp) - 1;
-        int64_t rhi = 0, sij = 0;
-        if (valid && lane == leader) {
-            int64_t e = p + 1;  // end of the run: a short probe, then a binary search
-            while (e < hi && e < p + 4 && a.g.dst[e] == i) ++e;
-            rhi = (e < hi && e == p + 4 && a.g.dst[e] == i) ? key_bound(a.g.dst, e, hi, i, true) : e;
-            sij = key_bound(a.g.dst, a.g.src_ptr[i], a.g.src_ptr[i + 1], j, false);
+        int64_t rev = 0;
+        if (PAIRS == 2 || (PAIRS == 1 && sj >= 0)) {
+            if (valid) {
+                const int il = i - begin, jl = j - begin;
+                const int64_t rhi = lo + a.pair_hi[(int64_t)j * PAIR_MAX + il];
+                const int64_t sij = a.g.src_ptr[i] + a.pair_lo[(int64_t)i * PAIR_MAX + jl];
+                rev = sij + (rhi - 1 - p);
+            }
+        } else {
+            // lanes of one run (same target i, contiguous) share the run's two searches
+            const unsigned grp = __match_any_sync(FULL, i);
+            const int leader = __ffs(grp) - 1;
+            int64_t rhi = 0, sij = 0;
+            if (valid && lane == leader) {
+                int64_t e = p + 1;  // end of the run: a short probe, then a binary search
+                while (e < hi && e < p + 4 && a.g.dst[e] == i) ++e;
+                rhi = (e < hi && e == p + 4 && a.g.dst[e] == i) ? key_bound(a.g.dst, e, hi, i, true) : e;
+                sij = key_bound(a.g.dst, a.g.src_ptr[i], a.g.src_ptr[i + 1], j, false);
+            }
+            rhi = __shfl_sync(FULL, rhi, leader);
+            sij = __shfl_sync(FULL, sij, leader);
+            rev = sij + (rhi - 1 - p);
         }
-        rhi = __shfl_sync(FULL, rhi, leader);
-        sij = __shfl_sync(FULL, sij, leader);
         if (!valid) continue;
-        const float3 g = edge_g(a, p);
-        const float3 gr = edge_g(a, sij + (rhi - 1 - p));
+        float3 g = make_float3(0.f, 0.f, 0.f), gr = g;
+        if (a.grad_vec) {
+            g = make_float3(a.grad_vec[3 * p], a.grad_vec[3 * p + 1], a.grad_vec[3 * p + 2]);
+            gr = make_float3(a.grad_vec[3 * rev], a.grad_vec[3 * rev + 1], a.grad_vec[3 * rev + 2]);
+        }
+        if (a.grad_len) {
+            const float l = a.len[p];
+            if (l > 0.f) {
+                const float f = __fdiv_rn(a.grad_len[p], l), fr = __fdiv_rn(a.grad_len[rev], l);
+                const float vx = a.vec[3 * p], vy = a.vec[3 * p + 1], vz = a.vec[3 * p + 2];
+                g.x = __fmaf_rn(f, vx, g.x);
+                g.y = __fmaf_rn(f, vy, g.y);
+                g.z = __fmaf_rn(f, vz, g.z);
+                gr.x = __fmaf_rn(fr, -vx, gr.x);  // the reverse edge's vector is -vec[p]
+                gr.y = __fmaf_rn(fr, -vy, gr.y);
+                gr.z = __fmaf_rn(fr, -vz, gr.z);
+            }
+        }
         acc[0] += gr.x - g.x;
         acc[1] += gr.y - g.y;
         acc[2] += gr.z - g.z;
@@ -275,14 +347,21 @@ __global__ void __launch_bounds__(256) bwd_sym_kernel(EdgeVecArgs a, float2 *__r
 #pragma unroll
     for (int q = 0; q < 3; ++q) tot[q] = warp_sum_ff(acc[q]);
     if (lane < 3) {
-        const int s = structure_of(a.atom_ptr, a.B, j);
+        const int s = sj >= 0 ? sj : structure_of(a.atom_ptr, a.B, j);
         a.grad_frac[3 * (int64_t)j + lane] = ff_times_LT(tot, a.lattice + 9 * (int64_t)s, lane);
     }
     store_lattice_partial(lpart, j, M);
 }
 
 cudaError_t launch_bwd_sym(const EdgeVecArgs &a, const Work &w, cudaStream_t s) {
-    if (a.N > 0) bwd_sym_kernel<<<(a.N + 7) / 8, 256, 0, s>>>(a, w.lpart);
+    if (a.N <= 0) return cudaSuccess;
+    const int blocks = (a.N + 7) / 8;
+    if (!a.pair_lo)
+        bwd_sym_kernel<0><<<blocks, 256, 0, s>>>(a, w.lpart);
+    else if (a.max_atoms > 0 && a.max_atoms <= PAIR_MAX)
+        bwd_sym_kernel<2><<<blocks, 256, 0, s>>>(a, w.lpart);
+    else
+        bwd_sym_kernel<1><<<blocks, 256, 0, s>>>(a, w.lpart);
     return cudaGetLastError();
 }
 
@@ -297,7 +376,11 @@ cudaError_t launch_bwd_dst(const EdgeVecArgs &a, const Work &w, cudaStream_t s) 
 }
 
 cudaError_t launch_bwd_lat(const EdgeVecArgs &a, const Work &w, cudaStream_t s) {
-    if (a.B > 0) bwd_lat_kernel<<<(a.B + 7) / 8, 256, 0, s>>>(a, w.lpart);
+    if (a.B <= 0) return cudaSuccess;
+    if (a.max_atoms > 0 && a.max_atoms <= 1024)
+        bwd_lat_kernel<<<(a.B + 7) / 8, 256, 0, s>>>(a, w.lpart);  // a warp per structure
+    else
+        bwd_lat_block_kernel<<<a.B, LAT_WARPS * 32, 0, s>>>(a, w.lpart);
     return cudaGetLastError();
 }
 

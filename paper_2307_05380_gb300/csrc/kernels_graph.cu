@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(GROUP == 32 ? 128 : GROUP) prep_kernel(PrepArg
             for (int k = 0; k < 3; ++k) R.nb[k] = nk[k];
     }
     recs[s] = R;  // a bad structure is reported by the kernel that scans its first atom
+    if (a.pair_ok) a.pair_ok[s] = n <= PAIR_MAX ? 1 : 0;
 }
 
 cudaError_t launch_prep(const PrepArgs &a, const Work &w, cudaStream_t s) {
@@ -806,6 +807,7 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_build_kernel(Build
             }
         }
     }
+    if (!PERSRC && a.write_pairs && spill && lane == 0) w.pair_ok[s] = 0;  // no pair table for this structure
     if (lane == 0) s_cnt[wid] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -843,11 +845,19 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_build_kernel(Build
     }
     if (m == 0 || base + m > g.capacity) return;  // nothing to write, or the capacity error
     if (!spill) {
+        // symmetric graphs of small structures: the run of every target in the pair table
+        const bool pairs = !PERSRC && a.write_pairs && S.n <= PAIR_MAX;
         for (int q = lane; q < m; q += 32) {
             const unsigned long long key = keys[q];
             int t0, t1, t2;
             unpack_t((uint32_t)(key & 0xffffffffull), t0, t1, t2);
-            const int64_t jr = (int64_t)S.begin + (int)(key >> 32);
+            const int jl = (int)(key >> 32);
+            const int64_t jr = (int64_t)S.begin + jl;
+            if (pairs) {
+                if (q == 0 || (int)(keys[q - 1] >> 32) != jl) w.pair_lo[(int64_t)i * PAIR_MAX + jl] = (uint16_t)q;
+                if (q == m - 1 || (int)(keys[q + 1] >> 32) != jl)
+                    w.pair_hi[(int64_t)i * PAIR_MAX + jl] = (uint16_t)(q + 1);
+            }
             emit_edge(g, S, i, base + q, jr, a.frac[3 * jr], a.frac[3 * jr + 1], a.frac[3 * jr + 2], t0, t1, t2);
         }
     } else {

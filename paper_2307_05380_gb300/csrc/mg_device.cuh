@@ -204,9 +204,10 @@ __device__ __forceinline__ void warp_smem_sort_u64(unsigned long long *b, int n,
     for (int q = n + lane; q < P; q += 32) b[q] = ~0ull;
     __syncwarp();
     for (int size = 2; size <= P; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int ls = __ffs(size) - 2; ls >= 0; --ls) {  // stride = 2^ls
+            const int stride = 1 << ls;
             for (int q = lane; q < P / 2; q += 32) {
-                const int x = 2 * stride * (q / stride) + (q % stride);
+                const int x = ((q >> ls) << (ls + 1)) | (q & (stride - 1));
                 const int y = x + stride;
                 const bool asc = (x & size) == 0;
                 const unsigned long long vx = b[x], vy = b[y];

@@ -27,7 +27,7 @@ namespace mg {
 struct Source {
     float L[9];
     float invd[3];
-    float L2norm2, L2norm;
+    float inv_L2n2, L2norm;  // 1 / |L_2|^2 and |L_2|
     float xi0, xi1, xi2;
     float3 pi;
     int i_loc;   // local index of the source atom within its structure
@@ -49,7 +49,7 @@ __device__ __forceinline__ void load_source(Source &S, const StructRec *__restri
         S.nb[k] = R.nb[k];
     }
     S.bin_base = R.bin_base;
-    S.L2norm2 = R.L2norm2;
+    S.inv_L2n2 = 1.0f / R.L2norm2;
     S.L2norm = R.L2norm;
     S.begin = R.atom_begin;
     S.n = R.n_atoms;
@@ -90,7 +90,7 @@ __device__ __forceinline__ int bin_of(float w, int n) {
 // (reach below half a cell on every axis) a target has at most one image in reach, so
 // each lane tests its own candidate directly and the flattening levels are skipped.
 template <class Visit>
-__device__ __forceinline__ void visit_targets(const Source &S, const float Rk[3], float rho2p, float mu0,
+__device__ __forceinline__ void visit_targets(const Source &S, const float Rk[3], float rho2p, float rho1, float mu0,
                                               bool single, int jl, bool vj, float4 xj, float4 pj,
                                               Visit &visit) {
     const int lane = lane_id();
@@ -153,7 +153,11 @@ __device__ __forceinline__ void visit_targets(const Source &S, const float Rk[3]
         RowRegs rr;
         rr.j = __shfl_sync(FULL, jl, ow);
         const int rem = vr ? q - o_excl : 0;
-        const int d0 = rem / max(o_n1, 1);
+        // rem / n1 from an approximate quotient, corrected to the exact integer one
+        const int n1 = max(o_n1, 1);
+        int d0 = (int)__fdividef((float)rem, (float)n1);
+        while (d0 * n1 > rem) --d0;
+        while ((d0 + 1) * n1 <= rem) ++d0;
         rr.t0 = o_lo0 + d0;
         rr.t1 = o_lo1 + (rem - d0 * o_n1);
         // row base b = a + t0 L0 + t1 L1
@@ -161,24 +165,25 @@ __device__ __forceinline__ void visit_targets(const Source &S, const float Rk[3]
         const float bx = __fmaf_rn(ft1, S.L[3], __fmaf_rn(ft0, S.L[0], ax));
         const float by = __fmaf_rn(ft1, S.L[4], __fmaf_rn(ft0, S.L[1], ay));
         const float bz = __fmaf_rn(ft1, S.L[5], __fmaf_rn(ft0, S.L[2], az));
-        // chord of the sphere along L_2: t2 in t2c +- w (widened)
+        // chord of the sphere along L_2: t2 in t2c +- w, widened by mu.  The FP32
+        // errors here (approximate reciprocal and square root included) stay below
+        // 1e-5 rho / |L_2| + 6e-7 |t2c| while |b| + |t2c| |L_2| <= 100 rho, far inside mu.
         int c_lo = o_lo2, c_hi = o_lo2 + o_n2 - 1;
         {
             const float bl = __fmaf_rn(bz, S.L[8], __fmaf_rn(by, S.L[7], __fmul_rn(bx, S.L[6])));
-            const float t2c = -bl / S.L2norm2;
+            const float t2c = -bl * S.inv_L2n2;
             const float px = __fmaf_rn(t2c, S.L[6], bx);
             const float py = __fmaf_rn(t2c, S.L[7], by);
             const float pz = __fmaf_rn(t2c, S.L[8], bz);
             const float perp2 = __fmaf_rn(pz, pz, __fmaf_rn(py, py, __fmul_rn(px, px)));
-            const float scale =
-                sqrtf(__fmaf_rn(bz, bz, __fmaf_rn(by, by, __fmul_rn(bx, bx)))) + fabsf(t2c) * S.L2norm;
-            if (scale <= 100.0f * sqrtf(rho2p)) {  // trimming error analysis holds
-                const float wsq = (rho2p - perp2) / S.L2norm2;
+            const float b2 = __fmaf_rn(bz, bz, __fmaf_rn(by, by, __fmul_rn(bx, bx)));
+            if (b2 <= 2500.0f * rho2p && fabsf(t2c) * S.L2norm <= 50.0f * rho1) {  // error analysis holds
+                const float wsq = (rho2p - perp2) * S.inv_L2n2;
                 if (wsq < 0.0f) {
                     c_hi = c_lo - 1;
                 } else {
-                    const float w = sqrtf(wsq);
-                    const float mu = mu0 + 4e-7f * fabsf(t2c);
+                    const float w = wsq > 0.0f ? wsq * rsqrtf(wsq) : 0.0f;
+                    const float mu = mu0 + 6e-7f * fabsf(t2c);
                     c_lo = max(c_lo, (int)ceilf(t2c - w - mu));
                     c_hi = min(c_hi, (int)floorf(t2c + w + mu));
                 }
@@ -228,6 +233,7 @@ __device__ __forceinline__ void for_each_candidate(const Source &S, const float 
 #pragma unroll
     for (int k = 0; k < 3; ++k) Rk[k] = rho * S.invd[k];
     const float rho2p = rho * rho * 1.0002f;
+    const float rho1 = rho * 1.0001f;  // >= sqrt(rho2p)
     const float mu0 = 1e-3f * (1.0f + rho / S.L2norm);
     const bool single = fmaxf(Rk[0], fmaxf(Rk[1], Rk[2])) < 0.49f;
 
@@ -241,7 +247,7 @@ __device__ __forceinline__ void for_each_candidate(const Source &S, const float 
                 xj = make_float4(frac[3 * row + 0], frac[3 * row + 1], frac[3 * row + 2], 0.f);
                 pj = pos[row];
             }
-            visit_targets(S, Rk, rho2p, mu0, single, jl, vj, xj, pj, visit);
+            visit_targets(S, Rk, rho2p, rho1, mu0, single, jl, vj, xj, pj, visit);
         }
         return;
     }
@@ -295,7 +301,7 @@ __device__ __forceinline__ void for_each_candidate(const Source &S, const float 
                 xj = cells.fx[ost + (q2 - oex)];
                 pj = cells.p[ost + (q2 - oex)];
             }
-            visit_targets(S, Rk, rho2p, mu0, single, va ? __float_as_int(xj.w) : 0, va, xj, pj, visit);
+            visit_targets(S, Rk, rho2p, rho1, mu0, single, va ? __float_as_int(xj.w) : 0, va, xj, pj, visit);
         }
     }
 }

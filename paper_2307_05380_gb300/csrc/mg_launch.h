@@ -32,11 +32,15 @@ struct Work {
     int32_t *atom_bin;        // [N] global bin of each atom (-1: all-pairs structure)
     unsigned long long *tile_flags;  // [N/BUILD_TILE + 2] look-back words of the one-pass build
     double *rr_atom;          // [N] per-source squared radius (keep-ties KNN: the k-th distance)
+    uint16_t *pair_lo;        // [N][PAIR_MAX] run of edges i -> j in i's segment: first and
+    uint16_t *pair_hi;        //   one-past-last position (structures of <= PAIR_MAX atoms)
+    int32_t *pair_ok;         // [B] 1: the pair table of the structure is complete
     int64_t max_edges;
 };
 
 constexpr int SCAN_TILE = 4096;
 constexpr int BUILD_TILE = 4;    // source atoms (one warp each) per look-back tile of the one-pass build
+constexpr int PAIR_MAX = 128;    // largest structure with a pair table (run of i -> j per (i, j))
 
 struct PrepArgs {
     int B, N;
@@ -54,6 +58,7 @@ struct PrepArgs {
     int64_t *edge_ptr;         // KNN: written here
     int max_atoms;             // host-known bound on atoms per structure (0: unknown)
     const float *cutoff_atom = nullptr;  // per-atom radii [N]: the structure's reach is their maximum
+    int32_t *pair_ok = nullptr;          // [B] set to (n <= PAIR_MAX) when a pair table is written
 };
 
 cudaError_t launch_prep(const PrepArgs &a, const Work &w, cudaStream_t s);
@@ -91,6 +96,7 @@ struct BuildArgs {
     const double *rr_atom = nullptr;   // [N] squared radius in FP64 (keep-ties KNN)
     int inclusive = 0;                 // 1: edge iff d2 <= rr (Alg. 2's filter)
     double *knn_dk = nullptr;          // KNN: write the k-th canonical d2 per atom, no edges
+    int write_pairs = 0;               // 1: record the pair table (symmetric cutoff graphs)
 };
 
 // One-pass cutoff build (batched): scan once, stage keys, look-back offsets, write.
@@ -109,12 +115,16 @@ cudaError_t launch_reset_queue(const Work &w, cudaStream_t s);
 
 struct EdgeVecArgs {
     int B, N;
+    int max_atoms;             // host-known bound on atoms per structure (0: unknown)
     const float *lattice, *frac;
     const int32_t *atom_ptr;
     mg_graph_t g;
     const float *grad_vec, *grad_len, *vec, *len;
     float *out_vec, *out_len;
     float *grad_frac, *grad_lattice;
+    // symmetric backward: the pair table of the graph's build (NULL: binary searches)
+    const uint16_t *pair_lo, *pair_hi;
+    const int32_t *pair_ok, *atom_struct;
 };
 cudaError_t launch_edgevec_fwd(const EdgeVecArgs &a, cudaStream_t s);
 cudaError_t launch_bwd_sym(const EdgeVecArgs &a, const Work &w, cudaStream_t s);  // symmetric graphs

@@ -292,3 +292,25 @@ def test_symmetrized_graph_backward_uses_reverse_edges():
     assert mg.last_launch_count() == 3  # bwd_src + bwd_dst + bwd_lat
     torch.testing.assert_close(f1, f2, rtol=1e-5, atol=1e-5 * float(f2.abs().max()))
     torch.testing.assert_close(L1, L2, rtol=1e-5, atol=1e-5 * float(L2.abs().max()))
+
+
+# ------------------------------------------------------------------ symmetric backward paths
+
+def test_symmetric_backward_pair_table_and_search_paths_identical():
+    """The reverse-edge backward finds reverse edges through the build's pair table
+    (structures of <= 128 atoms) or by binary search; both give bit-identical sums.
+    A per-structure rebuild records no pair table, so the same graph then takes the
+    search path."""
+    b = synth.make_batch(3, B=160)  # mostly small structures, a few above 128 atoms
+    assert int(np.diff(b.atom_ptr).max()) > 128
+    batch = to_device(b)
+    g = mg.cutoff_graph(batch, 5.0, with_perm=False)
+    gl = torch.from_numpy(synth.normal(12, 0, g.num_edges)).cuda()
+    v, ln = mg.edge_vectors_fwd(g)
+    f1, L1 = mg.edge_vectors_bwd(g, batch, None, gl, v, ln)
+    mg.rebuild(g, per_structure=True)
+    v2, ln2 = mg.edge_vectors_fwd(g)
+    assert torch.equal(v, v2) and torch.equal(ln, ln2)
+    f2, L2 = mg.edge_vectors_bwd(g, batch, None, gl, v2, ln2)
+    assert torch.equal(f1, f2) and torch.equal(L1, L2)
+    grad_check(b, g, synth.normal(12, 0, g.num_edges))
