@@ -344,18 +344,20 @@ def run_mine(args, rank, world, local_rank):
     host_out = {}
 
     def e2e_step():
+        # inputs in, both graphs rebuilt, loss backward, every output back; the host waits
+        # once, at the end, and then checks both status words it copied back with the rest
         batch.frac.copy_(frac_h, non_blocking=True)
         batch.lattice.copy_(lat_h, non_blocking=True)
         batch.atom_ptr.copy_(ptr_h, non_blocking=True)
-        gc = mg.update_graph(g_cut)
-        gk = mg.update_graph(g_knn)
+        mg.update_graph(g_cut, sync=False)
+        mg.update_graph(g_knn, sync=False)
         fr = batch.frac.detach().requires_grad_(True)
         la = batch.lattice.detach().requires_grad_(True)
-        vec, ln = mg.edge_vectors(fr, la, gc)
-        (ln * w_dev[:gc.num_edges]).sum().backward()
-        outs = [gc.src[:gc.num_edges], gc.dst[:gc.num_edges], gc.offset[:gc.num_edges], vec.detach(),
-                ln.detach(), gk.src[:gk.num_edges], gk.dst[:gk.num_edges], gk.offset[:gk.num_edges],
-                gk.vec[:gk.num_edges], gk.len[:gk.num_edges], fr.grad, la.grad]
+        vec, ln = mg.edge_vectors(fr, la, g_cut)
+        (ln * w_dev).sum().backward()
+        outs = [g_cut.status, g_knn.status, g_cut.src[:E_cut], g_cut.dst[:E_cut], g_cut.offset[:E_cut],
+                vec.detach(), ln.detach(), g_knn.src[:E_knn], g_knn.dst[:E_knn], g_knn.offset[:E_knn],
+                g_knn.vec[:E_knn], g_knn.len[:E_knn], fr.grad, la.grad]
         d2h = 0
         for q, t in enumerate(outs):
             if q not in host_out or host_out[q].shape != t.shape:
@@ -363,7 +365,9 @@ def run_mine(args, rank, world, local_rank):
             host_out[q].copy_(t, non_blocking=True)
             d2h += t.numel() * t.element_size()
         torch.cuda.synchronize(dev)
-        return gc.num_edges + gk.num_edges, d2h
+        for q, E in ((0, E_cut), (1, E_knn)):  # code 0 and the same edge count as the first build
+            assert int(host_out[q][0]) & 0xFFFFFFFF == 0 and int(host_out[q][1]) == E, host_out[q]
+        return E_cut + E_knn, d2h
 
     e2e_step()
     e2e_t, e2e_units, d2h = 0.0, 0, 0

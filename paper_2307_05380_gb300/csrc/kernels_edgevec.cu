@@ -28,23 +28,37 @@ __device__ __forceinline__ int structure_of(const int32_t *__restrict__ atom_ptr
     return lo;
 }
 
+// A thread per edge (grid-stride): every edge is independent, so the forward runs at
+// full occupancy whatever the degrees.  The structure of an edge comes from edge_ptr:
+// one binary search per warp for its first edge, then a forward step per lane when the
+// warp's 32 edges straddle a structure boundary.
 __global__ void __launch_bounds__(256) edgevec_fwd_kernel(EdgeVecArgs a) {
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = lane_id();
-    if (i >= a.N) return;
     const int64_t E = a.g.edge_ptr[a.B];
     if (E > a.g.capacity) return;
-    const int64_t lo = a.g.src_ptr[i], hi = a.g.src_ptr[i + 1];
-    if (hi <= lo) return;
-    const int s = structure_of(a.atom_ptr, a.B, i);
-    float L[9];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) L[q] = a.lattice[9 * (int64_t)s + q];
-    const float xi0 = a.frac[3 * (int64_t)i], xi1 = a.frac[3 * (int64_t)i + 1], xi2 = a.frac[3 * (int64_t)i + 2];
-    for (int64_t e = lo + lane; e < hi; e += 32) {
-        const int64_t j = a.g.dst[e];
+    const int lane = lane_id();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < E; w0 += stride) {
+        int s0 = 0;
+        if (lane == 0) {  // last structure whose first edge is <= w0
+            int lo = 0, hi = a.B;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (a.g.edge_ptr[mid] <= w0) lo = mid;
+                else hi = mid;
+            }
+            s0 = lo;
+        }
+        s0 = __shfl_sync(FULL, s0, 0);
+        const int64_t e = w0 + lane;
+        if (e >= E) continue;
+        int s = s0;
+        while (s + 1 < a.B && a.g.edge_ptr[s + 1] <= e) ++s;
+        const float *L = a.lattice + 9 * (int64_t)s;
+        const int64_t i = a.g.src[e], j = a.g.dst[e];
         const int t0 = a.g.offset[3 * e], t1 = a.g.offset[3 * e + 1], t2 = a.g.offset[3 * e + 2];
-        const float3 v = edge_vec_ff(L, xi0, xi1, xi2, a.frac[3 * j], a.frac[3 * j + 1], a.frac[3 * j + 2], t0, t1, t2);
+        const float Ls[9] = {L[0], L[1], L[2], L[3], L[4], L[5], L[6], L[7], L[8]};
+        const float3 v = edge_vec_ff(Ls, a.frac[3 * i], a.frac[3 * i + 1], a.frac[3 * i + 2], a.frac[3 * j],
+                                     a.frac[3 * j + 1], a.frac[3 * j + 2], t0, t1, t2);
         if (a.out_vec) {
             a.out_vec[3 * e] = v.x;
             a.out_vec[3 * e + 1] = v.y;
@@ -56,7 +70,11 @@ __global__ void __launch_bounds__(256) edgevec_fwd_kernel(EdgeVecArgs a) {
 
 cudaError_t launch_edgevec_fwd(const EdgeVecArgs &a, cudaStream_t s) {
     if (a.N <= 0) return cudaSuccess;
-    edgevec_fwd_kernel<<<(a.N + 7) / 8, 256, 0, s>>>(a);
+    // the edge count lives on the device: enough threads for every edge of a graph of
+    // up to the capacity, capped at 16 blocks per SM (grid-stride beyond)
+    const int64_t want = (a.g.capacity + 255) / 256;
+    const int blocks = (int)(want < 16 * num_sms() ? (want > 0 ? want : 1) : 16 * num_sms());
+    edgevec_fwd_kernel<<<blocks, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

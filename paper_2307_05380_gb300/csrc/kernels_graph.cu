@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(GROUP == 32 ? 128 : GROUP) prep_kernel(PrepArg
 
 cudaError_t launch_prep(const PrepArgs &a, const Work &w, cudaStream_t s) {
     if (a.B <= 0) return cudaSuccess;
-    if (a.max_atoms > 0 && a.max_atoms <= 256) {  // a warp per structure
+    if (a.max_atoms > 0 && a.max_atoms <= 2048) {  // a warp per structure (a few loads per lane)
         const int blocks = (a.B * 32 + 127) / 128;
         prep_kernel<32><<<blocks, 128, 0, s>>>(a, w.recs, w.pos, w.atom_struct, w.tile_flags, w.queue);
     } else {  // a block per structure

@@ -3,21 +3,25 @@
 // One warp per source atom.  Alg. 1 grows the evaluated area until the k-th distance
 // d^max_i is covered; Alg. 2 keeps the k closest in an "ordered stack".  Here:
 //   pass 1  scan every image within radius rho (interplanar box, mg_enum.cuh) and keep
-//           the k smallest FP32 squared distances in registers: a sorted 32*S-entry
+//           the 32*S nearest images (FP32 d2 with their j and t) in registers: a sorted
 //           array spread over the lanes, updated by warp-shuffle bitonic merges.  If
 //           fewer than k images lie within rho, or the k-th distance tau is not covered
 //           by rho with the error band to spare, rho grows and the pass repeats (the
 //           covered-radius test plays the role of closest_distance(border, rho)).
-//   pass 2  the same scan again: images with FP32 d2 < tau - 2 delta are certainly
-//           among the k nearest; images within tau +- 2 delta (the band) are staged in
-//           shared memory.  If the band holds exactly the slots left, all of it is
-//           taken; otherwise it is ranked by the canonical FP64 distance with the
-//           (d2, j, t) tie-break in a second register top-k (GB300's FP64 rate is low,
-//           so FP64 runs only when the order inside the band decides membership).  The
-//           k winners are sorted by (j, t) and written in canonical order.
+//   select  images with FP32 d2 < tau - 2 delta are certainly among the k nearest;
+//           images within tau +- 2 delta form the band.  When the kept images reach
+//           past the band (32*S > k leaves slack) both sets are read from registers;
+//           otherwise pass 2 scans again, staging the band in shared memory.  If the band
+//           holds exactly the slots left, all of it is taken; otherwise it is ranked by
+//           the canonical FP64 distance with the (d2, j, t) tie-break in a second
+//           register top-k (GB300's FP64 rate is low, so FP64 runs only when the order
+//           inside the band decides membership).  The k winners are sorted by (j, t) and
+//           written in canonical order.
 //           Keep-ties mode (Alg. 2's filter d <= d^k_i) writes only the k-th canonical
 //           d2 of each atom; the one-pass cutoff build then emits every image that close.
 // delta bounds the FP32 error (fp32_d2_error) plus the requested band.
+#include <type_traits>
+
 #include "mg_device.cuh"
 #include "mg_enum.cuh"
 #include "mg_launch.h"
@@ -47,6 +51,22 @@ __device__ __forceinline__ XKey kxor(XKey k, int m) {
 }
 __device__ __forceinline__ bool kless(XKey a, XKey b) { return a.d < b.d || (a.d == b.d && a.jt < b.jt); }
 __device__ __forceinline__ XKey kinf(XKey) { return XKey{~0ull, ~0ull}; }
+
+// FP32 key with the candidate's (local j << 32 | packed t): pass 1 keeps the 32 S nearest
+// images themselves, ordered by (d2, j, t).
+struct CKey {
+    float v;
+    unsigned long long jt;
+};
+__device__ __forceinline__ CKey kshfl(CKey k, int src) {
+    return CKey{__shfl_sync(FULL, k.v, src), __shfl_sync(FULL, k.jt, src)};
+}
+__device__ __forceinline__ CKey kxor(CKey k, int m) {
+    return CKey{__shfl_xor_sync(FULL, k.v, m), __shfl_xor_sync(FULL, k.jt, m)};
+}
+__device__ __forceinline__ bool kless(CKey a, CKey b) { return a.v < b.v || (a.v == b.v && a.jt < b.jt); }
+__device__ __forceinline__ CKey kinf(CKey) { return CKey{F_INF, ~0ull}; }
+constexpr unsigned long long JT_OUT_OF_RANGE = ~0ull - 1;  // an offset the packed key cannot hold
 
 template <class K>
 __device__ __forceinline__ K kmin(K a, K b) { return kless(b, a) ? b : a; }
@@ -141,8 +161,12 @@ constexpr int BAND_CAP = 64;  // band candidates staged per source in shared mem
 
 // At most 85 registers (6 blocks of 4 warps per SM): measured faster than 128 registers
 // (fewer resident warps) and than 64 (more spills) on the bench workloads.
-template <int S, int SCHED>
+// ONEPASS: pass 1 keeps (d2, j, t) keys and the selection usually reads them from
+// registers; otherwise pass 1 keeps FP32 distances only (fewer registers and shuffles)
+// and pass 2 always scans again.
+template <int S, int SCHED, bool ONEPASS>
 __global__ void __launch_bounds__(KNN_WARPS * 32, 6) knn_kernel(BuildArgs a, Work w) {
+    using PKey = typename std::conditional<ONEPASS, CKey, FKey>::type;
     __shared__ unsigned long long sel_all[KNN_WARPS][S * 32 > 64 ? S * 32 : 64];
     __shared__ unsigned long long band_all[KNN_WARPS][BAND_CAP];
     const int wid = threadIdx.x >> 5, lane = lane_id();
@@ -165,26 +189,42 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 6) knn_kernel(BuildArgs a, Wor
         Source Src;
         load_source(Src, w.recs, s, a.frac, w.pos, i);
 
-        // ---------------- pass 1: grow rho until the k-th FP32 distance is covered
+        // ---------------- pass 1: grow rho until the k-th FP32 distance is covered; the
+        // 32 S nearest images are kept with their (j, t)
         float rho = R.cut, tau = F_INF, delta = 0.f;
         bool ok = false;
+        TopK<PKey, S> tk;
         for (int iter = 0; iter < 64 && !ok; ++iter) {
-            TopK<FKey, S> tk;
             tk.init();
             float thr = F_INF;
             int found = 0;
             const float rho2 = rho * rho;
-            for_each_candidate(Src, a.frac, w.pos, cells, true, rho,[&](bool vc, float d2, bool self, int, int,
-                                                              const RowRegs &) {
+            for_each_candidate(Src, a.frac, w.pos, cells, true, rho, [&](bool vc, float d2, bool self, int ow,
+                                                                          int t2, const RowRegs &rw) {
                 const bool c = vc && !self && d2 < rho2;
                 found += __popc(__ballot_sync(FULL, c));
                 const float v = c ? d2 : F_INF;
                 if (__any_sync(FULL, v < thr)) {
-                    tk.insert(FKey{v < thr ? v : F_INF});
-                    thr = tk.kth(k).v;
+                    const bool ins = v < thr;
+                    if constexpr (ONEPASS) {
+                        const int jj = __shfl_sync(FULL, rw.j, ow);
+                        const int t0 = __shfl_sync(FULL, rw.t0, ow);
+                        const int t1 = __shfl_sync(FULL, rw.t1, ow);
+                        unsigned long long jt = ~0ull;
+                        if (ins)
+                            jt = (abs(t0) > OFFSET_KEY_LIM || abs(t1) > OFFSET_KEY_LIM || abs(t2) > OFFSET_KEY_LIM)
+                                     ? JT_OUT_OF_RANGE
+                                     : (((unsigned long long)(unsigned)jj << 32) | pack_t(t0, t1, t2));
+                        tk.insert(CKey{ins ? v : F_INF, jt});
+                        thr = tk.kth(32 * S).v;  // the kept images are the 32 S nearest seen
+                    } else {
+                        tk.insert(FKey{ins ? v : F_INF});
+                        thr = tk.kth(k).v;
+                    }
                 }
                 if (a.collect_stats) ncand += __popc(__ballot_sync(FULL, vc && !self));
             });
+            thr = tk.kth(k).v;
             delta = fp32_d2_error(R, rho, rho2) + 2.0f * a.band_rel * rho2;
             if (found >= k && thr + 3.0f * delta < rho2) {
                 tau = thr;
@@ -201,122 +241,203 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 6) knn_kernel(BuildArgs a, Wor
             continue;
         }
 
-        // ---------------- pass 2: certain members; the band is staged, then ranked only
-        // if it holds more candidates than the slots left (FP64 only in that case)
         const float lo_thr = tau - 2.0f * delta, hi_thr = tau + 2.0f * delta;
-        int m = 0, nb = 0;
-        bool range_bad = false;
-        for_each_candidate(Src, a.frac, w.pos, cells, true, rho, [&](bool vc, float d2, bool self, int ow, int t2,
-                                                                      const RowRegs &rw) {
-            const bool c = vc && !self;
-            const bool in = c && d2 < lo_thr;
-            const bool band = c && !in && d2 <= hi_thr;
-            if (__any_sync(FULL, in || band)) {
-                const int jj = __shfl_sync(FULL, rw.j, ow);
-                const int t0 = __shfl_sync(FULL, rw.t0, ow);
-                const int t1 = __shfl_sync(FULL, rw.t1, ow);
-                if ((in || band) && (abs(t0) > OFFSET_KEY_LIM || abs(t1) > OFFSET_KEY_LIM || abs(t2) > OFFSET_KEY_LIM))
-                    range_bad = true;
-                const unsigned long long jt = ((unsigned long long)(unsigned)jj << 32) | pack_t(t0, t1, t2);
-                const unsigned bin = __ballot_sync(FULL, in);
-                if (in) {
-                    const int p = m + __popc(bin & lt);
-                    if (p < k) sel[p] = jt;
-                }
-                m += __popc(bin);
-                const unsigned bb = __ballot_sync(FULL, band);
-                if (band) {
-                    const int p = nb + __popc(bb & lt);
-                    if (p < BAND_CAP) bl[p] = jt;
-                }
-                nb += __popc(bb);
+        unsigned long long dk_bits = 0;  // keep-ties mode: the k-th canonical d2
+        bool spare = false;
+        if constexpr (ONEPASS) spare = tk.kth(32 * S).v > hi_thr;
+        if (spare) {
+          if constexpr (ONEPASS) {
+            // ---------------- the kept images hold every certain member (FP32 d2 below
+            // tau - 2 delta) and the whole band: no second scan.  Ranks [0, m) are
+            // certain, [m, m + nb) the band, ranked in FP64 only if it holds more
+            // candidates than the slots left.
+            int m = 0, nb = 0;
+            bool range_bad = false;
+#pragma unroll
+            for (int q = 0; q < S; ++q) {
+                const CKey c = tk.a[q];
+                m += __popc(__ballot_sync(FULL, c.v < lo_thr));
+                nb += __popc(__ballot_sync(FULL, c.v >= lo_thr && c.v <= hi_thr));
+                if (c.v <= hi_thr && c.jt == JT_OUT_OF_RANGE) range_bad = true;
             }
-        });
-        if (__any_sync(FULL, range_bad)) {
-            if (lane == 0) set_error(g.status, MG_ERR_OFFSET_RANGE, s);
-            continue;
-        }
-        if (m >= k || m + nb < k) {  // cannot happen: fewer than k FP32 distances lie below tau
-            if (lane == 0) set_error(g.status, MG_ERR_INTERNAL, s);
-            continue;
-        }
-        const int need = k - m;
-        __syncwarp();
-        // the k-th canonical d2 (keep-ties mode): the largest selected band member, since
-        // every certain member lies below tau - delta and the k-th distance does not
-        unsigned long long dk_bits = 0;
-        if (nb == need && nb <= BAND_CAP) {  // every band member fills a remaining slot
-            for (int q = lane; q < nb; q += 32) sel[m + q] = bl[q];
-            if (a.knn_dk) {
-                for (int q = lane; q < nb; q += 32) {
-                    const unsigned long long jt = bl[q];
-                    int t0, t1, t2;
-                    unpack_t((uint32_t)(jt & 0xffffffffull), t0, t1, t2);
-                    const int64_t jr = (int64_t)Src.begin + (int)(jt >> 32);
-                    const double d = canon_d2(Src.L, Src.xi0, Src.xi1, Src.xi2, a.frac[3 * jr], a.frac[3 * jr + 1],
-                                              a.frac[3 * jr + 2], t0, t1, t2);
-                    const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
-                    dk_bits = bits > dk_bits ? bits : dk_bits;  // non-negative: bits order like values
+            if (__any_sync(FULL, range_bad)) {
+                if (lane == 0) set_error(g.status, MG_ERR_OFFSET_RANGE, s);
+                continue;
+            }
+            if (m >= k || m + nb < k) {  // cannot happen: fewer than k FP32 distances lie below tau
+                if (lane == 0) set_error(g.status, MG_ERR_INTERNAL, s);
+                continue;
+            }
+            const int need = k - m;
+            if (nb == need) {  // every band member fills a remaining slot
+#pragma unroll
+                for (int q = 0; q < S; ++q) {
+                    const int r = 32 * q + lane;
+                    if (r < k) sel[r] = tk.a[q].jt;
+                    if (a.knn_dk && r >= m && r < k) {
+                        const unsigned long long jt = tk.a[q].jt;
+                        int t0, t1, t2;
+                        unpack_t((uint32_t)(jt & 0xffffffffull), t0, t1, t2);
+                        const int64_t jr = (int64_t)Src.begin + (int)(jt >> 32);
+                        const double d = canon_d2(Src.L, Src.xi0, Src.xi1, Src.xi2, a.frac[3 * jr],
+                                                  a.frac[3 * jr + 1], a.frac[3 * jr + 2], t0, t1, t2);
+                        const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
+                        dk_bits = bits > dk_bits ? bits : dk_bits;
+                    }
+                }
+                if (a.knn_dk) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const unsigned long long y = __shfl_xor_sync(FULL, dk_bits, o);
+                        dk_bits = y > dk_bits ? y : dk_bits;
+                    }
+                }
+            } else {  // rank the band by (canonical FP64 d2, j, t)
+                if (a.collect_stats) nre += nb;
+                TopK<XKey, S> ek;
+                ek.init();
+#pragma unroll
+                for (int q = 0; q < S; ++q) {
+                    const int r = 32 * q + lane;
+                    const unsigned long long jt = tk.a[q].jt;
+                    if (r < m) sel[r] = jt;
+                    XKey key = kinf(XKey{});
+                    if (r >= m && r < m + nb) {
+                        int t0, t1, t2;
+                        unpack_t((uint32_t)(jt & 0xffffffffull), t0, t1, t2);
+                        const int64_t jr = (int64_t)Src.begin + (int)(jt >> 32);
+                        const double d = canon_d2(Src.L, Src.xi0, Src.xi1, Src.xi2, a.frac[3 * jr],
+                                                  a.frac[3 * jr + 1], a.frac[3 * jr + 2], t0, t1, t2);
+                        key = XKey{(unsigned long long)__double_as_longlong(d), jt};
+                    }
+                    ek.insert(key);
                 }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const unsigned long long y = __shfl_xor_sync(FULL, dk_bits, o);
-                    dk_bits = y > dk_bits ? y : dk_bits;
+                for (int q = 0; q < S; ++q) {
+                    const int p = q * 32 + lane;
+                    if (p < need) sel[m + p] = ek.a[q].jt;
                 }
+                if (a.knn_dk) dk_bits = ek.kth(need).d;
             }
-        } else {  // rank the band by (canonical FP64 d2, j, t)
-            TopK<XKey, S> ek;
-            ek.init();
-            if (a.collect_stats) nre += nb;
-            if (nb <= BAND_CAP) {
-                for (int b0 = 0; b0 < nb; b0 += 32) {
-                    const int q = b0 + lane;
-                    XKey key = kinf(XKey{});
-                    if (q < nb) {
+            __syncwarp();
+          }
+        } else {
+            // ---------------- pass 2 (the band reaches past the kept images): certain members;
+            // the band is staged, then ranked only if it holds more candidates than the slots
+            // left (FP64 only in that case)
+            int m = 0, nb = 0;
+            bool range_bad = false;
+            for_each_candidate(Src, a.frac, w.pos, cells, true, rho, [&](bool vc, float d2, bool self, int ow, int t2,
+                                                                          const RowRegs &rw) {
+                const bool c = vc && !self;
+                const bool in = c && d2 < lo_thr;
+                const bool band = c && !in && d2 <= hi_thr;
+                if (__any_sync(FULL, in || band)) {
+                    const int jj = __shfl_sync(FULL, rw.j, ow);
+                    const int t0 = __shfl_sync(FULL, rw.t0, ow);
+                    const int t1 = __shfl_sync(FULL, rw.t1, ow);
+                    if ((in || band) && (abs(t0) > OFFSET_KEY_LIM || abs(t1) > OFFSET_KEY_LIM || abs(t2) > OFFSET_KEY_LIM))
+                        range_bad = true;
+                    const unsigned long long jt = ((unsigned long long)(unsigned)jj << 32) | pack_t(t0, t1, t2);
+                    const unsigned bin = __ballot_sync(FULL, in);
+                    if (in) {
+                        const int p = m + __popc(bin & lt);
+                        if (p < k) sel[p] = jt;
+                    }
+                    m += __popc(bin);
+                    const unsigned bb = __ballot_sync(FULL, band);
+                    if (band) {
+                        const int p = nb + __popc(bb & lt);
+                        if (p < BAND_CAP) bl[p] = jt;
+                    }
+                    nb += __popc(bb);
+                }
+            });
+            if (__any_sync(FULL, range_bad)) {
+                if (lane == 0) set_error(g.status, MG_ERR_OFFSET_RANGE, s);
+                continue;
+            }
+            if (m >= k || m + nb < k) {  // cannot happen: fewer than k FP32 distances lie below tau
+                if (lane == 0) set_error(g.status, MG_ERR_INTERNAL, s);
+                continue;
+            }
+            const int need = k - m;
+            __syncwarp();
+            // the k-th canonical d2 (keep-ties mode): the largest selected band member, since
+            // every certain member lies below tau - delta and the k-th distance does not
+            if (nb == need && nb <= BAND_CAP) {  // every band member fills a remaining slot
+                for (int q = lane; q < nb; q += 32) sel[m + q] = bl[q];
+                if (a.knn_dk) {
+                    for (int q = lane; q < nb; q += 32) {
                         const unsigned long long jt = bl[q];
                         int t0, t1, t2;
                         unpack_t((uint32_t)(jt & 0xffffffffull), t0, t1, t2);
                         const int64_t jr = (int64_t)Src.begin + (int)(jt >> 32);
                         const double d = canon_d2(Src.L, Src.xi0, Src.xi1, Src.xi2, a.frac[3 * jr], a.frac[3 * jr + 1],
                                                   a.frac[3 * jr + 2], t0, t1, t2);
-                        key = XKey{(unsigned long long)__double_as_longlong(d), jt};
+                        const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
+                        dk_bits = bits > dk_bits ? bits : dk_bits;  // non-negative: bits order like values
                     }
-                    ek.insert(key);
-                }
-            } else {  // the band did not fit in shared memory: stream it again with FP64 keys
-                XKey ethr = kinf(XKey{});
-                for_each_candidate(Src, a.frac, w.pos, cells, true, rho, [&](bool vc, float d2, bool self, int ow,
-                                                                              int t2, const RowRegs &rw) {
-                    const bool c = vc && !self;
-                    const bool band = c && d2 >= lo_thr && d2 <= hi_thr;
-                    if (__any_sync(FULL, band)) {
-                        const int jj = __shfl_sync(FULL, rw.j, ow);
-                        const int t0 = __shfl_sync(FULL, rw.t0, ow);
-                        const int t1 = __shfl_sync(FULL, rw.t1, ow);
-                        XKey key = kinf(XKey{});
-                        if (band) {
-                            const int64_t jr = (int64_t)Src.begin + jj;
-                            const double d = canon_d2(Src.L, Src.xi0, Src.xi1, Src.xi2, a.frac[3 * jr],
-                                                      a.frac[3 * jr + 1], a.frac[3 * jr + 2], t0, t1, t2);
-                            key = XKey{(unsigned long long)__double_as_longlong(d),
-                                       ((unsigned long long)(unsigned)jj << 32) | pack_t(t0, t1, t2)};
-                        }
-                        const bool ins = band && kless(key, ethr);
-                        if (__any_sync(FULL, ins)) {
-                            ek.insert(ins ? key : kinf(XKey{}));
-                            ethr = ek.kth(k);
-                        }
-                    }
-                });
-            }
 #pragma unroll
-            for (int q = 0; q < S; ++q) {
-                const int p = q * 32 + lane;
-                if (p < need) sel[m + p] = ek.a[q].jt;
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const unsigned long long y = __shfl_xor_sync(FULL, dk_bits, o);
+                        dk_bits = y > dk_bits ? y : dk_bits;
+                    }
+                }
+            } else {  // rank the band by (canonical FP64 d2, j, t)
+                TopK<XKey, S> ek;
+                ek.init();
+                if (a.collect_stats) nre += nb;
+                if (nb <= BAND_CAP) {
+                    for (int b0 = 0; b0 < nb; b0 += 32) {
+                        const int q = b0 + lane;
+                        XKey key = kinf(XKey{});
+                        if (q < nb) {
+                            const unsigned long long jt = bl[q];
+                            int t0, t1, t2;
+                            unpack_t((uint32_t)(jt & 0xffffffffull), t0, t1, t2);
+                            const int64_t jr = (int64_t)Src.begin + (int)(jt >> 32);
+                            const double d = canon_d2(Src.L, Src.xi0, Src.xi1, Src.xi2, a.frac[3 * jr], a.frac[3 * jr + 1],
+                                                      a.frac[3 * jr + 2], t0, t1, t2);
+                            key = XKey{(unsigned long long)__double_as_longlong(d), jt};
+                        }
+                        ek.insert(key);
+                    }
+                } else {  // the band did not fit in shared memory: stream it again with FP64 keys
+                    XKey ethr = kinf(XKey{});
+                    for_each_candidate(Src, a.frac, w.pos, cells, true, rho, [&](bool vc, float d2, bool self, int ow,
+                                                                                  int t2, const RowRegs &rw) {
+                        const bool c = vc && !self;
+                        const bool band = c && d2 >= lo_thr && d2 <= hi_thr;
+                        if (__any_sync(FULL, band)) {
+                            const int jj = __shfl_sync(FULL, rw.j, ow);
+                            const int t0 = __shfl_sync(FULL, rw.t0, ow);
+                            const int t1 = __shfl_sync(FULL, rw.t1, ow);
+                            XKey key = kinf(XKey{});
+                            if (band) {
+                                const int64_t jr = (int64_t)Src.begin + jj;
+                                const double d = canon_d2(Src.L, Src.xi0, Src.xi1, Src.xi2, a.frac[3 * jr],
+                                                          a.frac[3 * jr + 1], a.frac[3 * jr + 2], t0, t1, t2);
+                                key = XKey{(unsigned long long)__double_as_longlong(d),
+                                           ((unsigned long long)(unsigned)jj << 32) | pack_t(t0, t1, t2)};
+                            }
+                            const bool ins = band && kless(key, ethr);
+                            if (__any_sync(FULL, ins)) {
+                                ek.insert(ins ? key : kinf(XKey{}));
+                                ethr = ek.kth(k);
+                            }
+                        }
+                    });
+                }
+#pragma unroll
+                for (int q = 0; q < S; ++q) {
+                    const int p = q * 32 + lane;
+                    if (p < need) sel[m + p] = ek.a[q].jt;
+                }
+                if (a.knn_dk) dk_bits = ek.kth(need).d;
             }
-            if (a.knn_dk) dk_bits = ek.kth(need).d;
-        }
-        __syncwarp();
+            __syncwarp();
+        }  // pass 2
         if (a.knn_dk) {  // keep-ties mode: the radius only; a cutoff pass emits the edges
             if (lane == 0) a.knn_dk[i] = __longlong_as_double((long long)dk_bits);
             continue;
@@ -375,7 +496,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 6) knn_kernel(BuildArgs a, Wor
     }
 }
 
-template <int S>
+template <int S, bool ONEPASS>
 static cudaError_t launch_knn_s(const BuildArgs &a, const Work &w, cudaStream_t s) {
     const int atoms = a.atom_hi - a.atom_lo;
     const int threads = KNN_WARPS * 32;
@@ -384,21 +505,25 @@ static cudaError_t launch_knn_s(const BuildArgs &a, const Work &w, cudaStream_t 
         cudaError_t e = launch_reset_queue(w, s);
         if (e) return e;
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, knn_kernel<S, 2>, threads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, knn_kernel<S, 2, ONEPASS>, threads, 0);
         int blocks = max(1, per_sm) * num_sms();
         blocks = min(blocks, flat_blocks);
-        knn_kernel<S, 2><<<blocks, threads, 0, s>>>(a, w);
+        knn_kernel<S, 2, ONEPASS><<<blocks, threads, 0, s>>>(a, w);
     } else {
-        knn_kernel<S, 1><<<flat_blocks, threads, 0, s>>>(a, w);
+        knn_kernel<S, 1, ONEPASS><<<flat_blocks, threads, 0, s>>>(a, w);
     }
     return cudaGetLastError();
 }
 
+// k <= 24: one warp-wide block of keys (d2, j, t) holds k plus at least 8 spare images,
+// so the band usually fits and the second scan is skipped.  Larger k: FP32 distances
+// only and two scans (measured faster at k = 32 than 64 keys with their (j, t)).
 cudaError_t launch_knn(const BuildArgs &a, const Work &w, cudaStream_t s) {
     if (a.atom_hi <= a.atom_lo) return cudaSuccess;
-    if (a.knn_k <= 32) return launch_knn_s<1>(a, w, s);
-    if (a.knn_k <= 64) return launch_knn_s<2>(a, w, s);
-    return launch_knn_s<4>(a, w, s);
+    if (a.knn_k <= 24) return launch_knn_s<1, true>(a, w, s);
+    if (a.knn_k <= 32) return launch_knn_s<1, false>(a, w, s);
+    if (a.knn_k <= 64) return launch_knn_s<2, false>(a, w, s);
+    return launch_knn_s<4, false>(a, w, s);
 }
 
 // src_ptr[i] = k i, edge_ptr[s] = k atom_ptr[s], status counts.

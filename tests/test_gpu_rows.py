@@ -314,3 +314,16 @@ def test_symmetric_backward_pair_table_and_search_paths_identical():
     f2, L2 = mg.edge_vectors_bwd(g, batch, None, gl, v2, ln2)
     assert torch.equal(f1, f2) and torch.equal(L1, L2)
     grad_check(b, g, synth.normal(12, 0, g.num_edges))
+
+
+def test_knn_band_past_the_kept_images_takes_the_second_scan():
+    """FCC shells hold 12, 6 and 24 images: at k = 20 the k-th distance lies in a shell
+    that runs past the 32 images pass 1 keeps, so the selection scans again; exact-k
+    ties broken by (d2, j, t) and keep-ties (all 42) both match the oracle."""
+    a = 3.0
+    b = synth.crystal(np.asarray(GOLD["knn_keep_ties_fcc"]["lattice_over_a"]) * a, [[0, 0, 0]])
+    g = mg.knn_graph(to_device(b), 20)
+    got = graph_arrays(g)
+    assert_same_edges(got, oracle.knn(b.lattice, b.frac, b.atom_ptr, 20), "fcc k=20")
+    gt, _ = ties_parity(b, 20)
+    assert gt.num_edges == 42
