@@ -109,7 +109,12 @@ typedef struct {
                               image whose canonical d2 is <= the k-th one (ties at the k-th
                               distance all kept, so >= k edges per atom; the capacity then
                               works as for a cutoff graph).  Other values: invalid argument */
-    int32_t schedule;      /* 0 auto (tuned), 1 flat grid, 2 persistent work queue (KNN) */
+    int32_t schedule;      /* 0 auto (tuned), 1 flat grid, 2 persistent work queue (KNN).
+                              Cutoff builds: auto picks the one-pass build (decoupled
+                              look-back) below 8192 atoms and the staged build (scan and
+                              stage keys, scan the counts, write) from there when the
+                              workspace covers the capacity; 3 forces the one-pass build,
+                              4 the staged one (if the workspace covers the capacity) */
     int32_t collect_stats; /* 1: count FP32 candidates and FP64 re-tests into status */
     int32_t fault_tile;    /* -1.  Testing only: the one-pass cutoff build's tile with this
                               index never publishes its offset, so the bounded waits of the

@@ -28,30 +28,30 @@ __device__ __forceinline__ int structure_of(const int32_t *__restrict__ atom_ptr
     return lo;
 }
 
-// A thread per edge (grid-stride): every edge is independent, so the forward runs at
-// full occupancy whatever the degrees.  The structure of an edge comes from edge_ptr:
-// one binary search per warp for its first edge, then a forward step per lane when the
-// warp's 32 edges straddle a structure boundary.
+// A thread per edge: every edge is independent, so the forward runs at full occupancy
+// whatever the degrees.  Each warp takes one contiguous range of edges, 32 at a time,
+// so the structure of an edge (from edge_ptr) is found by one binary search per warp and
+// then only moves forward.
 __global__ void __launch_bounds__(256) edgevec_fwd_kernel(EdgeVecArgs a) {
     const int64_t E = a.g.edge_ptr[a.B];
     if (E > a.g.capacity) return;
     const int lane = lane_id();
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < E; w0 += stride) {
-        int s0 = 0;
-        if (lane == 0) {  // last structure whose first edge is <= w0
-            int lo = 0, hi = a.B;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (a.g.edge_ptr[mid] <= w0) lo = mid;
-                else hi = mid;
-            }
-            s0 = lo;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t chunk = ((E + warps - 1) / warps + 31) & ~(int64_t)31;
+    const int64_t e0 = wid * chunk, e1 = min(E, e0 + chunk);
+    if (e0 >= e1) return;
+    int s = 0;  // last structure whose first edge is <= e0
+    {
+        int lo = 0, hi = a.B;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (a.g.edge_ptr[mid] <= e0) lo = mid;
+            else hi = mid;
         }
-        s0 = __shfl_sync(FULL, s0, 0);
-        const int64_t e = w0 + lane;
-        if (e >= E) continue;
-        int s = s0;
+        s = lo;
+    }
+    for (int64_t e = e0 + lane; e < e1; e += 32) {
         while (s + 1 < a.B && a.g.edge_ptr[s + 1] <= e) ++s;
         const float *L = a.lattice + 9 * (int64_t)s;
         const int64_t i = a.g.src[e], j = a.g.dst[e];
@@ -70,8 +70,8 @@ __global__ void __launch_bounds__(256) edgevec_fwd_kernel(EdgeVecArgs a) {
 
 cudaError_t launch_edgevec_fwd(const EdgeVecArgs &a, cudaStream_t s) {
     if (a.N <= 0) return cudaSuccess;
-    // the edge count lives on the device: enough threads for every edge of a graph of
-    // up to the capacity, capped at 16 blocks per SM (grid-stride beyond)
+    // the edge count lives on the device: one thread per edge of a graph of up to the
+    // capacity, capped at 16 blocks per SM (longer ranges per warp beyond)
     const int64_t want = (a.g.capacity + 255) / 256;
     const int blocks = (int)(want < 16 * num_sms() ? (want > 0 ? want : 1) : 16 * num_sms());
     edgevec_fwd_kernel<<<blocks, 256, 0, s>>>(a);
@@ -213,17 +213,17 @@ __global__ void __launch_bounds__(256) bwd_dst_kernel(EdgeVecArgs a, const float
     }
 }
 
-__global__ void __launch_bounds__(256) bwd_lat_kernel(EdgeVecArgs a, const float2 *__restrict__ lpart) {
-    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// One warp: the lattice gradient of structure s from its atoms' partials, in atom order
+// per lane and a fixed butterfly (deterministic).
+__device__ __forceinline__ void lattice_reduce_warp(const EdgeVecArgs &a, const float2 *__restrict__ lpart, int s) {
     const int lane = lane_id();
-    if (s >= a.B) return;
     const int lo = a.atom_ptr[s], hi = a.atom_ptr[s + 1];
     float2 acc[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) acc[q] = make_float2(0.f, 0.f);
     for (int r = lo + lane; r < hi; r += 32)
 #pragma unroll
-        for (int q = 0; q < 9; ++q) acc[q] = ff_add(acc[q], lpart[9 * (int64_t)r + q]);
+        for (int q = 0; q < 9; ++q) acc[q] = ff_add(acc[q], __ldcg(&lpart[9 * (int64_t)r + q]));  // L2: written by other SMs
     float out = 0.f;
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
@@ -232,6 +232,12 @@ __global__ void __launch_bounds__(256) bwd_lat_kernel(EdgeVecArgs a, const float
         if (lane == q) out = __fadd_rn(h.x, __fadd_rn(h.y, __fadd_rn(l.x, l.y)));
     }
     if (lane < 9) a.grad_lattice[9 * (int64_t)s + lane] = out;
+}
+
+__global__ void __launch_bounds__(256) bwd_lat_kernel(EdgeVecArgs a, const float2 *__restrict__ lpart) {
+    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s >= a.B) return;
+    lattice_reduce_warp(a, lpart, s);
 }
 
 // Large structures: a block of LAT_WARPS warps per structure, warp w taking every
@@ -369,6 +375,25 @@ __global__ void __launch_bounds__(256, 5) bwd_sym_kernel(EdgeVecArgs a, float2 *
         a.grad_frac[3 * (int64_t)j + lane] = ff_times_LT(tot, a.lattice + 9 * (int64_t)s, lane);
     }
     store_lattice_partial(lpart, j, M);
+    if (a.lat_cnt) {
+        // the last warp of the structure to store its partial reduces the structure's
+        // lattice gradient (the order of the sum does not depend on which warp it is)
+        const int s = sj >= 0 ? sj : structure_of(a.atom_ptr, a.B, j);
+        __threadfence();
+        int last = 0;
+        if (lane == 0) last = atomicAdd(&a.lat_cnt[s], 1) == a.atom_ptr[s + 1] - a.atom_ptr[s] - 1;
+        if (__shfl_sync(FULL, last, 0)) {
+            __threadfence();
+            lattice_reduce_warp(a, lpart, s);
+            if (lane == 0) a.lat_cnt[s] = 0;  // ready for the next backward
+            // empty structures after s (and before the first atom's) get a zero gradient
+            for (int q = s + 1; q < a.B && a.atom_ptr[q] == a.atom_ptr[q + 1]; ++q)
+                if (lane < 9) a.grad_lattice[9 * (int64_t)q + lane] = 0.f;
+            if (a.atom_ptr[s] == 0)
+                for (int q = s - 1; q >= 0; --q)
+                    if (lane < 9) a.grad_lattice[9 * (int64_t)q + lane] = 0.f;
+        }
+    }
 }
 
 cudaError_t launch_bwd_sym(const EdgeVecArgs &a, const Work &w, cudaStream_t s) {

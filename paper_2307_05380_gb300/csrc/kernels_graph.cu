@@ -38,7 +38,11 @@ __global__ void __launch_bounds__(GROUP == 32 ? 128 : GROUP) prep_kernel(PrepArg
         const int ntiles = (a.N + BUILD_TILE - 1) / BUILD_TILE + 1;
         for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x)
             tile_flags[t] = 0;
-        if (blockIdx.x == 0 && threadIdx.x == 0) queue[3] = 0;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            queue[3] = 0;
+            queue[4] = 0;  // queue[4..5]: 64-bit slot counter of the staged build
+            queue[5] = 0;
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && (a.init_status || (a.knn_k > 0 && a.edge_ptr))) {
         // nothing else writes the status word before the kernels that follow prep
@@ -208,6 +212,7 @@ __global__ void __launch_bounds__(GROUP == 32 ? 128 : GROUP) prep_kernel(PrepArg
     }
     recs[s] = R;  // a bad structure is reported by the kernel that scans its first atom
     if (a.pair_ok) a.pair_ok[s] = n <= PAIR_MAX ? 1 : 0;
+    if (a.lat_cnt) a.lat_cnt[s] = 0;
 }
 
 cudaError_t launch_prep(const PrepArgs &a, const Work &w, cudaStream_t s) {
@@ -705,6 +710,161 @@ __device__ long long tile_lookback(const unsigned long long *flags, int tile, mg
 constexpr int BUILD_WARPS = BUILD_TILE;
 constexpr int BUILD_CAP = 1024;  // edges of one source staged in shared memory
 
+// Per-source state of a cutoff-type build: the source's constants and its radius,
+// thresholds and FP64 squared radius (the structure's, or per source).
+struct SrcScan {
+    Source S;
+    float thr_lo, thr_hi, cut;
+    double rr;
+    int s;  // structure of the source
+};
+
+// Source constants; false when the structure is unusable (its first atom reports it).
+template <bool PERSRC>
+__device__ __forceinline__ bool source_setup(const BuildArgs &a, const Work &w, int i, SrcScan &c) {
+    c.s = w.atom_struct[i];
+    const StructRec &R = w.recs[c.s];
+    if (R.bad) {
+        if (lane_id() == 0 && i == R.atom_begin) set_error(a.g.status, R.bad, c.s + a.struct_offset);
+        return false;
+    }
+    load_source(c.S, w.recs, c.s, a.frac, w.pos, i);
+    c.thr_lo = R.thr_lo;
+    c.thr_hi = R.thr_hi;
+    c.cut = R.cut;
+    c.rr = R.rr;
+    if (PERSRC && a.cut_atom) {  // the source's own radius c_i (Def. 3)
+        c.cut = a.cut_atom[i];
+        c.rr = (double)c.cut * (double)c.cut;
+        band_thresholds(R, c.cut, c.rr, a.band_rel, c.thr_lo, c.thr_hi);
+    } else if (PERSRC && a.rr_atom) {  // a squared radius given in FP64 (keep-ties KNN)
+        c.rr = a.rr_atom[i];
+        c.cut = __double2float_ru(sqrt(c.rr)) * (1.0f + 1e-6f);
+        band_thresholds(R, c.cut, c.rr, a.band_rel, c.thr_lo, c.thr_hi);
+    }
+    return true;
+}
+
+// One scan of a source: FP32 test, FP64 re-test in the band, the edges' (j, t) keys
+// staged in `keys` (canonical order; sorted for cell-list sources).  Returns the edge
+// count; `spill` when the keys did not fit or an offset exceeds the packed key.
+template <bool PERSRC>
+__device__ __forceinline__ int scan_source(const BuildArgs &a, const Work &w, const SrcScan &c,
+                                           unsigned long long *keys, bool &spill) {
+    const Source &S = c.S;
+    const Cells cells{w.cell_start, w.cell_fx, w.cell_p};
+    const unsigned lt = (1u << lane_id()) - 1u;
+    const bool incl = PERSRC && a.inclusive != 0;
+    const float thr_lo = c.thr_lo, thr_hi = c.thr_hi;
+    const double rr = c.rr;
+    int m = 0;
+    bool range_bad = false;
+    unsigned long long nre = 0, ncand = 0;
+    for_each_candidate(S, a.frac, w.pos, cells, true, c.cut, [&](bool vc, float d2, bool self, int ow, int t2,
+                                                                  const RowRegs &rw) {
+        const bool cand = vc && !self;
+        bool in = cand && d2 < thr_lo;
+        const bool band = cand && !in && d2 <= thr_hi;
+        if (__any_sync(FULL, in || band)) {
+            const int jj = __shfl_sync(FULL, rw.j, ow);
+            const int t0 = __shfl_sync(FULL, rw.t0, ow);
+            const int t1 = __shfl_sync(FULL, rw.t1, ow);
+            if (band) {
+                const int64_t jr = (int64_t)S.begin + jj;
+                const double d = canon_d2(S.L, S.xi0, S.xi1, S.xi2, a.frac[3 * jr], a.frac[3 * jr + 1],
+                                          a.frac[3 * jr + 2], t0, t1, t2);
+                in = incl ? d <= rr : d < rr;
+            }
+            if (a.collect_stats) nre += __popc(__ballot_sync(FULL, band));
+            const unsigned bal = __ballot_sync(FULL, in);
+            if (in) {
+                if (abs(t0) > OFFSET_KEY_LIM || abs(t1) > OFFSET_KEY_LIM || abs(t2) > OFFSET_KEY_LIM)
+                    range_bad = true;
+                const int p = m + __popc(bal & lt);
+                if (p < BUILD_CAP) keys[p] = ((unsigned long long)(unsigned)jj << 32) | pack_t(t0, t1, t2);
+            }
+            m += __popc(bal);
+        }
+        if (a.collect_stats) ncand += __popc(__ballot_sync(FULL, cand));
+    });
+    spill = m > BUILD_CAP || __any_sync(FULL, range_bad);
+    if (!spill && S.nb[0] != 0 && m > 1) {
+        int P = 64;
+        while (P < m) P <<= 1;
+        warp_smem_sort_u64(keys, m, P);
+    }
+    if (a.collect_stats && lane_id() == 0 && ncand) {
+        Status *st = reinterpret_cast<Status *>(a.g.status);
+        atomicAdd(&st->rechecked, nre);
+        atomicAdd(&st->candidates, ncand);
+    }
+    if (!PERSRC && a.write_pairs && spill && lane_id() == 0) w.pair_ok[c.s] = 0;  // no pair table here
+    return m;
+}
+
+// The m edges of source i at rows base .. base + m - 1: from the staged keys (shared
+// or global memory), recording the pair table of symmetric graphs of small structures;
+// a spilled source is enumerated again in canonical all-pairs order.
+template <bool PERSRC>
+__device__ __forceinline__ void emit_source(const BuildArgs &a, const Work &w, const SrcScan &c, int i, int64_t base,
+                                            int m, const unsigned long long *keys, bool spill) {
+    const Source &S = c.S;
+    const mg_graph_t &g = a.g;
+    const int lane = lane_id();
+    if (!spill) {
+        const bool pairs = !PERSRC && a.write_pairs && S.n <= PAIR_MAX;
+        for (int q = lane; q < m; q += 32) {
+            const unsigned long long key = keys[q];
+            int t0, t1, t2;
+            unpack_t((uint32_t)(key & 0xffffffffull), t0, t1, t2);
+            const int jl = (int)(key >> 32);
+            const int64_t jr = (int64_t)S.begin + jl;
+            if (pairs) {
+                if (q == 0 || (int)(keys[q - 1] >> 32) != jl) w.pair_lo[(int64_t)i * PAIR_MAX + jl] = (uint16_t)q;
+                if (q == m - 1 || (int)(keys[q + 1] >> 32) != jl)
+                    w.pair_hi[(int64_t)i * PAIR_MAX + jl] = (uint16_t)(q + 1);
+            }
+            emit_edge(g, S, i, base + q, jr, a.frac[3 * jr], a.frac[3 * jr + 1], a.frac[3 * jr + 2], t0, t1, t2);
+        }
+        return;
+    }
+    const Cells cells{w.cell_start, w.cell_fx, w.cell_p};
+    const unsigned lt = (1u << lane) - 1u;
+    const float thr_lo = c.thr_lo, thr_hi = c.thr_hi;
+    const double rr = c.rr;
+    int64_t out = base;
+    const int64_t endp = base + m;
+    for_each_candidate(S, a.frac, w.pos, cells, false, c.cut,
+                       [&](bool vc, float d2, bool self, int ow, int t2, const RowRegs &rw) {
+        const bool cand = vc && !self;
+        bool in = cand && d2 < thr_lo;
+        const bool band = cand && !in && d2 <= thr_hi;
+        if (__any_sync(FULL, in || band)) {
+            const int jj = __shfl_sync(FULL, rw.j, ow);
+            const int t0 = __shfl_sync(FULL, rw.t0, ow);
+            const int t1 = __shfl_sync(FULL, rw.t1, ow);
+            const int64_t jr = (int64_t)S.begin + jj;
+            float xj0 = 0.f, xj1 = 0.f, xj2 = 0.f;
+            if (in || band) {
+                xj0 = a.frac[3 * jr];
+                xj1 = a.frac[3 * jr + 1];
+                xj2 = a.frac[3 * jr + 2];
+            }
+            if (band) {
+                const double d = canon_d2(S.L, S.xi0, S.xi1, S.xi2, xj0, xj1, xj2, t0, t1, t2);
+                in = (PERSRC && a.inclusive) ? d <= rr : d < rr;
+            }
+            const unsigned bal = __ballot_sync(FULL, in);
+            if (in) {
+                const int64_t e = out + __popc(bal & lt);
+                if (e < endp) emit_edge(g, S, i, e, jr, xj0, xj1, xj2, t0, t1, t2);
+            }
+            out += __popc(bal);
+        }
+    });
+    if (lane == 0 && out != endp) set_error(g.status, MG_ERR_INTERNAL, c.s);
+}
+
 // Cutoff graph in one pass.  Tiles of BUILD_WARPS consecutive source atoms are taken in
 // order (a ticket per block, so every tile a block waits on is already running); each
 // warp scans its source once and stages the edges' (j, t) keys in shared memory
@@ -725,9 +885,7 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_build_kernel(Build
     __shared__ long long s_prefix;
     const int wid = threadIdx.x >> 5, lane = lane_id();
     unsigned long long *keys = keys_all[wid];
-    const unsigned lt = (1u << lane) - 1u;
     const mg_graph_t g = a.g;
-    const Cells cells{w.cell_start, w.cell_fx, w.cell_p};
     unsigned long long *flags = w.tile_flags;
     const int ntiles = gridDim.x;
 
@@ -736,78 +894,15 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_build_kernel(Build
     const int tile = s_tile;
     const int i = a.atom_lo + tile * BUILD_WARPS + wid;
     const bool have = i < a.atom_hi;
-    int s = 0;
     int m = 0;
     bool spill = false;  // edges not staged: emit through a second all-pairs scan
-    Source S;
-    float thr_lo = 0.f, thr_hi = 0.f, cut = 0.f;
-    double rr = 0.0;
-    unsigned long long nre = 0, ncand = 0;
+    SrcScan c;
+    c.s = 0;
+    bool usable = false;
     if (have) {
-        s = w.atom_struct[i];
-        const StructRec &R = w.recs[s];
-        if (R.bad) {
-            if (lane == 0 && i == R.atom_begin) set_error(g.status, R.bad, s + a.struct_offset);
-        } else {
-            load_source(S, w.recs, s, a.frac, w.pos, i);
-            thr_lo = R.thr_lo;
-            thr_hi = R.thr_hi;
-            cut = R.cut;
-            rr = R.rr;
-            if (PERSRC && a.cut_atom) {  // the source's own radius c_i (Def. 3)
-                cut = a.cut_atom[i];
-                rr = (double)cut * (double)cut;
-                band_thresholds(R, cut, rr, a.band_rel, thr_lo, thr_hi);
-            } else if (PERSRC && a.rr_atom) {  // a squared radius given in FP64 (keep-ties KNN)
-                rr = a.rr_atom[i];
-                cut = __double2float_ru(sqrt(rr)) * (1.0f + 1e-6f);
-                band_thresholds(R, cut, rr, a.band_rel, thr_lo, thr_hi);
-            }
-            const bool cellp = S.nb[0] != 0;
-            const bool incl = PERSRC && a.inclusive != 0;
-            bool range_bad = false;
-            for_each_candidate(S, a.frac, w.pos, cells, true, cut, [&](bool vc, float d2, bool self, int ow,
-                                                                        int t2, const RowRegs &rw) {
-                const bool cand = vc && !self;
-                bool in = cand && d2 < thr_lo;
-                const bool band = cand && !in && d2 <= thr_hi;
-                if (__any_sync(FULL, in || band)) {
-                    const int jj = __shfl_sync(FULL, rw.j, ow);
-                    const int t0 = __shfl_sync(FULL, rw.t0, ow);
-                    const int t1 = __shfl_sync(FULL, rw.t1, ow);
-                    if (band) {
-                        const int64_t jr = (int64_t)S.begin + jj;
-                        const double d = canon_d2(S.L, S.xi0, S.xi1, S.xi2, a.frac[3 * jr], a.frac[3 * jr + 1],
-                                                  a.frac[3 * jr + 2], t0, t1, t2);
-                        in = incl ? d <= rr : d < rr;
-                    }
-                    if (a.collect_stats) nre += __popc(__ballot_sync(FULL, band));
-                    const unsigned bal = __ballot_sync(FULL, in);
-                    if (in) {
-                        if (abs(t0) > OFFSET_KEY_LIM || abs(t1) > OFFSET_KEY_LIM || abs(t2) > OFFSET_KEY_LIM)
-                            range_bad = true;
-                        const int p = m + __popc(bal & lt);
-                        if (p < BUILD_CAP)
-                            keys[p] = ((unsigned long long)(unsigned)jj << 32) | pack_t(t0, t1, t2);
-                    }
-                    m += __popc(bal);
-                }
-                if (a.collect_stats) ncand += __popc(__ballot_sync(FULL, cand));
-            });
-            spill = m > BUILD_CAP || __any_sync(FULL, range_bad);
-            if (!spill && cellp && m > 1) {
-                int P = 64;
-                while (P < m) P <<= 1;
-                warp_smem_sort_u64(keys, m, P);
-            }
-            if (a.collect_stats && lane == 0 && ncand) {
-                Status *st = reinterpret_cast<Status *>(g.status);
-                atomicAdd(&st->rechecked, nre);
-                atomicAdd(&st->candidates, ncand);
-            }
-        }
+        usable = source_setup<PERSRC>(a, w, i, c);
+        if (usable) m = scan_source<PERSRC>(a, w, c, keys, spill);
     }
-    if (!PERSRC && a.write_pairs && spill && lane == 0) w.pair_ok[s] = 0;  // no pair table for this structure
     if (lane == 0) s_cnt[wid] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -841,58 +936,123 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_build_kernel(Build
     for (int q = 0; q < wid; ++q) base += s_cnt[q];
     if (lane == 0) {
         a.src_ptr[i] = base;
+        const int s = w.atom_struct[i];
         for (int q = s; q >= 0 && a.atom_ptr[q] == i; --q) g.edge_ptr[q] = base;  // structures starting at i
     }
     if (m == 0 || base + m > g.capacity) return;  // nothing to write, or the capacity error
-    if (!spill) {
-        // symmetric graphs of small structures: the run of every target in the pair table
-        const bool pairs = !PERSRC && a.write_pairs && S.n <= PAIR_MAX;
-        for (int q = lane; q < m; q += 32) {
-            const unsigned long long key = keys[q];
-            int t0, t1, t2;
-            unpack_t((uint32_t)(key & 0xffffffffull), t0, t1, t2);
-            const int jl = (int)(key >> 32);
-            const int64_t jr = (int64_t)S.begin + jl;
-            if (pairs) {
-                if (q == 0 || (int)(keys[q - 1] >> 32) != jl) w.pair_lo[(int64_t)i * PAIR_MAX + jl] = (uint16_t)q;
-                if (q == m - 1 || (int)(keys[q + 1] >> 32) != jl)
-                    w.pair_hi[(int64_t)i * PAIR_MAX + jl] = (uint16_t)(q + 1);
-            }
-            emit_edge(g, S, i, base + q, jr, a.frac[3 * jr], a.frac[3 * jr + 1], a.frac[3 * jr + 2], t0, t1, t2);
-        }
-    } else {
-        int64_t out = base;
-        const int64_t endp = base + m;
-        for_each_candidate(S, a.frac, w.pos, cells, false, cut,
-                           [&](bool vc, float d2, bool self, int ow, int t2, const RowRegs &rw) {
-            const bool cand = vc && !self;
-            bool in = cand && d2 < thr_lo;
-            const bool band = cand && !in && d2 <= thr_hi;
-            if (__any_sync(FULL, in || band)) {
-                const int jj = __shfl_sync(FULL, rw.j, ow);
-                const int t0 = __shfl_sync(FULL, rw.t0, ow);
-                const int t1 = __shfl_sync(FULL, rw.t1, ow);
-                const int64_t jr = (int64_t)S.begin + jj;
-                float xj0 = 0.f, xj1 = 0.f, xj2 = 0.f;
-                if (in || band) {
-                    xj0 = a.frac[3 * jr];
-                    xj1 = a.frac[3 * jr + 1];
-                    xj2 = a.frac[3 * jr + 2];
-                }
-                if (band) {
-                    const double d = canon_d2(S.L, S.xi0, S.xi1, S.xi2, xj0, xj1, xj2, t0, t1, t2);
-                    in = (PERSRC && a.inclusive) ? d <= rr : d < rr;
-                }
-                const unsigned bal = __ballot_sync(FULL, in);
-                if (in) {
-                    const int64_t e = out + __popc(bal & lt);
-                    if (e < endp) emit_edge(g, S, i, e, jr, xj0, xj1, xj2, t0, t1, t2);
-                }
-                out += __popc(bal);
-            }
-        });
-        if (lane == 0 && out != endp) set_error(g.status, MG_ERR_INTERNAL, s);
+    emit_source<PERSRC>(a, w, c, i, base, m, keys, spill);
+}
+
+// Decoupled build, part 1 (no dependence between sources): each warp scans a source and
+// copies its staged keys to a global staging area at a slot taken with one atomic add;
+// the count goes to cnt[i] and the slot to stage_off[i] (-1: spilled source).
+template <bool PERSRC>
+__global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_stage_kernel(BuildArgs a, Work w) {
+    __shared__ unsigned long long keys_all[BUILD_WARPS][BUILD_CAP];
+    const int wid = threadIdx.x >> 5, lane = lane_id();
+    unsigned long long *keys = keys_all[wid];
+    const int i = a.atom_lo + blockIdx.x * BUILD_WARPS + wid;
+    if (i >= a.atom_hi) return;
+    SrcScan c;
+    int m = 0;
+    bool spill = false;
+    if (source_setup<PERSRC>(a, w, i, c)) m = scan_source<PERSRC>(a, w, c, keys, spill);
+    long long off = -1;
+    if (!spill && m > 0) {
+        if (lane == 0) off = (long long)atomicAdd(w.stage_ctr, (unsigned long long)m);
+        off = __shfl_sync(FULL, off, 0);
+        if (off + m <= w.max_edges)
+            for (int q = lane; q < m; q += 32) w.stage[off + q] = keys[q];
+        else
+            spill = true;  // staging area full (more edges than the workspace covers)
     }
+    if (lane == 0) {
+        w.cnt[i] = m;
+        w.stage_off[i] = spill ? -1 : off;
+    }
+}
+
+// Staged build, part 2 (after the scan of the counts): a thread per edge row.  Each
+// warp takes a contiguous range of rows, so the source of a row comes from src_ptr by one
+// binary search per warp and then forward steps; its key is the staged one.  The pair
+// table of symmetric graphs records each run's ends from the neighbouring keys.
+// Spilled sources are left to cutoff_spill_kernel.
+template <bool PERSRC>
+__global__ void __launch_bounds__(256) cutoff_emit_kernel(BuildArgs a, Work w) {
+    const mg_graph_t &g = a.g;
+    const int64_t E = a.src_ptr[a.atom_hi];
+    if (E > g.capacity) return;  // reported by the finalize kernel
+    const int lane = lane_id();
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t lo_e = a.src_ptr[a.atom_lo];
+    const int64_t span = E - lo_e;
+    const int64_t chunk = ((span + warps - 1) / warps + 31) & ~(int64_t)31;
+    const int64_t e0 = lo_e + wid * chunk, e1 = min(E, e0 + chunk);
+    if (e0 >= e1) return;
+    int i = a.atom_lo;  // last source whose first row is <= e0
+    {
+        int lo = a.atom_lo, hi = a.atom_hi;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (a.src_ptr[mid] <= e0) lo = mid;
+            else hi = mid;
+        }
+        i = lo;
+    }
+    for (int64_t e = e0 + lane; e < e1; e += 32) {
+        while (i + 1 < a.atom_hi && a.src_ptr[i + 1] <= e) ++i;
+        const long long off = w.stage_off[i];
+        if (off < 0) continue;  // spilled source
+        const int64_t base = a.src_ptr[i];
+        const int m = (int)(a.src_ptr[i + 1] - base);
+        const int q = (int)(e - base);
+        const StructRec &R = w.recs[w.atom_struct[i]];
+        const unsigned long long key = w.stage[off + q];
+        int t0, t1, t2;
+        unpack_t((uint32_t)(key & 0xffffffffull), t0, t1, t2);
+        const int jl = (int)(key >> 32);
+        const int64_t jr = (int64_t)R.atom_begin + jl;
+        if (!PERSRC && a.write_pairs && R.n_atoms <= PAIR_MAX) {
+            if (q == 0 || (int)(w.stage[off + q - 1] >> 32) != jl) w.pair_lo[(int64_t)i * PAIR_MAX + jl] = (uint16_t)q;
+            if (q == m - 1 || (int)(w.stage[off + q + 1] >> 32) != jl)
+                w.pair_hi[(int64_t)i * PAIR_MAX + jl] = (uint16_t)(q + 1);
+        }
+        g.src[e] = i;
+        g.dst[e] = (int32_t)jr;
+        g.offset[3 * e + 0] = t0;
+        g.offset[3 * e + 1] = t1;
+        g.offset[3 * e + 2] = t2;
+        if (g.vec || g.len) {
+            const float L[9] = {R.L[0], R.L[1], R.L[2], R.L[3], R.L[4], R.L[5], R.L[6], R.L[7], R.L[8]};
+            const float3 v = edge_vec_ff(L, a.frac[3 * (int64_t)i], a.frac[3 * (int64_t)i + 1],
+                                         a.frac[3 * (int64_t)i + 2], a.frac[3 * jr], a.frac[3 * jr + 1],
+                                         a.frac[3 * jr + 2], t0, t1, t2);
+            if (g.vec) {
+                g.vec[3 * e + 0] = v.x;
+                g.vec[3 * e + 1] = v.y;
+                g.vec[3 * e + 2] = v.z;
+            }
+            if (g.len) g.len[e] = vec_len(v);
+        }
+    }
+}
+
+// Staged build, spilled sources (more edges than the shared staging holds, an offset
+// outside the packed key, or a full staging area): a warp each enumerates its source
+// again in canonical all-pairs order, writing at src_ptr[i].
+template <bool PERSRC>
+__global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_spill_kernel(BuildArgs a, Work w) {
+    const int i = a.atom_lo + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (i >= a.atom_hi) return;
+    if (w.stage_off[i] >= 0) return;
+    if (a.src_ptr[a.atom_hi] > a.g.capacity) return;  // reported by the finalize kernel
+    const int64_t base = a.src_ptr[i];
+    const int m = (int)(a.src_ptr[i + 1] - base);
+    if (m == 0) return;
+    SrcScan c;
+    if (!source_setup<PERSRC>(a, w, i, c)) return;
+    emit_source<PERSRC>(a, w, c, i, base, m, nullptr, true);
 }
 
 cudaError_t launch_cutoff_build(const BuildArgs &a, const Work &w, cudaStream_t s) {
@@ -903,6 +1063,43 @@ cudaError_t launch_cutoff_build(const BuildArgs &a, const Work &w, cudaStream_t 
         cutoff_build_kernel<true><<<tiles, BUILD_WARPS * 32, 0, s>>>(a, w);
     else
         cutoff_build_kernel<false><<<tiles, BUILD_WARPS * 32, 0, s>>>(a, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cutoff_stage(const BuildArgs &a, const Work &w, cudaStream_t s) {
+    const int atoms = a.atom_hi - a.atom_lo;
+    if (atoms <= 0) return cudaSuccess;
+    const int blocks = (atoms + BUILD_WARPS - 1) / BUILD_WARPS;
+    if (a.cut_atom || a.rr_atom)
+        cutoff_stage_kernel<true><<<blocks, BUILD_WARPS * 32, 0, s>>>(a, w);
+    else
+        cutoff_stage_kernel<false><<<blocks, BUILD_WARPS * 32, 0, s>>>(a, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cutoff_counts(const BuildArgs &a, const Work &w, cudaStream_t s) {
+    const int atoms = a.atom_hi - a.atom_lo;
+    ScanArgs sa{atoms, w.cnt + a.atom_lo, a.src_ptr + a.atom_lo};
+    cudaError_t e = launch_scan(sa, w, s);
+    if (e) return e;
+    return launch_cutoff_finalize(a, w, s);
+}
+
+cudaError_t launch_cutoff_emit(const BuildArgs &a, const Work &w, cudaStream_t s) {
+    const int atoms = a.atom_hi - a.atom_lo;
+    if (atoms <= 0) return cudaSuccess;
+    // rows live on the device: a thread per row of a graph up to the capacity, capped at
+    // 16 blocks per SM (longer ranges per warp beyond)
+    const int64_t want = (a.g.capacity + 255) / 256;
+    const int blocks = (int)(want < 16 * num_sms() ? (want > 0 ? want : 1) : 16 * num_sms());
+    const int sblocks = (atoms + BUILD_WARPS - 1) / BUILD_WARPS;
+    if (a.cut_atom || a.rr_atom) {
+        cutoff_emit_kernel<true><<<blocks, 256, 0, s>>>(a, w);
+        cutoff_spill_kernel<true><<<sblocks, BUILD_WARPS * 32, 0, s>>>(a, w);
+    } else {
+        cutoff_emit_kernel<false><<<blocks, 256, 0, s>>>(a, w);
+        cutoff_spill_kernel<false><<<sblocks, BUILD_WARPS * 32, 0, s>>>(a, w);
+    }
     return cudaGetLastError();
 }
 

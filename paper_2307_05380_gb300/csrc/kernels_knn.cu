@@ -169,9 +169,13 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 6) knn_kernel(BuildArgs a, Wor
     using PKey = typename std::conditional<ONEPASS, CKey, FKey>::type;
     __shared__ unsigned long long sel_all[KNN_WARPS][S * 32 > 64 ? S * 32 : 64];
     __shared__ unsigned long long band_all[KNN_WARPS][BAND_CAP];
+    __shared__ float bufv_all[KNN_WARPS][64];               // pass-1 candidates waiting for a merge
+    __shared__ unsigned long long bufjt_all[KNN_WARPS][64];
     const int wid = threadIdx.x >> 5, lane = lane_id();
     unsigned long long *sel = sel_all[wid];
     unsigned long long *bl = band_all[wid];
+    float *bufv = bufv_all[wid];
+    unsigned long long *bufjt = bufjt_all[wid];
     const int k = a.knn_k;
     const unsigned lt = (1u << lane) - 1u;
     const mg_graph_t g = a.g;
@@ -196,34 +200,57 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 6) knn_kernel(BuildArgs a, Wor
         TopK<PKey, S> tk;
         for (int iter = 0; iter < 64 && !ok; ++iter) {
             tk.init();
-            float thr = F_INF;
-            int found = 0;
+            float thr = F_INF;  // images at least this far cannot enter the kept set
+            int found = 0, nbuf = 0;
             const float rho2 = rho * rho;
+            // candidates below thr wait in shared memory; 32 at a time go through one
+            // register merge (thr is refreshed then: a stale thr only admits more)
+            auto merge = [&](int from, int cnt) {
+                const int q = from + lane;
+                const bool have = lane < cnt;
+                const float v = have ? bufv[q] : F_INF;
+                if constexpr (ONEPASS) {
+                    tk.insert(CKey{v, have ? bufjt[q] : ~0ull});
+                    thr = tk.kth(32 * S).v;  // the kept images are the 32 S nearest seen
+                } else {
+                    tk.insert(FKey{v});
+                    thr = tk.kth(k).v;
+                }
+            };
             for_each_candidate(Src, a.frac, w.pos, cells, true, rho, [&](bool vc, float d2, bool self, int ow,
                                                                           int t2, const RowRegs &rw) {
                 const bool c = vc && !self && d2 < rho2;
                 found += __popc(__ballot_sync(FULL, c));
-                const float v = c ? d2 : F_INF;
-                if (__any_sync(FULL, v < thr)) {
-                    const bool ins = v < thr;
+                const bool ins = c && d2 < thr;
+                const unsigned bal = __ballot_sync(FULL, ins);
+                if (bal) {
+                    const int p = nbuf + __popc(bal & lt);
                     if constexpr (ONEPASS) {
                         const int jj = __shfl_sync(FULL, rw.j, ow);
                         const int t0 = __shfl_sync(FULL, rw.t0, ow);
                         const int t1 = __shfl_sync(FULL, rw.t1, ow);
-                        unsigned long long jt = ~0ull;
                         if (ins)
-                            jt = (abs(t0) > OFFSET_KEY_LIM || abs(t1) > OFFSET_KEY_LIM || abs(t2) > OFFSET_KEY_LIM)
-                                     ? JT_OUT_OF_RANGE
-                                     : (((unsigned long long)(unsigned)jj << 32) | pack_t(t0, t1, t2));
-                        tk.insert(CKey{ins ? v : F_INF, jt});
-                        thr = tk.kth(32 * S).v;  // the kept images are the 32 S nearest seen
-                    } else {
-                        tk.insert(FKey{ins ? v : F_INF});
-                        thr = tk.kth(k).v;
+                            bufjt[p] = (abs(t0) > OFFSET_KEY_LIM || abs(t1) > OFFSET_KEY_LIM || abs(t2) > OFFSET_KEY_LIM)
+                                           ? JT_OUT_OF_RANGE
+                                           : (((unsigned long long)(unsigned)jj << 32) | pack_t(t0, t1, t2));
+                    }
+                    if (ins) bufv[p] = d2;
+                    nbuf += __popc(bal);
+                    if (nbuf >= 32) {  // merge the last 32, keep the rest waiting
+                        __syncwarp();
+                        nbuf -= 32;
+                        merge(nbuf, 32);
+                        __syncwarp();
                     }
                 }
                 if (a.collect_stats) ncand += __popc(__ballot_sync(FULL, vc && !self));
             });
+            if (nbuf > 0) {
+                __syncwarp();
+                merge(0, nbuf);
+                nbuf = 0;
+                __syncwarp();
+            }
             thr = tk.kth(k).v;
             delta = fp32_d2_error(R, rho, rho2) + 2.0f * a.band_rel * rho2;
             if (found >= k && thr + 3.0f * delta < rho2) {

@@ -22,7 +22,10 @@ struct Work {
     int64_t *src_ptr;         // [N+1] used when the graph has none
     float2 *gpart;            // [N][3] source-side gradient partials (float-float)
     float2 *lpart;            // [N][9] per-atom lattice-gradient partials (float-float)
-    int32_t *sort_tmp;        // [max_edges] scratch for long destination segments
+    int32_t *sort_tmp;        // [max_edges] scratch for long destination segments (aliases stage)
+    unsigned long long *stage;      // [max_edges] staged (j, t) keys of the decoupled build
+    long long *stage_off;           // [N] slot of each source's keys in `stage` (-1: spilled)
+    unsigned long long *stage_ctr;  // next free slot (queue[4..5])
     unsigned int *queue;      // [4] work-queue counters
     int32_t *bin_cnt;         // [N+B] atoms per cell-list bin
     int32_t *bin_cursor;      // [N+B] scatter cursors of the bins
@@ -35,6 +38,7 @@ struct Work {
     uint16_t *pair_lo;        // [N][PAIR_MAX] run of edges i -> j in i's segment: first and
     uint16_t *pair_hi;        //   one-past-last position (structures of <= PAIR_MAX atoms)
     int32_t *pair_ok;         // [B] 1: the pair table of the structure is complete
+    int32_t *lat_cnt;         // [B] atoms of the structure whose lattice partial is stored
     int64_t max_edges;
 };
 
@@ -59,6 +63,7 @@ struct PrepArgs {
     int max_atoms;             // host-known bound on atoms per structure (0: unknown)
     const float *cutoff_atom = nullptr;  // per-atom radii [N]: the structure's reach is their maximum
     int32_t *pair_ok = nullptr;          // [B] set to (n <= PAIR_MAX) when a pair table is written
+    int32_t *lat_cnt = nullptr;          // [B] zeroed with the pair table (backward's counters)
 };
 
 cudaError_t launch_prep(const PrepArgs &a, const Work &w, cudaStream_t s);
@@ -101,6 +106,12 @@ struct BuildArgs {
 
 // One-pass cutoff build (batched): scan once, stage keys, look-back offsets, write.
 cudaError_t launch_cutoff_build(const BuildArgs &a, const Work &w, cudaStream_t s);
+// Staged cutoff build: scan and stage keys globally (stage), scan the counts and write
+// the pointers and status (counts: 4 launches), write the edges (emit).  Sources whose
+// keys do not fit the staging area (w.max_edges) are enumerated again by emit.
+cudaError_t launch_cutoff_stage(const BuildArgs &a, const Work &w, cudaStream_t s);
+cudaError_t launch_cutoff_counts(const BuildArgs &a, const Work &w, cudaStream_t s);
+cudaError_t launch_cutoff_emit(const BuildArgs &a, const Work &w, cudaStream_t s);
 // Two-pass form (per-structure builds): count, separate scan, write.
 cudaError_t launch_cutoff_count(const BuildArgs &a, const Work &w, cudaStream_t s);
 // Edge pointers, status and capacity check after the scan of counts.
@@ -125,6 +136,8 @@ struct EdgeVecArgs {
     // symmetric backward: the pair table of the graph's build (NULL: binary searches)
     const uint16_t *pair_lo, *pair_hi;
     const int32_t *pair_ok, *atom_struct;
+    int32_t *lat_cnt;          // non-NULL: the last warp of a structure reduces its lattice
+                               // gradient (counters start at zero and are left at zero)
 };
 cudaError_t launch_edgevec_fwd(const EdgeVecArgs &a, cudaStream_t s);
 cudaError_t launch_bwd_sym(const EdgeVecArgs &a, const Work &w, cudaStream_t s);  // symmetric graphs

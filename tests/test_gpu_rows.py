@@ -327,3 +327,64 @@ def test_knn_band_past_the_kept_images_takes_the_second_scan():
     assert_same_edges(got, oracle.knn(b.lattice, b.frac, b.atom_ptr, 20), "fcc k=20")
     gt, _ = ties_parity(b, 20)
     assert gt.num_edges == 42
+
+
+# ------------------------------------------------------------------ the two cutoff builds
+
+@pytest.mark.parametrize("schedule", [3, 4])
+def test_one_pass_and_staged_builds_match_the_oracle(schedule):
+    """schedule 3 forces the one-pass build (look-back), 4 the staged build (scan and
+    stage, scan the counts, write); both are exact on every kind of source: all-pairs,
+    cell-list, per-atom radii and keep-ties KNN."""
+    opts = mg.make_opts(schedule=schedule)
+    b = synth.make_batch(2, B=96)
+    cutoff_got = graph_arrays(mg.cutoff_graph(to_device(b), 6.0, opts=opts))
+    assert_same_edges(cutoff_got, oracle.cutoff(b.lattice, b.frac, b.atom_ptr, 6.0), "cutoff")
+    assert_perm_dst(cutoff_got, b.total_atoms)
+    b5 = synth.make_batch(5).subset([0])
+    g5 = mg.cutoff_graph(to_device(b5), 8.0, with_perm=False, opts=opts)
+    got5 = graph_arrays(g5)
+    srcs = np.arange(0, b5.total_atoms, 97, dtype=np.int32)
+    want5 = oracle.cutoff(b5.lattice, b5.frac, b5.atom_ptr, 8.0, sources=srcs)
+    sel = np.concatenate([np.arange(got5["src_ptr"][s], got5["src_ptr"][s + 1]) for s in srcs])
+    assert_same_edges({k: got5[k][sel] for k in ("src", "dst", "offset")}, want5, "cell-list")
+    radii = radii_for(b, 17, 3.0, 6.0)
+    ga = mg.cutoff_graph_atoms(to_device(b), torch.from_numpy(radii).cuda(), opts=opts)
+    assert_same_edges(graph_arrays(ga), oracle.cutoff_atoms(b.lattice, b.frac, b.atom_ptr,
+                                                            radii.astype(np.float64)), "per-atom")
+    gk = mg.knn_graph(to_device(b), 16, keep_ties=True, opts=opts)
+    assert_same_edges(graph_arrays(gk), oracle.knn(b.lattice, b.frac, b.atom_ptr, 16, keep_ties=True), "ties")
+    # the symmetric backward reads the pair table either build records
+    batch = to_device(b)
+    g = mg.cutoff_graph(batch, 6.0, with_perm=False, opts=opts)
+    grad_check(b, g, synth.normal(21, schedule, g.num_edges))
+
+
+def test_fused_lattice_reduction_with_empty_structures():
+    """The symmetric backward reduces each structure's lattice gradient in the last warp
+    to finish it; empty structures (first, middle, last) still get a zero gradient, and
+    the result equals the separate reduction kernel bit for bit."""
+    parts = [synth.make_batch(2, B=6)]
+    b0 = synth.concat(parts)
+    counts = [0] + np.diff(b0.atom_ptr).tolist()[:3] + [0, 0] + np.diff(b0.atom_ptr).tolist()[3:] + [0]
+    lat = np.concatenate([np.eye(3, dtype=np.float32)[None] * 4, b0.lattice[:3],
+                          np.eye(3, dtype=np.float32)[None].repeat(2, 0) * 5, b0.lattice[3:],
+                          np.eye(3, dtype=np.float32)[None] * 6])
+    ptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    b = synth.Batch(lat, b0.frac, ptr)
+    batch = to_device(b)
+    g = mg.cutoff_graph(batch, 5.0, with_perm=False)
+    gl = torch.from_numpy(synth.normal(31, 0, g.num_edges)).cuda()
+    v, ln = mg.edge_vectors_fwd(g)
+    gf_fused = torch.full((b.total_atoms, 3), float("nan"), device="cuda")
+    gL_fused = torch.full((b.num_structures, 3, 3), float("nan"), device="cuda")
+    mg.edge_vectors_bwd(g, batch, None, gl, v, ln, gf_fused, gL_fused)
+    assert mg.last_launch_count() == 1  # the reduction joined the backward kernel
+    for s in np.flatnonzero(np.diff(ptr) == 0):
+        assert torch.all(gL_fused[s] == 0)
+    mg.rebuild(g, per_structure=True)  # no pair table, no counters: the separate kernel
+    v2, ln2 = mg.edge_vectors_fwd(g)
+    gf2, gL2 = mg.edge_vectors_bwd(g, batch, None, gl, v2, ln2)
+    assert mg.last_launch_count() == 2
+    assert torch.equal(gf_fused, gf2) and torch.equal(gL_fused, gL2)
+    grad_check(b, g, synth.normal(31, 1, g.num_edges))
