@@ -241,8 +241,11 @@ mg_status_t mg_symmetrize(mg_context_t ctx, const mg_batch_t *batch, const mg_gr
                           mg_graph_t *out, void *workspace, size_t workspace_bytes, void *stream);
 
 /* Time the available schedules for this batch shape on the caller's buffers and keep
- * the fastest per size class in the context (synchronises; results are identical for
- * every schedule).  kind/cutoff/k as in mg_build_per_structure. */
+ * the fastest per size class (largest structure: <= 32, <= 128, <= 512 atoms, larger)
+ * in the context: KNN flat grid or persistent work queue; cutoff graphs the one-pass or
+ * the staged build (the latter only when the workspace covers graph->capacity).
+ * Synchronises; results are identical for every schedule.  kind/cutoff/k as in
+ * mg_build_per_structure. */
 mg_status_t mg_autotune(mg_context_t ctx, const mg_batch_t *batch, int32_t kind, float cutoff,
                         int32_t k, mg_graph_t *graph, void *workspace, size_t workspace_bytes,
                         void *stream);

@@ -305,9 +305,12 @@ mg_status_t enqueue_build(mg_context *ctx, int kind, const mg_batch_t *b, float 
     // The decoupled build (scan and stage, scan of counts, write) when the workspace can
     // stage every edge and the batch is large: measured 10-29% faster than the one-pass
     // build from 37k atoms up, 17% slower at 3.6k atoms (its extra launches).  schedule 3
-    // / 4 force the one-pass / decoupled form; the one-pass form's testing hook forces it.
+    // / 4 force the one-pass / decoupled form, as does a schedule mg_autotune measured for
+    // this size class; the one-pass form's testing hook forces it.
+    int csched = o.schedule;
+    if (csched == 0) csched = ctx->tuned[0][size_class(b)];
     const bool can_stage = o.fault_tile < 0 && me >= g->capacity;
-    const bool staged = can_stage && (o.schedule == 4 || (o.schedule != 3 && N >= STAGED_MIN_ATOMS));
+    const bool staged = can_stage && (csched == 4 || (csched != 3 && N >= STAGED_MIN_ATOMS));
     auto cutoff_build = [&](const BuildArgs &args) -> bool {  // false on a launch error
         if (!staged) {  // one pass: scan, look-back offsets, write (also src_ptr, edge_ptr, count)
             if (launch_cutoff_build(args, w, st)) return false;
@@ -909,9 +912,15 @@ mg_status_t mg_autotune(mg_context_t ctx, const mg_batch_t *b, int32_t kind, flo
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) return MG_ERR_CUDA;
+    // KNN: flat grid (1) or persistent queue (2); cutoff graphs: the one-pass build (3)
+    // or the staged build (4), the latter only when the workspace can stage the capacity
+    const int first = kind == MG_KIND_KNN ? 1 : 3;
+    int last = kind == MG_KIND_KNN ? 2 : 4;
+    if (kind == MG_KIND_CUTOFF && (!g || ws_max_edges(b->num_structures, b->total_atoms, ws_bytes) < g->capacity))
+        last = 3;
     float best = 1e30f;
-    int best_s = 1;
-    for (int sched = 1; sched <= 2; ++sched) {
+    int best_s = first;
+    for (int sched = first; sched <= last; ++sched) {
         mg_opts_t o = defaults(nullptr);
         o.schedule = sched;
         float tot = 0.f;

@@ -287,8 +287,10 @@ __device__ __forceinline__ int64_t key_bound(const int32_t *__restrict__ keys, i
 // segment at s_ij + (rhi - 1 - p) (the run of i's edges to j holds the reversed run in
 // the opposite offset order; s_ij its start, [rlo, rhi) the run of p in j's segment).
 // PAIRS 0: the runs come from binary searches done once per run by its first lane;
-// PAIRS 1: from the build's pair table where the structure has one, else searches;
-// PAIRS 2: every structure has a table (two loads per edge).
+// PAIRS 1: from the build's pair table where the structure has a complete one (none for
+// a structure with a source that did not fit the build's staging), else searches.
+// A reverse index outside i's segment (an inconsistent graph) is reported as
+// MG_ERR_INTERNAL in the graph's status word and not followed.
 // The reverse edge's vector and length are those of p negated (the forward evaluates
 // both edges with sign-symmetric float-float arithmetic), so only its incoming
 // gradients are gathered.
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(256, 5) bwd_sym_kernel(EdgeVecArgs a, float2 *
     int sj = -1, begin = 0;  // structure of j when its pair table is usable
     if (PAIRS) {
         const int s = a.atom_struct[j];
-        if (PAIRS == 2 || a.pair_ok[s]) {
+        if (a.pair_ok[s]) {
             sj = s;
             begin = a.atom_ptr[s];
         }
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(256, 5) bwd_sym_kernel(EdgeVecArgs a, float2 *
         const bool valid = p < hi;
         const int i = valid ? a.g.dst[p] : -1;
         int64_t rev = 0;
-        if (PAIRS == 2 || (PAIRS == 1 && sj >= 0)) {
+        if (PAIRS && sj >= 0) {
             if (valid) {
                 const int il = i - begin, jl = j - begin;
                 const int64_t rhi = lo + a.pair_hi[(int64_t)j * PAIR_MAX + il];
@@ -342,6 +344,10 @@ __global__ void __launch_bounds__(256, 5) bwd_sym_kernel(EdgeVecArgs a, float2 *
             rev = sij + (rhi - 1 - p);
         }
         if (!valid) continue;
+        if (rev < a.g.src_ptr[i] || rev >= a.g.src_ptr[i + 1]) {  // never for a graph built here
+            set_error(a.g.status, MG_ERR_INTERNAL, -1);
+            rev = p;
+        }
         float3 g = make_float3(0.f, 0.f, 0.f), gr = g;
         if (a.grad_vec) {
             g = make_float3(a.grad_vec[3 * p], a.grad_vec[3 * p + 1], a.grad_vec[3 * p + 2]);
@@ -401,8 +407,6 @@ cudaError_t launch_bwd_sym(const EdgeVecArgs &a, const Work &w, cudaStream_t s) 
     const int blocks = (a.N + 7) / 8;
     if (!a.pair_lo)
         bwd_sym_kernel<0><<<blocks, 256, 0, s>>>(a, w.lpart);
-    else if (a.max_atoms > 0 && a.max_atoms <= PAIR_MAX)
-        bwd_sym_kernel<2><<<blocks, 256, 0, s>>>(a, w.lpart);
     else
         bwd_sym_kernel<1><<<blocks, 256, 0, s>>>(a, w.lpart);
     return cudaGetLastError();

@@ -961,10 +961,12 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_stage_kernel(Build
     if (!spill && m > 0) {
         if (lane == 0) off = (long long)atomicAdd(w.stage_ctr, (unsigned long long)m);
         off = __shfl_sync(FULL, off, 0);
-        if (off + m <= w.max_edges)
+        if (off + m <= w.max_edges) {
             for (int q = lane; q < m; q += 32) w.stage[off + q] = keys[q];
-        else
+        } else {
             spill = true;  // staging area full (more edges than the workspace covers)
+            if (!PERSRC && a.write_pairs && lane == 0) w.pair_ok[c.s] = 0;
+        }
     }
     if (lane == 0) {
         w.cnt[i] = m;

@@ -548,8 +548,7 @@ static cudaError_t launch_knn_s(const BuildArgs &a, const Work &w, cudaStream_t 
 cudaError_t launch_knn(const BuildArgs &a, const Work &w, cudaStream_t s) {
     if (a.atom_hi <= a.atom_lo) return cudaSuccess;
     if (a.knn_k <= 24) return launch_knn_s<1, true>(a, w, s);
-    if (a.knn_k <= 32) return launch_knn_s<1, false>(a, w, s);
-    if (a.knn_k <= 64) return launch_knn_s<2, false>(a, w, s);
+    if (a.knn_k <= 56) return launch_knn_s<2, true>(a, w, s);
     return launch_knn_s<4, false>(a, w, s);
 }
 

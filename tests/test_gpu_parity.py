@@ -269,8 +269,12 @@ def test_schedules_and_per_structure_identical():
     batch = to_device(b)
     ref = graph_arrays(mg.cutoff_graph(batch, 6.0, opts=mg.make_opts(schedule=1)))
     per = graph_arrays(mg.cutoff_graph(batch, 6.0, opts=mg.make_opts(schedule=2)))
+    onepass = graph_arrays(mg.cutoff_graph(batch, 6.0, opts=mg.make_opts(schedule=3)))
+    staged = graph_arrays(mg.cutoff_graph(batch, 6.0, opts=mg.make_opts(schedule=4)))
     ps = graph_arrays(mg.build_per_structure(batch, "cutoff", cutoff=6.0))
-    for other in (per, ps):
+    mg.autotune(batch, "cutoff", cutoff=6.0)
+    tuned = graph_arrays(mg.cutoff_graph(batch, 6.0))
+    for other in (per, onepass, staged, ps, tuned):
         for key in ref:
             np.testing.assert_array_equal(ref[key], other[key], err_msg=key)
     kref = graph_arrays(mg.knn_graph(batch, 16, opts=mg.make_opts(schedule=1)))

@@ -388,3 +388,21 @@ def test_fused_lattice_reduction_with_empty_structures():
     assert mg.last_launch_count() == 2
     assert torch.equal(gf_fused, gf2) and torch.equal(gL_fused, gL2)
     grad_check(b, g, synth.normal(31, 1, g.num_edges))
+
+
+@pytest.mark.parametrize("schedule", [3, 4])
+def test_sources_beyond_the_shared_staging_are_enumerated_again(schedule):
+    """A source with more than 1024 edges does not fit the shared-memory staging: both
+    builds count it, then enumerate it again in canonical order (here one atom in a
+    unit cube at cutoff 7.3: every image within 7.3 of it, ~1600 edges, next to normal
+    sources)."""
+    opts = mg.make_opts(schedule=schedule)
+    b = synth.concat([synth.crystal(np.eye(3), [[0.1, 0.2, 0.3]]), synth.make_batch(1, B=3)])
+    g = mg.cutoff_graph(to_device(b), 7.3, opts=opts)
+    got = graph_arrays(g)
+    want = oracle.cutoff(b.lattice, b.frac, b.atom_ptr, 7.3)
+    assert np.diff(got["src_ptr"]).max() > 1024
+    assert_same_edges(got, want, "spilled source")
+    assert_vectors(b, got)
+    assert_perm_dst(got, b.total_atoms)
+    grad_check(b, g, synth.normal(41, schedule, g.num_edges))
