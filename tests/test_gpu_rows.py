@@ -406,3 +406,28 @@ def test_sources_beyond_the_shared_staging_are_enumerated_again(schedule):
     assert_vectors(b, got)
     assert_perm_dst(got, b.total_atoms)
     grad_check(b, g, synth.normal(41, schedule, g.num_edges))
+
+
+def test_staged_build_replay_and_device_errors():
+    """The staged build captured in a plan and replayed for moving geometry, and a
+    structure with bad input reported while the others are still built."""
+    opts = mg.make_opts(schedule=4)
+    b = synth.make_batch(4, B=64)
+    batch = to_device(b)
+    g = mg.cutoff_graph(batch, 5.0, capacity=400000, opts=opts)
+    cur = b
+    for step in range(3):
+        cur = synth.perturb(cur, seed=13, step=step)
+        g = mg.update_graph(g, torch.from_numpy(cur.frac).cuda(), torch.from_numpy(cur.lattice).cuda())
+        got = graph_arrays(g)
+        assert_same_edges(got, oracle.cutoff(cur.lattice, cur.frac, cur.atom_ptr, 5.0), f"step {step}")
+        assert_vectors(cur, got)
+    grad_check(cur, g, synth.normal(51, 0, g.num_edges))
+    bad = synth.make_batch(1, B=3)
+    lat = bad.lattice.copy()
+    lat[1] = 0.0  # singular
+    gb = mg.cutoff_graph(to_device(synth.Batch(lat, bad.frac, bad.atom_ptr)), 5.0, sync=False, opts=opts)
+    st = gb.read_status()
+    assert st["code"] == 3 and st["first_bad_structure"] == 1
+    want = oracle.cutoff(bad.lattice[:1], bad.frac[:bad.atom_ptr[1]], bad.atom_ptr[:2], 5.0)
+    assert int(gb.edge_ptr[1].item()) == len(want["src"])
