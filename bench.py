@@ -335,40 +335,58 @@ def run_mine(args, rank, world, local_rank):
         tot_units, max_ms = reduce_over_ranks(tot_units, max_ms, dev)
     value = tot_units / (max_ms / 1e3)
 
-    # e2e through the public API: pinned host inputs in, results out, every step
+    # e2e: the step's library calls (both graph updates, forward, backward with the loss
+    # gradient) from pinned host inputs to pinned host outputs.  Every step copies the
+    # inputs in and every output back: both graphs' edges, status words, vectors and
+    # gradients.  Each graph's copies start as soon as it is final, so they overlap the
+    # rest of the step; the host waits once, at the end, then checks both status words.
     frac_h = torch.from_numpy(b.frac).pin_memory()
     lat_h = torch.from_numpy(b.lattice).pin_memory()
     ptr_h = torch.from_numpy(b.atom_ptr).pin_memory()
-    w_dev = grad_len[:E_cut]
+    w_dev = grad_len  # dLoss/dlen of the loss sum(w * len)
     e2e_steps = max(5, min(args.steps, 50))
+    copy_stream = torch.cuda.Stream(dev)
+    ev_in, ev_cut = torch.cuda.Event(), torch.cuda.Event()
     host_out = {}
 
+    def to_host(q, t):
+        if q not in host_out:
+            host_out[q] = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+        host_out[q].copy_(t, non_blocking=True)
+        return t.numel() * t.element_size()
+
     def e2e_step():
-        # inputs in, both graphs rebuilt, loss backward, every output back; the host waits
-        # once, at the end, and then checks both status words it copied back with the rest
         batch.frac.copy_(frac_h, non_blocking=True)
         batch.lattice.copy_(lat_h, non_blocking=True)
         batch.atom_ptr.copy_(ptr_h, non_blocking=True)
-        mg.update_graph(g_cut, sync=False)
-        mg.update_graph(g_knn, sync=False)
-        fr = batch.frac.detach().requires_grad_(True)
-        la = batch.lattice.detach().requires_grad_(True)
-        vec, ln = mg.edge_vectors(fr, la, g_cut)
-        (ln * w_dev).sum().backward()
-        outs = [g_cut.status, g_knn.status, g_cut.src[:E_cut], g_cut.dst[:E_cut], g_cut.offset[:E_cut],
-                vec.detach(), ln.detach(), g_knn.src[:E_knn], g_knn.dst[:E_knn], g_knn.offset[:E_knn],
-                g_knn.vec[:E_knn], g_knn.len[:E_knn], fr.grad, la.grad]
+        ev_in.record(main_stream)
+        knn_stream.wait_event(ev_in)
         d2h = 0
-        for q, t in enumerate(outs):
-            if q not in host_out or host_out[q].shape != t.shape:
-                host_out[q] = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
-            host_out[q].copy_(t, non_blocking=True)
-            d2h += t.numel() * t.element_size()
+        torch.cuda.set_stream(knn_stream)
+        mg.update_graph(g_knn, sync=False)
+        for q, t in enumerate((g_knn.status, g_knn.src[:E_knn], g_knn.dst[:E_knn], g_knn.offset[:E_knn],
+                               g_knn.vec[:E_knn], g_knn.len[:E_knn])):
+            d2h += to_host(("knn", q), t)
+        ev_join.record(knn_stream)
+        torch.cuda.set_stream(main_stream)
+        mg.update_graph(g_cut, sync=False)
+        ev_cut.record(main_stream)
+        copy_stream.wait_event(ev_cut)
+        torch.cuda.set_stream(copy_stream)
+        for q, t in enumerate((g_cut.status, g_cut.src[:E_cut], g_cut.dst[:E_cut], g_cut.offset[:E_cut])):
+            d2h += to_host(("cut", q), t)
+        torch.cuda.set_stream(main_stream)
+        mg.edge_vectors_fwd(g_cut, out_vec=out_vec, out_len=out_len)
+        mg.edge_vectors_bwd(g_cut, batch, None, w_dev, out_vec, out_len, grad_frac, grad_lat)
+        for q, t in enumerate((out_vec[:E_cut], out_len[:E_cut], grad_frac, grad_lat)):
+            d2h += to_host(("step", q), t)
         torch.cuda.synchronize(dev)
-        for q, E in ((0, E_cut), (1, E_knn)):  # code 0 and the same edge count as the first build
-            assert int(host_out[q][0]) & 0xFFFFFFFF == 0 and int(host_out[q][1]) == E, host_out[q]
+        for key, E in ((("cut", 0), E_cut), (("knn", 0), E_knn)):  # code 0, same edge count as the first build
+            st_h = host_out[key]
+            assert int(st_h[0]) & 0xFFFFFFFF == 0 and int(st_h[1]) == E, st_h
         return E_cut + E_knn, d2h
 
+    mg.profile_enable(False, dev)  # no stage events in the user's path
     e2e_step()
     e2e_t, e2e_units, d2h = 0.0, 0, 0
     for _ in range(e2e_steps):
@@ -377,6 +395,7 @@ def run_mine(args, rank, world, local_rank):
         u_, d2h = e2e_step()
         e2e_t += time.perf_counter() - t0
         e2e_units += u_
+    mg.profile_enable(True, dev)
     h2d = (frac_h.numel() * 4 + lat_h.numel() * 4 + ptr_h.numel() * 4)
     e2e_val = e2e_units / e2e_t
     if world > 1:  # e2e throughput of the replicas adds up

@@ -437,12 +437,19 @@ class EdgeVectors(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, frac, lattice, graph: Graph):
-        batch = graph.batch.with_geometry(frac.detach().contiguous(), lattice.detach().contiguous())
+        gb = graph.batch
+        if (frac.data_ptr() == gb.frac.data_ptr() and lattice.data_ptr() == gb.lattice.data_ptr()
+                and frac.shape == gb.frac.shape and lattice.shape == gb.lattice.shape
+                and frac.is_contiguous() and lattice.is_contiguous()):
+            batch = gb  # the graph's own coordinate buffers
+        else:
+            batch = gb.with_geometry(frac.detach().contiguous(), lattice.detach().contiguous())
         vec, ln = edge_vectors_fwd(graph, batch)
         E = graph.num_edges
         ctx.graph = graph
         ctx.batch = batch
         ctx.save_for_backward(vec, ln)
+        ctx.set_materialize_grads(False)  # an unused output passes NULL, not a zero array
         return vec[:E], ln[:E]
 
     @staticmethod

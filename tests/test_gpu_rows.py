@@ -390,6 +390,30 @@ def test_fused_lattice_reduction_with_empty_structures():
     grad_check(b, g, synth.normal(31, 1, g.num_edges))
 
 
+def test_symmetric_backward_large_structures_and_grad_vec():
+    """Structures above 1024 atoms: the symmetric backward followed by the block-per-
+    structure lattice reduction.  Both incoming gradients (grad_vec and grad_len)
+    against the oracle; deterministic."""
+    b = synth.make_batch(5, B=4)
+    assert int(np.diff(b.atom_ptr).max()) > 1024
+    batch = to_device(b)
+    g = mg.cutoff_graph(batch, 5.0, with_perm=False)
+    E = g.num_edges
+    v, ln = mg.edge_vectors_fwd(g)
+    gv = torch.from_numpy(synth.normal(41, 0, 3 * E).reshape(-1, 3)).cuda()
+    gl = torch.from_numpy(synth.normal(41, 1, E)).cuda()
+    f1, L1 = mg.edge_vectors_bwd(g, batch, gv, gl, v, ln)
+    assert mg.last_launch_count() == 2  # bwd_sym + the block-per-structure reduction
+    f2, L2 = mg.edge_vectors_bwd(g, batch, gv, gl, v, ln)
+    assert torch.equal(f1, f2) and torch.equal(L1, L2)
+    got = graph_arrays(g)
+    gf, gL = oracle.edge_grad(b.lattice, b.frac, b.atom_ptr, got["src"], got["dst"], got["offset"],
+                              gv.cpu().numpy().astype(np.float64), gl.cpu().numpy().astype(np.float64))
+    np.testing.assert_allclose(f1.cpu().numpy(), gf, rtol=1e-4, atol=1e-4 * np.abs(gf).max())
+    np.testing.assert_allclose(L1.cpu().numpy(), gL, rtol=1e-4, atol=1e-4 * np.abs(gL).max())
+    grad_check(b, g, synth.normal(41, 2, E))
+
+
 @pytest.mark.parametrize("schedule", [3, 4])
 def test_sources_beyond_the_shared_staging_are_enumerated_again(schedule):
     """A source with more than 1024 edges does not fit the shared-memory staging: both
