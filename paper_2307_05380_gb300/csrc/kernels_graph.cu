@@ -685,23 +685,39 @@ __device__ __forceinline__ unsigned long long load_flag(const unsigned long long
 // Exclusive prefix of tile `tile` from its predecessors' published words.  Every wait is
 // bounded: a predecessor that publishes nothing within the limit makes the build report
 // MG_ERR_TIMEOUT (and the prefix is then wrong) instead of hanging.
-__device__ long long tile_lookback(const unsigned long long *flags, int tile, mg_device_status_t *status) {
+// The warp reads the flags of the 32 nearest predecessors not yet accounted for and
+// consumes them once every flag up to the nearest published prefix is set; a window with
+// an unpublished flag is read again (nothing is skipped), so a tile never waits on a
+// predecessor beyond its nearest prefix.  Called by a whole warp; every lane returns the
+// prefix.
+__device__ long long tile_lookback_warp(const unsigned long long *flags, int tile, mg_device_status_t *status) {
+    const int lane = lane_id();
     long long excl = 0;
-    int q = tile - 1, spins = 0;
-    while (q >= 0) {
-        const unsigned long long v = load_flag(&flags[q]);
+    int top = tile - 1, spins = 0;
+    while (top >= 0) {
+        const int q = top - lane;
+        const unsigned long long v = q >= 0 ? load_flag(&flags[q]) : TILE_PREFIX;  // before tile 0: prefix 0
         const unsigned long long f = v & ~TILE_VALUE;
-        if (f == 0) {
+        const unsigned pre = __ballot_sync(FULL, f == TILE_PREFIX);
+        const unsigned none = __ballot_sync(FULL, f == 0);
+        const int kp = pre ? __ffs(pre) - 1 : 31;  // nearest prefix in the window
+        const unsigned need = kp == 31 ? FULL : ((2u << kp) - 1u);
+        if (none & need) {
             if (++spins > LOOKBACK_SPIN_LIMIT) {
-                set_error(status, MG_ERR_TIMEOUT, -1);
+                // give up at the first unpublished predecessor, keeping what precedes it:
+                // every tile stopped by the same silent predecessor then gets the same
+                // shifted prefix, so the offsets stay monotone (the build still fails)
+                const int kz = __ffs(none & need) - 1;
+                excl += warp_sum(lane < kz ? (long long)(v & TILE_VALUE) : 0ll);
+                if (lane == 0) set_error(status, MG_ERR_TIMEOUT, -1);
                 break;
             }
             __nanosleep(32);
             continue;
         }
-        excl += (long long)(v & TILE_VALUE);
-        if (f == TILE_PREFIX) break;
-        --q;
+        excl += warp_sum(lane <= kp ? (long long)(v & TILE_VALUE) : 0ll);
+        if (pre) break;
+        top -= 32;
         spins = 0;
     }
     return excl;
@@ -905,21 +921,22 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_build_kernel(Build
     }
     if (lane == 0) s_cnt[wid] = m;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (wid == 0) {  // the tile's count and prefix: one warp looks back
         long long agg = 0;
         for (int q = 0; q < BUILD_WARPS; ++q) agg += s_cnt[q];
         long long prefix = 0;
         if (tile == a.fault_tile) {
             // testing hook: this tile publishes nothing; the waits of later tiles run out
         } else if (tile == 0) {
-            atomicExch(&flags[0], TILE_PREFIX | (unsigned long long)agg);
+            if (lane == 0) atomicExch(&flags[0], TILE_PREFIX | (unsigned long long)agg);
         } else {
-            atomicExch(&flags[tile], TILE_AGG | (unsigned long long)agg);
-            prefix = tile_lookback(flags, tile, g.status);
-            atomicExch(&flags[tile], TILE_PREFIX | (unsigned long long)(prefix + agg));
+            if (lane == 0) atomicExch(&flags[tile], TILE_AGG | (unsigned long long)agg);
+            __syncwarp();
+            prefix = tile_lookback_warp(flags, tile, g.status);
+            if (lane == 0) atomicExch(&flags[tile], TILE_PREFIX | (unsigned long long)(prefix + agg));
         }
-        s_prefix = prefix;
-        if (tile == ntiles - 1) {  // the last tile knows the edge count
+        if (lane == 0) s_prefix = prefix;
+        if (lane == 0 && tile == ntiles - 1) {  // the last tile knows the edge count
             const long long tot = prefix + agg;
             Status *st = reinterpret_cast<Status *>(g.status);
             st->num_edges = (unsigned long long)tot;
@@ -1221,7 +1238,9 @@ __global__ void __launch_bounds__(256) dst_perm_symmetric_kernel(int N, const in
                                                                  int32_t *__restrict__ perm,
                                                                  int64_t *__restrict__ dst_ptr,
                                                                  mg_device_status_t *status) {
-    if (*E_dev > capacity) return;
+    const int64_t E = *E_dev;
+    if (E > capacity) return;
+    if (reinterpret_cast<const Status *>(status)->code == MG_ERR_TIMEOUT) return;  // offsets not valid
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (j >= N) return;
     const int64_t lo = src_ptr[j], hi = src_ptr[j + 1];
@@ -1229,11 +1248,23 @@ __global__ void __launch_bounds__(256) dst_perm_symmetric_kernel(int N, const in
         dst_ptr[j] = lo;
         if (j == N - 1) dst_ptr[N] = hi;
     }
+    if (lo < 0 || hi > E) {  // never for a graph built here
+        if (lane_id() == 0) set_error(status, MG_ERR_INTERNAL, -1);
+        return;
+    }
     for (int64_t p = lo + lane_id(); p < hi; p += 32) {
         const int i = dst[p];
+        if (i < 0 || i >= N) {  // never for a graph built here
+            set_error(status, MG_ERR_INTERNAL, -1);
+            continue;
+        }
         const int64_t rlo = bound32(dst, lo, hi, i, false);
         const int64_t rhi = bound32(dst, lo, hi, i, true);
         const int64_t ilo = src_ptr[i], ihi = src_ptr[i + 1];
+        if (ilo < 0 || ihi > E || ihi < ilo) {  // never for a graph built here
+            set_error(status, MG_ERR_INTERNAL, -1);
+            continue;
+        }
         const int64_t sij = bound32(dst, ilo, ihi, j, false);
         if (p == rlo) {  // the reverse run must have the same length
             const int64_t len = rhi - rlo;
