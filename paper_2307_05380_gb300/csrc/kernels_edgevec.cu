@@ -119,6 +119,47 @@ __device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
     return make_float2(s, __fadd_rn(__fadd_rn(a.y, b.y), e));
 }
 
+// Compensated warp sums of 16 FP32 values per lane at once (reduce-scatter): at each
+// butterfly step a lane keeps half of its values and sends the other half to its
+// partner, so lane l ends with the sum of value l >> 1 after 24 shuffles instead of 160.
+// Each value meets the same partners in the same order as in warp_sum_ff, and ff_add
+// is exact in its TwoSum and symmetric, so the sums are bit-identical to it.
+__device__ __forceinline__ float2 warp_reduce16_ff(const float v[16]) {
+    const int lane = lane_id();
+    float2 a[8];
+    {
+        const bool up = lane & 16;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float keep = up ? v[8 + k] : v[k], send = up ? v[k] : v[8 + k];
+            a[k] = ff_add(make_float2(keep, 0.f), make_float2(__shfl_xor_sync(FULL, send, 16), 0.f));
+        }
+    }
+    float2 b[4];
+    {
+        const bool up = lane & 8;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 keep = up ? a[4 + k] : a[k], send = up ? a[k] : a[4 + k];
+            b[k] = ff_add(keep, make_float2(__shfl_xor_sync(FULL, send.x, 8), __shfl_xor_sync(FULL, send.y, 8)));
+        }
+    }
+    float2 c[2];
+    {
+        const bool up = lane & 4;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float2 keep = up ? b[2 + k] : b[k], send = up ? b[k] : b[2 + k];
+            c[k] = ff_add(keep, make_float2(__shfl_xor_sync(FULL, send.x, 4), __shfl_xor_sync(FULL, send.y, 4)));
+        }
+    }
+    const bool up = lane & 2;
+    const float2 keep = up ? c[1] : c[0], send = up ? c[0] : c[1];
+    float2 d = ff_add(keep, make_float2(__shfl_xor_sync(FULL, send.x, 2), __shfl_xor_sync(FULL, send.y, 2)));
+    return ff_add(d, make_float2(__shfl_xor_sync(FULL, d.x, 1), __shfl_xor_sync(FULL, d.y, 1)));
+}
+
+
 __device__ __forceinline__ float2 ff_neg(float2 a) { return make_float2(-a.x, -a.y); }
 
 // (sum_c g_c L[k][c]) for a float-float gradient: FP32 terms, error within a few
@@ -130,6 +171,26 @@ __device__ __forceinline__ float ff_times_LT(const float2 g[3], const float *L, 
     h = __fmaf_rn(g[0].y, L[3 * k + 0], h);
     h = __fmaf_rn(g[1].y, L[3 * k + 1], h);
     return __fmaf_rn(g[2].y, L[3 * k + 2], h);
+}
+
+// A source atom's three gradient sums and nine lattice partials in one reduce-scatter:
+// grad_frac[j] from the gradient sums (lanes 0-2), lpart[j] from the lattice partials.
+__device__ __forceinline__ void store_atom_sums(float *__restrict__ grad_frac, float2 *__restrict__ lpart, int64_t j,
+                                                const float acc[3], const float M[9], const float *L) {
+    const int lane = lane_id();
+    float v[16];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) v[q] = acc[q];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) v[3 + q] = M[q];
+#pragma unroll
+    for (int q = 12; q < 16; ++q) v[q] = 0.f;
+    const float2 r = warp_reduce16_ff(v);  // lanes 2q, 2q + 1: value q
+    float2 tot[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) tot[q] = make_float2(__shfl_sync(FULL, r.x, 2 * q), __shfl_sync(FULL, r.y, 2 * q));
+    if (lane < 3) grad_frac[3 * j + lane] = ff_times_LT(tot, L, lane);
+    if (!(lane & 1) && lane >= 6 && lane < 24) lpart[9 * j + (lane / 2 - 3)] = r;
 }
 
 // Lattice partial of one edge: M[k][c] += df_k g_c with df = x_j - x_i + t carried
@@ -373,14 +434,10 @@ __global__ void __launch_bounds__(256, 5) bwd_sym_kernel(EdgeVecArgs a, float2 *
         const float xi[3] = {a.frac[3 * (int64_t)i], a.frac[3 * (int64_t)i + 1], a.frac[3 * (int64_t)i + 2]};
         add_lattice_term(M, xj, xi, t, g);
     }
-    float2 tot[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) tot[q] = warp_sum_ff(acc[q]);
-    if (lane < 3) {
+    {
         const int s = sj >= 0 ? sj : structure_of(a.atom_ptr, a.B, j);
-        a.grad_frac[3 * (int64_t)j + lane] = ff_times_LT(tot, a.lattice + 9 * (int64_t)s, lane);
+        store_atom_sums(a.grad_frac, lpart, j, acc, M, a.lattice + 9 * (int64_t)s);
     }
-    store_lattice_partial(lpart, j, M);
     if (a.lat_cnt) {
         // the last warp of the structure to store its partial reduces the structure's
         // lattice gradient (the order of the sum does not depend on which warp it is)

@@ -829,18 +829,33 @@ __device__ __forceinline__ void emit_source(const BuildArgs &a, const Work &w, c
     const int lane = lane_id();
     if (!spill) {
         const bool pairs = !PERSRC && a.write_pairs && S.n <= PAIR_MAX;
-        for (int q = lane; q < m; q += 32) {
-            const unsigned long long key = keys[q];
-            int t0, t1, t2;
-            unpack_t((uint32_t)(key & 0xffffffffull), t0, t1, t2);
-            const int jl = (int)(key >> 32);
-            const int64_t jr = (int64_t)S.begin + jl;
-            if (pairs) {
-                if (q == 0 || (int)(keys[q - 1] >> 32) != jl) w.pair_lo[(int64_t)i * PAIR_MAX + jl] = (uint16_t)q;
-                if (q == m - 1 || (int)(keys[q + 1] >> 32) != jl)
-                    w.pair_hi[(int64_t)i * PAIR_MAX + jl] = (uint16_t)(q + 1);
+        // two edges per lane and step: both targets' coordinates are loaded before
+        // either edge is computed and stored, so their latencies overlap
+        for (int q0 = lane; q0 < m; q0 += 64) {
+            const int q1 = q0 + 32;
+            const bool two = q1 < m;
+            const unsigned long long k0 = keys[q0], k1 = two ? keys[q1] : k0;
+            const int64_t j0 = (int64_t)S.begin + (int)(k0 >> 32), j1 = (int64_t)S.begin + (int)(k1 >> 32);
+            const float x00 = a.frac[3 * j0], x01 = a.frac[3 * j0 + 1], x02 = a.frac[3 * j0 + 2];
+            const float x10 = a.frac[3 * j1], x11 = a.frac[3 * j1 + 1], x12 = a.frac[3 * j1 + 2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (h == 1 && !two) break;
+                const int q = h ? q1 : q0;
+                const unsigned long long key = h ? k1 : k0;
+                int t0, t1, t2;
+                unpack_t((uint32_t)(key & 0xffffffffull), t0, t1, t2);
+                const int jl = (int)(key >> 32);
+                if (pairs) {
+                    if (q == 0 || (int)(keys[q - 1] >> 32) != jl) w.pair_lo[(int64_t)i * PAIR_MAX + jl] = (uint16_t)q;
+                    if (q == m - 1 || (int)(keys[q + 1] >> 32) != jl)
+                        w.pair_hi[(int64_t)i * PAIR_MAX + jl] = (uint16_t)(q + 1);
+                }
+                if (h == 0)
+                    emit_edge(g, S, i, base + q, j0, x00, x01, x02, t0, t1, t2);
+                else
+                    emit_edge(g, S, i, base + q, j1, x10, x11, x12, t0, t1, t2);
             }
-            emit_edge(g, S, i, base + q, jr, a.frac[3 * jr], a.frac[3 * jr + 1], a.frac[3 * jr + 2], t0, t1, t2);
         }
         return;
     }
