@@ -28,6 +28,24 @@ __device__ __forceinline__ int structure_of(const int32_t *__restrict__ atom_ptr
     return lo;
 }
 
+// Largest s in [0, n) with ptr[s] <= key (ptr non-decreasing, ptr[0] <= key), found by
+// the whole warp in rounds of 32 probes: about log32(n) dependent loads instead of
+// log2(n) for a binary search.  Warp-uniform arguments.
+__device__ __forceinline__ int warp_last_leq(const int64_t *__restrict__ ptr, int n, int64_t key) {
+    const int lane = lane_id();
+    int lo = 0, len = n;  // the answer lies in [lo, lo + len) and ptr[lo] <= key
+    while (len > 1) {
+        const int step = (len + 31) / 32;
+        const int idx = lo + lane * step;
+        const bool le = idx < lo + len && ptr[idx] <= key;
+        const int c = __popc(__ballot_sync(FULL, le));  // probes 0 .. c-1 satisfy it (c >= 1)
+        const int end = lo + len;
+        lo += (c - 1) * step;
+        len = min(step, end - lo);
+    }
+    return lo;
+}
+
 // A thread per edge: every edge is independent, so the forward runs at full occupancy
 // whatever the degrees.  Each warp takes one contiguous range of edges, 32 at a time,
 // so the structure of an edge (from edge_ptr) is found by one binary search per warp and
@@ -41,16 +59,7 @@ __global__ void __launch_bounds__(256) edgevec_fwd_kernel(EdgeVecArgs a) {
     const int64_t chunk = ((E + warps - 1) / warps + 31) & ~(int64_t)31;
     const int64_t e0 = wid * chunk, e1 = min(E, e0 + chunk);
     if (e0 >= e1) return;
-    int s = 0;  // last structure whose first edge is <= e0
-    {
-        int lo = 0, hi = a.B;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (a.g.edge_ptr[mid] <= e0) lo = mid;
-            else hi = mid;
-        }
-        s = lo;
-    }
+    int s = warp_last_leq(a.g.edge_ptr, a.B, e0);  // last structure whose first edge is <= e0
     for (int64_t e = e0 + lane; e < e1; e += 32) {
         while (s + 1 < a.B && a.g.edge_ptr[s + 1] <= e) ++s;
         const float *L = a.lattice + 9 * (int64_t)s;
@@ -173,6 +182,30 @@ __device__ __forceinline__ float ff_times_LT(const float2 g[3], const float *L, 
     return __fmaf_rn(g[2].y, L[3 * k + 2], h);
 }
 
+// The same for 32 values: lane l ends with the sum of value l (62 shuffles instead of 320).
+__device__ __forceinline__ float2 warp_reduce32_ff(const float v[32]) {
+    const int lane = lane_id();
+    float2 a[16];
+    {
+        const bool up = lane & 16;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const float keep = up ? v[16 + k] : v[k], send = up ? v[k] : v[16 + k];
+            a[k] = ff_add(make_float2(keep, 0.f), make_float2(__shfl_xor_sync(FULL, send, 16), 0.f));
+        }
+    }
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) {  // keep half of the o-slot window, send the other half
+        const bool up = lane & o;
+#pragma unroll
+        for (int k = 0; k < o; ++k) {
+            const float2 keep = up ? a[o + k] : a[k], send = up ? a[k] : a[o + k];
+            a[k] = ff_add(keep, make_float2(__shfl_xor_sync(FULL, send.x, o), __shfl_xor_sync(FULL, send.y, o)));
+        }
+    }
+    return a[0];
+}
+
 // A source atom's three gradient sums and nine lattice partials in one reduce-scatter:
 // grad_frac[j] from the gradient sums (lanes 0-2), lpart[j] from the lattice partials.
 __device__ __forceinline__ void store_atom_sums(float *__restrict__ grad_frac, float2 *__restrict__ lpart, int64_t j,
@@ -285,14 +318,18 @@ __device__ __forceinline__ void lattice_reduce_warp(const EdgeVecArgs &a, const 
     for (int r = lo + lane; r < hi; r += 32)
 #pragma unroll
         for (int q = 0; q < 9; ++q) acc[q] = ff_add(acc[q], __ldcg(&lpart[9 * (int64_t)r + q]));  // L2: written by other SMs
-    float out = 0.f;
+    // the nine high and nine low parts summed across the warp in one reduce-scatter
+    float v[32];
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-        const float2 h = warp_sum_ff(acc[q].x);
-        const float2 l = warp_sum_ff(acc[q].y);
-        if (lane == q) out = __fadd_rn(h.x, __fadd_rn(h.y, __fadd_rn(l.x, l.y)));
+        v[q] = acc[q].x;
+        v[9 + q] = acc[q].y;
     }
-    if (lane < 9) a.grad_lattice[9 * (int64_t)s + lane] = out;
+#pragma unroll
+    for (int q = 18; q < 32; ++q) v[q] = 0.f;
+    const float2 h = warp_reduce32_ff(v);  // lane q: value q
+    const float2 l = make_float2(__shfl_sync(FULL, h.x, (lane + 9) & 31), __shfl_sync(FULL, h.y, (lane + 9) & 31));
+    if (lane < 9) a.grad_lattice[9 * (int64_t)s + lane] = __fadd_rn(h.x, __fadd_rn(h.y, __fadd_rn(l.x, l.y)));
 }
 
 __global__ void __launch_bounds__(256) bwd_lat_kernel(EdgeVecArgs a, const float2 *__restrict__ lpart) {
@@ -358,7 +395,7 @@ __device__ __forceinline__ int64_t key_bound(const int32_t *__restrict__ keys, i
 // grad_frac[j] = sum_p (g_rev(p) - g_p) L^T; the lattice partial sums (x_i - x_j + t)^T g_p.
 // Fixed per-lane order and a fixed warp reduction: deterministic, no destination order.
 template <int PAIRS>
-__global__ void __launch_bounds__(256, 5) bwd_sym_kernel(EdgeVecArgs a, float2 *__restrict__ lpart) {
+__global__ void __launch_bounds__(256, 4) bwd_sym_kernel(EdgeVecArgs a, float2 *__restrict__ lpart) {
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = lane_id();
     if (j >= a.N) return;
@@ -377,17 +414,44 @@ __global__ void __launch_bounds__(256, 5) bwd_sym_kernel(EdgeVecArgs a, float2 *
     float M[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) M[q] = 0.f;
+    // software-pipelined: the next chunk's targets are loaded one chunk ahead, and every
+    // load that depends on the edge alone is issued before the chain through the target
+    // (pair table, segment bounds) to the reverse edge's gradient
+    int i_next = (lo + lane < hi) ? a.g.dst[lo + lane] : -1;
     for (int64_t p0 = lo; p0 < hi; p0 += 32) {
         const int64_t p = p0 + lane;
         const bool valid = p < hi;
-        const int i = valid ? a.g.dst[p] : -1;
+        const int i = i_next;
+        i_next = (p + 32 < hi) ? a.g.dst[p + 32] : -1;
+        float3 g = make_float3(0.f, 0.f, 0.f);
+        float f = 0.f, vx = 0.f, vy = 0.f, vz = 0.f, l = 0.f;
+        int t[3] = {0, 0, 0};
+        float xi[3] = {0.f, 0.f, 0.f};
+        int64_t ilo = 0, ihi = 0;
+        if (valid) {
+            if (a.grad_vec) g = make_float3(a.grad_vec[3 * p], a.grad_vec[3 * p + 1], a.grad_vec[3 * p + 2]);
+            if (a.grad_len) {
+                l = a.len[p];
+                vx = a.vec[3 * p];
+                vy = a.vec[3 * p + 1];
+                vz = a.vec[3 * p + 2];
+                if (l > 0.f) f = __fdiv_rn(a.grad_len[p], l);
+            }
+            t[0] = a.g.offset[3 * p];
+            t[1] = a.g.offset[3 * p + 1];
+            t[2] = a.g.offset[3 * p + 2];
+            xi[0] = a.frac[3 * (int64_t)i];
+            xi[1] = a.frac[3 * (int64_t)i + 1];
+            xi[2] = a.frac[3 * (int64_t)i + 2];
+            ilo = a.g.src_ptr[i];
+            ihi = a.g.src_ptr[i + 1];
+        }
         int64_t rev = 0;
         if (PAIRS && sj >= 0) {
             if (valid) {
                 const int il = i - begin, jl = j - begin;
                 const int64_t rhi = lo + a.pair_hi[(int64_t)j * PAIR_MAX + il];
-                const int64_t sij = a.g.src_ptr[i] + a.pair_lo[(int64_t)i * PAIR_MAX + jl];
-                rev = sij + (rhi - 1 - p);
+                rev = ilo + a.pair_lo[(int64_t)i * PAIR_MAX + jl] + (rhi - 1 - p);
             }
         } else {
             // lanes of one run (same target i, contiguous) share the run's two searches
@@ -398,40 +462,31 @@ __global__ void __launch_bounds__(256, 5) bwd_sym_kernel(EdgeVecArgs a, float2 *
                 int64_t e = p + 1;  // end of the run: a short probe, then a binary search
                 while (e < hi && e < p + 4 && a.g.dst[e] == i) ++e;
                 rhi = (e < hi && e == p + 4 && a.g.dst[e] == i) ? key_bound(a.g.dst, e, hi, i, true) : e;
-                sij = key_bound(a.g.dst, a.g.src_ptr[i], a.g.src_ptr[i + 1], j, false);
+                sij = key_bound(a.g.dst, ilo, ihi, j, false);
             }
             rhi = __shfl_sync(FULL, rhi, leader);
             sij = __shfl_sync(FULL, sij, leader);
             rev = sij + (rhi - 1 - p);
         }
         if (!valid) continue;
-        if (rev < a.g.src_ptr[i] || rev >= a.g.src_ptr[i + 1]) {  // never for a graph built here
+        if (rev < ilo || rev >= ihi) {  // never for a graph built here
             set_error(a.g.status, MG_ERR_INTERNAL, -1);
             rev = p;
         }
-        float3 g = make_float3(0.f, 0.f, 0.f), gr = g;
-        if (a.grad_vec) {
-            g = make_float3(a.grad_vec[3 * p], a.grad_vec[3 * p + 1], a.grad_vec[3 * p + 2]);
-            gr = make_float3(a.grad_vec[3 * rev], a.grad_vec[3 * rev + 1], a.grad_vec[3 * rev + 2]);
-        }
-        if (a.grad_len) {
-            const float l = a.len[p];
-            if (l > 0.f) {
-                const float f = __fdiv_rn(a.grad_len[p], l), fr = __fdiv_rn(a.grad_len[rev], l);
-                const float vx = a.vec[3 * p], vy = a.vec[3 * p + 1], vz = a.vec[3 * p + 2];
-                g.x = __fmaf_rn(f, vx, g.x);
-                g.y = __fmaf_rn(f, vy, g.y);
-                g.z = __fmaf_rn(f, vz, g.z);
-                gr.x = __fmaf_rn(fr, -vx, gr.x);  // the reverse edge's vector is -vec[p]
-                gr.y = __fmaf_rn(fr, -vy, gr.y);
-                gr.z = __fmaf_rn(fr, -vz, gr.z);
-            }
+        float3 gr = make_float3(0.f, 0.f, 0.f);
+        if (a.grad_vec) gr = make_float3(a.grad_vec[3 * rev], a.grad_vec[3 * rev + 1], a.grad_vec[3 * rev + 2]);
+        if (a.grad_len && l > 0.f) {
+            const float fr = __fdiv_rn(a.grad_len[rev], l);
+            g.x = __fmaf_rn(f, vx, g.x);
+            g.y = __fmaf_rn(f, vy, g.y);
+            g.z = __fmaf_rn(f, vz, g.z);
+            gr.x = __fmaf_rn(fr, -vx, gr.x);  // the reverse edge's vector is -vec[p]
+            gr.y = __fmaf_rn(fr, -vy, gr.y);
+            gr.z = __fmaf_rn(fr, -vz, gr.z);
         }
         acc[0] += gr.x - g.x;
         acc[1] += gr.y - g.y;
         acc[2] += gr.z - g.z;
-        const int t[3] = {a.g.offset[3 * p], a.g.offset[3 * p + 1], a.g.offset[3 * p + 2]};
-        const float xi[3] = {a.frac[3 * (int64_t)i], a.frac[3 * (int64_t)i + 1], a.frac[3 * (int64_t)i + 2]};
         add_lattice_term(M, xj, xi, t, g);
     }
     {
