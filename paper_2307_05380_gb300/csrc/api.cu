@@ -57,6 +57,7 @@ struct Plan {
     void *ws = nullptr;
     size_t ws_bytes = 0;
     cudaGraphExec_t exec = nullptr;
+    bool exec_profiled = false;  // exec was recorded with stage events (profiling on)
     int launches = 0;
     Prof prof;
 };
@@ -282,12 +283,15 @@ mg_status_t enqueue_build(mg_context *ctx, int kind, const mg_batch_t *b, float 
     if (launch_prep(pa, w, st)) return MG_ERR_CUDA;
     ++n;
     mk.mark("prep");
+    bool after_prep = !mk.on();  // the next launch directly follows prep in the stream
     if (b->max_atoms <= 0 || b->max_atoms >= CELL_MIN_ATOMS) {  // some structure may use a cell list
         if (launch_bins(B, N, b->frac, w, st)) return MG_ERR_CUDA;
         n += 6;
         mk.mark("bin");
+        after_prep = false;
     }
     BuildArgs ba;
+    ba.pdl = after_prep ? 1 : 0;  // the build kernel may launch while prep finishes
     ba.struct_offset = 0;
     ba.B = B;
     ba.N = N;
@@ -560,6 +564,12 @@ mg_status_t mg_update_graph(mg_context_t ctx, const mg_batch_t *batch, mg_graph_
         return r;
     }
     const int which = p.kind == MG_KIND_KNN ? MG_PROF_KNN : MG_PROF_CUTOFF;
+    if (p.exec && p.exec_profiled != ctx->prof_on) {
+        // recorded under the other profiling setting: record again, with stage events when
+        // profiling is on, without them (and with programmatic launches) when it is off
+        cudaGraphExecDestroy(p.exec);
+        p.exec = nullptr;
+    }
     if (!p.exec) {
         // with profiling on, the plan gets its own stage events (created before capture)
         Prof *prof = nullptr;
@@ -585,6 +595,7 @@ mg_status_t mg_update_graph(mg_context_t ctx, const mg_batch_t *batch, mg_graph_
             return MG_ERR_CUDA;
         }
         p.launches = n;
+        p.exec_profiled = ctx->prof_on;
     }
     if (cudaGraphLaunch(p.exec, st) != cudaSuccess) return MG_ERR_CUDA;
     ctx->last_launches = p.launches;

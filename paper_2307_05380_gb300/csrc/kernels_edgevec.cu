@@ -51,6 +51,7 @@ __device__ __forceinline__ int warp_last_leq(const int64_t *__restrict__ ptr, in
 // so the structure of an edge (from edge_ptr) is found by one binary search per warp and
 // then only moves forward.
 __global__ void __launch_bounds__(256) edgevec_fwd_kernel(EdgeVecArgs a) {
+    pdl_trigger();  // the backward may launch now; it waits for this grid before reading
     const int64_t E = a.g.edge_ptr[a.B];
     if (E > a.g.capacity) return;
     const int lane = lane_id();
@@ -396,6 +397,7 @@ __device__ __forceinline__ int64_t key_bound(const int32_t *__restrict__ keys, i
 // Fixed per-lane order and a fixed warp reduction: deterministic, no destination order.
 template <int PAIRS>
 __global__ void __launch_bounds__(256, 4) bwd_sym_kernel(EdgeVecArgs a, float2 *__restrict__ lpart) {
+    pdl_wait();  // launched early behind the forward: its vectors must be complete
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = lane_id();
     if (j >= a.N) return;
@@ -517,11 +519,9 @@ __global__ void __launch_bounds__(256, 4) bwd_sym_kernel(EdgeVecArgs a, float2 *
 cudaError_t launch_bwd_sym(const EdgeVecArgs &a, const Work &w, cudaStream_t s) {
     if (a.N <= 0) return cudaSuccess;
     const int blocks = (a.N + 7) / 8;
-    if (!a.pair_lo)
-        bwd_sym_kernel<0><<<blocks, 256, 0, s>>>(a, w.lpart);
-    else
-        bwd_sym_kernel<1><<<blocks, 256, 0, s>>>(a, w.lpart);
-    return cudaGetLastError();
+    float2 *lpart = w.lpart;
+    if (!a.pair_lo) return launch_pdl(bwd_sym_kernel<0>, dim3(blocks), dim3(256), s, a, lpart);
+    return launch_pdl(bwd_sym_kernel<1>, dim3(blocks), dim3(256), s, a, lpart);
 }
 
 cudaError_t launch_bwd_src(const EdgeVecArgs &a, const Work &w, cudaStream_t s) {

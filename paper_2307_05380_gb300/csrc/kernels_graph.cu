@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(GROUP == 32 ? 128 : GROUP) prep_kernel(PrepArg
                                                                         unsigned long long *__restrict__ tile_flags,
                                                                         unsigned int *__restrict__ queue) {
     __shared__ float red[GROUP == 32 ? 1 : 6 * (GROUP / 32)];
+    pdl_trigger();  // a build kernel launched behind prep waits for it before reading
     if (a.zero_tiles) {  // the one-pass build's look-back words and tile ticket start at zero
         const int ntiles = (a.N + BUILD_TILE - 1) / BUILD_TILE + 1;
         for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x)
@@ -920,6 +921,7 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_build_kernel(Build
     unsigned long long *flags = w.tile_flags;
     const int ntiles = gridDim.x;
 
+    pdl_wait();  // prep's records, positions and zeroed counters
     if (threadIdx.x == 0) s_tile = (int)atomicAdd(&w.queue[3], 1u);
     __syncthreads();
     const int tile = s_tile;
@@ -983,6 +985,7 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_stage_kernel(Build
     __shared__ unsigned long long keys_all[BUILD_WARPS][BUILD_CAP];
     const int wid = threadIdx.x >> 5, lane = lane_id();
     unsigned long long *keys = keys_all[wid];
+    pdl_wait();  // prep's records, positions and zeroed counters
     const int i = a.atom_lo + blockIdx.x * BUILD_WARPS + wid;
     if (i >= a.atom_hi) return;
     SrcScan c;
@@ -1093,10 +1096,9 @@ cudaError_t launch_cutoff_build(const BuildArgs &a, const Work &w, cudaStream_t 
     const int atoms = a.atom_hi - a.atom_lo;
     if (atoms <= 0) return cudaSuccess;
     const int tiles = (atoms + BUILD_WARPS - 1) / BUILD_WARPS;
-    if (a.cut_atom || a.rr_atom)
-        cutoff_build_kernel<true><<<tiles, BUILD_WARPS * 32, 0, s>>>(a, w);
-    else
-        cutoff_build_kernel<false><<<tiles, BUILD_WARPS * 32, 0, s>>>(a, w);
+    void (*kern)(BuildArgs, Work) = (a.cut_atom || a.rr_atom) ? cutoff_build_kernel<true> : cutoff_build_kernel<false>;
+    if (a.pdl) return launch_pdl(kern, dim3(tiles), dim3(BUILD_WARPS * 32), s, a, w);
+    kern<<<tiles, BUILD_WARPS * 32, 0, s>>>(a, w);
     return cudaGetLastError();
 }
 
@@ -1104,10 +1106,9 @@ cudaError_t launch_cutoff_stage(const BuildArgs &a, const Work &w, cudaStream_t 
     const int atoms = a.atom_hi - a.atom_lo;
     if (atoms <= 0) return cudaSuccess;
     const int blocks = (atoms + BUILD_WARPS - 1) / BUILD_WARPS;
-    if (a.cut_atom || a.rr_atom)
-        cutoff_stage_kernel<true><<<blocks, BUILD_WARPS * 32, 0, s>>>(a, w);
-    else
-        cutoff_stage_kernel<false><<<blocks, BUILD_WARPS * 32, 0, s>>>(a, w);
+    void (*kern)(BuildArgs, Work) = (a.cut_atom || a.rr_atom) ? cutoff_stage_kernel<true> : cutoff_stage_kernel<false>;
+    if (a.pdl) return launch_pdl(kern, dim3(blocks), dim3(BUILD_WARPS * 32), s, a, w);
+    kern<<<blocks, BUILD_WARPS * 32, 0, s>>>(a, w);
     return cudaGetLastError();
 }
 

@@ -171,6 +171,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 6) knn_kernel(BuildArgs a, Wor
     __shared__ unsigned long long band_all[KNN_WARPS][BAND_CAP];
     __shared__ float bufv_all[KNN_WARPS][64];               // pass-1 candidates waiting for a merge
     __shared__ unsigned long long bufjt_all[KNN_WARPS][64];
+    pdl_wait();  // prep's records and positions (a no-op unless launched behind prep)
     const int wid = threadIdx.x >> 5, lane = lane_id();
     unsigned long long *sel = sel_all[wid];
     unsigned long long *bl = band_all[wid];
@@ -537,6 +538,7 @@ static cudaError_t launch_knn_s(const BuildArgs &a, const Work &w, cudaStream_t 
         blocks = min(blocks, flat_blocks);
         knn_kernel<S, 2, ONEPASS><<<blocks, threads, 0, s>>>(a, w);
     } else {
+        if (a.pdl) return launch_pdl(knn_kernel<S, 1, ONEPASS>, dim3(flat_blocks), dim3(threads), s, a, w);
         knn_kernel<S, 1, ONEPASS><<<flat_blocks, threads, 0, s>>>(a, w);
     }
     return cudaGetLastError();

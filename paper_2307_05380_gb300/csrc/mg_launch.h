@@ -102,6 +102,8 @@ struct BuildArgs {
     int inclusive = 0;                 // 1: edge iff d2 <= rr (Alg. 2's filter)
     double *knn_dk = nullptr;          // KNN: write the k-th canonical d2 per atom, no edges
     int write_pairs = 0;               // 1: record the pair table (symmetric cutoff graphs)
+    int pdl = 0;                       // host: launch the first build kernel with programmatic
+                                       // stream serialization (it directly follows prep)
 };
 
 // One-pass cutoff build (batched): scan once, stage keys, look-back offsets, write.
