@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(256) cutoff_count_kernel(BuildArgs a, Work w) 
         const double rr = R.rr;
         int count = 0;
         const Cells cells{w.cell_start, w.cell_fx, w.cell_p};
-        for_each_candidate(S, a.frac, w.pos, cells, true, R.cut, [&](bool vc, float d2, bool self, int ow, int t2,
+        for_each_candidate(S, a.frac, w.pos, cells, true, R.cut, nullptr, [&](bool vc, float d2, bool self, int ow, int t2,
                                                                       const RowRegs &rw) {
             const bool cand = vc && !self;
             bool in = cand && d2 < thr_lo;
@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(WRITE_WARPS * 32) cutoff_write_kernel(BuildArg
         if (S.nb[0] != 0 && deg <= WRITE_CAP) {
             int m = 0;
             bool range_bad = false;
-            for_each_candidate(S, a.frac, w.pos, cells, true, R.cut, [&](bool vc, float d2, bool self, int ow,
+            for_each_candidate(S, a.frac, w.pos, cells, true, R.cut, nullptr, [&](bool vc, float d2, bool self, int ow,
                                                                           int t2, const RowRegs &rw) {
                 const bool cand = vc && !self;
                 bool in = cand && d2 < thr_lo;
@@ -626,7 +626,7 @@ __global__ void __launch_bounds__(WRITE_WARPS * 32) cutoff_write_kernel(BuildArg
         }
         if (done) continue;
         int64_t out = base;
-        for_each_candidate(S, a.frac, w.pos, cells, false, R.cut, [&](bool vc, float d2, bool self, int ow,
+        for_each_candidate(S, a.frac, w.pos, cells, false, R.cut, nullptr, [&](bool vc, float d2, bool self, int ow,
                                                                        int t2, const RowRegs &rw) {
             const bool cand = vc && !self;
             bool in = cand && d2 < thr_lo;
@@ -767,7 +767,7 @@ __device__ __forceinline__ bool source_setup(const BuildArgs &a, const Work &w, 
 // count; `spill` when the keys did not fit or an offset exceeds the packed key.
 template <bool PERSRC>
 __device__ __forceinline__ int scan_source(const BuildArgs &a, const Work &w, const SrcScan &c,
-                                           unsigned long long *keys, bool &spill) {
+                                           unsigned long long *keys, unsigned char *trim, bool &spill) {
     const Source &S = c.S;
     const Cells cells{w.cell_start, w.cell_fx, w.cell_p};
     const unsigned lt = (1u << lane_id()) - 1u;
@@ -777,7 +777,7 @@ __device__ __forceinline__ int scan_source(const BuildArgs &a, const Work &w, co
     int m = 0;
     bool range_bad = false;
     unsigned long long nre = 0, ncand = 0;
-    for_each_candidate(S, a.frac, w.pos, cells, true, c.cut, [&](bool vc, float d2, bool self, int ow, int t2,
+    for_each_candidate(S, a.frac, w.pos, cells, true, c.cut, trim, [&](bool vc, float d2, bool self, int ow, int t2,
                                                                   const RowRegs &rw) {
         const bool cand = vc && !self;
         bool in = cand && d2 < thr_lo;
@@ -824,7 +824,7 @@ __device__ __forceinline__ int scan_source(const BuildArgs &a, const Work &w, co
 // a spilled source is enumerated again in canonical all-pairs order.
 template <bool PERSRC>
 __device__ __forceinline__ void emit_source(const BuildArgs &a, const Work &w, const SrcScan &c, int i, int64_t base,
-                                            int m, const unsigned long long *keys, bool spill) {
+                                            int m, const unsigned long long *keys, unsigned char *trim, bool spill) {
     const Source &S = c.S;
     const mg_graph_t &g = a.g;
     const int lane = lane_id();
@@ -866,7 +866,7 @@ __device__ __forceinline__ void emit_source(const BuildArgs &a, const Work &w, c
     const double rr = c.rr;
     int64_t out = base;
     const int64_t endp = base + m;
-    for_each_candidate(S, a.frac, w.pos, cells, false, c.cut,
+    for_each_candidate(S, a.frac, w.pos, cells, false, c.cut, trim,
                        [&](bool vc, float d2, bool self, int ow, int t2, const RowRegs &rw) {
         const bool cand = vc && !self;
         bool in = cand && d2 < thr_lo;
@@ -912,11 +912,13 @@ __device__ __forceinline__ void emit_source(const BuildArgs &a, const Work &w, c
 template <bool PERSRC>
 __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_build_kernel(BuildArgs a, Work w) {
     __shared__ unsigned long long keys_all[BUILD_WARPS][BUILD_CAP];
+    __shared__ __align__(4) unsigned char trim_all[BUILD_WARPS][32 * TRIM_STRIDE];  // row-trimming tables
     __shared__ int s_tile;
     __shared__ int s_cnt[BUILD_WARPS];
     __shared__ long long s_prefix;
     const int wid = threadIdx.x >> 5, lane = lane_id();
     unsigned long long *keys = keys_all[wid];
+    unsigned char *trim = trim_all[wid];
     const mg_graph_t g = a.g;
     unsigned long long *flags = w.tile_flags;
     const int ntiles = gridDim.x;
@@ -934,7 +936,7 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_build_kernel(Build
     bool usable = false;
     if (have) {
         usable = source_setup<PERSRC>(a, w, i, c);
-        if (usable) m = scan_source<PERSRC>(a, w, c, keys, spill);
+        if (usable) m = scan_source<PERSRC>(a, w, c, keys, trim, spill);
     }
     if (lane == 0) s_cnt[wid] = m;
     __syncthreads();
@@ -974,7 +976,7 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_build_kernel(Build
         for (int q = s; q >= 0 && a.atom_ptr[q] == i; --q) g.edge_ptr[q] = base;  // structures starting at i
     }
     if (m == 0 || base + m > g.capacity) return;  // nothing to write, or the capacity error
-    emit_source<PERSRC>(a, w, c, i, base, m, keys, spill);
+    emit_source<PERSRC>(a, w, c, i, base, m, keys, trim, spill);
 }
 
 // Decoupled build, part 1 (no dependence between sources): each warp scans a source and
@@ -991,7 +993,7 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_stage_kernel(Build
     SrcScan c;
     int m = 0;
     bool spill = false;
-    if (source_setup<PERSRC>(a, w, i, c)) m = scan_source<PERSRC>(a, w, c, keys, spill);
+    if (source_setup<PERSRC>(a, w, i, c)) m = scan_source<PERSRC>(a, w, c, keys, nullptr, spill);
     long long off = -1;
     if (!spill && m > 0) {
         if (lane == 0) off = (long long)atomicAdd(w.stage_ctr, (unsigned long long)m);
@@ -1089,7 +1091,7 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_spill_kernel(Build
     if (m == 0) return;
     SrcScan c;
     if (!source_setup<PERSRC>(a, w, i, c)) return;
-    emit_source<PERSRC>(a, w, c, i, base, m, nullptr, true);
+    emit_source<PERSRC>(a, w, c, i, base, m, nullptr, nullptr, true);
 }
 
 cudaError_t launch_cutoff_build(const BuildArgs &a, const Work &w, cudaStream_t s) {

@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 6) knn_kernel(BuildArgs a, Wor
                     thr = tk.kth(k).v;
                 }
             };
-            for_each_candidate(Src, a.frac, w.pos, cells, true, rho, [&](bool vc, float d2, bool self, int ow,
+            for_each_candidate(Src, a.frac, w.pos, cells, true, rho, nullptr, [&](bool vc, float d2, bool self, int ow,
                                                                           int t2, const RowRegs &rw) {
                 const bool c = vc && !self && d2 < rho2;
                 found += __popc(__ballot_sync(FULL, c));
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 6) knn_kernel(BuildArgs a, Wor
             // left (FP64 only in that case)
             int m = 0, nb = 0;
             bool range_bad = false;
-            for_each_candidate(Src, a.frac, w.pos, cells, true, rho, [&](bool vc, float d2, bool self, int ow, int t2,
+            for_each_candidate(Src, a.frac, w.pos, cells, true, rho, nullptr, [&](bool vc, float d2, bool self, int ow, int t2,
                                                                           const RowRegs &rw) {
                 const bool c = vc && !self;
                 const bool in = c && d2 < lo_thr;
@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 6) knn_kernel(BuildArgs a, Wor
                     }
                 } else {  // the band did not fit in shared memory: stream it again with FP64 keys
                     XKey ethr = kinf(XKey{});
-                    for_each_candidate(Src, a.frac, w.pos, cells, true, rho, [&](bool vc, float d2, bool self, int ow,
+                    for_each_candidate(Src, a.frac, w.pos, cells, true, rho, nullptr, [&](bool vc, float d2, bool self, int ow,
                                                                                   int t2, const RowRegs &rw) {
                         const bool c = vc && !self;
                         const bool band = c && d2 >= lo_thr && d2 <= hi_thr;

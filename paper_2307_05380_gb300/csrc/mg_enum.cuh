@@ -74,6 +74,43 @@ struct RowRegs {
     int t0, t1;
 };
 
+// Row trimming: the (t0, t1) rows of a target's box are the lattice points of a
+// parallelogram around the ellipse in which the sphere projects along L_2; a row holds
+// candidates only if its line b + t2 L_2 passes within the radius.  With u, w the parts
+// of L_0, L_1 orthogonal to L_2 and c that of the target offset, row (t0, t1) qualifies
+// iff |c + t0 u + t1 w| < rho: for each t0 an interval of t1, found in closed form.
+// Each target lane keeps, in a per-warp shared-memory area, the inclusive prefix of its
+// rows per t0 (bytes) and each interval's first t1 (offset from the box, 4 bits), for
+// boxes of at most TRIM_T0 x TRIM_T1 rows; larger boxes keep all their rows.  Pays where
+// a warp's scan is a latency chain (the one-pass build); where the scan is issue-bound
+// (the staged build, KNN) the table costs more instructions than the rows it saves.
+constexpr int TRIM_T0 = 12, TRIM_T1 = 15;
+constexpr int TRIM_STRIDE = 20;  // bytes per lane: 12 prefixes, 6 bytes of start nibbles (5 words: no bank conflicts)
+struct Trim {
+    float u[3], w[3];  // L_0 and L_1 minus their components along L_2
+    float inv_ww;      // 1 / |w|^2
+    float mu;          // widening of each t1 interval (t1 units)
+    bool ok;           // usable (w not degenerate)
+};
+
+__device__ __forceinline__ Trim make_trim(const Source &S, float rho) {
+    Trim T;
+    const float *L = S.L;
+    const float d0 = (L[0] * L[6] + L[1] * L[7] + L[2] * L[8]) * S.inv_L2n2;
+    const float d1 = (L[3] * L[6] + L[4] * L[7] + L[5] * L[8]) * S.inv_L2n2;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        T.u[k] = __fmaf_rn(-d0, L[6 + k], L[k]);
+        T.w[k] = __fmaf_rn(-d1, L[6 + k], L[3 + k]);
+    }
+    const float ww = T.w[0] * T.w[0] + T.w[1] * T.w[1] + T.w[2] * T.w[2];
+    const float l1 = L[3] * L[3] + L[4] * L[4] + L[5] * L[5];
+    T.ok = ww > 1e-6f * l1 && isfinite(ww);
+    T.inv_ww = T.ok ? 1.0f / ww : 0.f;
+    T.mu = T.ok ? 1e-3f * (1.0f + rho * sqrtf(T.inv_ww)) : 0.f;
+    return T;
+}
+
 // Wrapped fractional coordinate in [0, 1).
 __device__ __forceinline__ float wrap01(float x) {
     float w = __fsub_rn(x, floorf(x));
@@ -92,7 +129,7 @@ __device__ __forceinline__ int bin_of(float w, int n) {
 template <class Visit>
 __device__ __forceinline__ void visit_targets(const Source &S, const float Rk[3], float rho2p, float rho1, float mu0,
                                               bool single, int jl, bool vj, float4 xj, float4 pj,
-                                              Visit &visit) {
+                                              const Trim &T, unsigned char *trim, Visit &visit) {
     const int lane = lane_id();
     int lo[3], nn[3];
     float3 a = make_float3(0.f, 0.f, 0.f);
@@ -132,7 +169,54 @@ __device__ __forceinline__ void visit_targets(const Source &S, const float Rk[3]
         visit(has, d2, self, lane, lo[2], rr);
         return;
     }
-    const int rows = (nn[2] > 0) ? nn[0] * nn[1] : 0;
+    int rows = (nn[2] > 0) ? nn[0] * nn[1] : 0;
+    int trimmed = 0;
+    if (trim) {
+        __syncwarp();  // every lane is done with the previous targets' tables
+        unsigned char *mine = trim + TRIM_STRIDE * lane;
+        if (T.ok && rows > 0 && nn[0] <= TRIM_T0 && nn[1] <= TRIM_T1) {
+            // c = the target offset minus its component along L_2
+            const float al = (a.x * S.L[6] + a.y * S.L[7] + a.z * S.L[8]) * S.inv_L2n2;
+            const float c0 = __fmaf_rn(-al, S.L[6], a.x), c1 = __fmaf_rn(-al, S.L[7], a.y),
+                        c2 = __fmaf_rn(-al, S.L[8], a.z);
+            int pre = 0;
+            for (int r = 0; r < nn[0]; ++r) {
+                const float ft0 = (float)(lo[0] + r);
+                const float q0 = __fmaf_rn(ft0, T.u[0], c0), q1 = __fmaf_rn(ft0, T.u[1], c1),
+                            q2 = __fmaf_rn(ft0, T.u[2], c2);
+                // closest point of the line q + t1 w to the source: perpendicular p = q + m w
+                const float m = -(q0 * T.w[0] + q1 * T.w[1] + q2 * T.w[2]) * T.inv_ww;
+                const float p0 = __fmaf_rn(m, T.w[0], q0), p1 = __fmaf_rn(m, T.w[1], q1),
+                            p2 = __fmaf_rn(m, T.w[2], q2);
+                const float perp2 = __fmaf_rn(p2, p2, __fmaf_rn(p1, p1, __fmul_rn(p0, p0)));
+                const float q2n = __fmaf_rn(q2, q2, __fmaf_rn(q1, q1, __fmul_rn(q0, q0)));
+                int s1 = 0, cnt = nn[1];
+                // the same error analysis as the chord below: FP32 errors stay far inside the
+                // radius margin and mu while |q| and |m w| are at most 50 rho
+                if (q2n <= 2500.0f * rho2p && fabsf(m) * fabsf(m) <= 2500.0f * rho2p * T.inv_ww) {
+                    const float hsq = (rho2p - perp2) * T.inv_ww;
+                    if (hsq < 0.0f) {
+                        cnt = 0;
+                    } else {
+                        const float h = hsq > 0.0f ? hsq * rsqrtf(hsq) : 0.0f;
+                        const float mu = T.mu + 6e-7f * fabsf(m);
+                        const int l1 = max(lo[1], (int)ceilf(m - h - mu));
+                        const int h1 = min(lo[1] + nn[1] - 1, (int)floorf(m + h + mu));
+                        cnt = max(0, h1 - l1 + 1);
+                        s1 = cnt > 0 ? l1 - lo[1] : 0;
+                    }
+                }
+                pre += cnt;
+                mine[r] = (unsigned char)pre;
+                if (r & 1) mine[TRIM_T0 + (r >> 1)] |= (unsigned char)(s1 << 4);
+                else mine[TRIM_T0 + (r >> 1)] = (unsigned char)s1;
+            }
+            for (int r = nn[0]; r < TRIM_T0; ++r) mine[r] = 0xff;  // keeps the prefixes monotone
+            rows = pre;
+            trimmed = 1;
+        }
+        __syncwarp();  // tables visible to the row lanes
+    }
     const int incl = warp_incl_scan(rows);
     const int total = __shfl_sync(FULL, incl, 31);
     const int excl = incl - rows;
@@ -153,13 +237,28 @@ __device__ __forceinline__ void visit_targets(const Source &S, const float Rk[3]
         RowRegs rr;
         rr.j = __shfl_sync(FULL, jl, ow);
         const int rem = vr ? q - o_excl : 0;
-        // rem / n1 from an approximate quotient, corrected to the exact integer one
-        const int n1 = max(o_n1, 1);
-        int d0 = (int)__fdividef((float)rem, (float)n1);
-        while (d0 * n1 > rem) --d0;
-        while ((d0 + 1) * n1 <= rem) ++d0;
-        rr.t0 = o_lo0 + d0;
-        rr.t1 = o_lo1 + (rem - d0 * o_n1);
+        if (__shfl_sync(FULL, trimmed, ow)) {
+            // the owner's trimmed rows: the t0 whose prefix first exceeds rem, then t1
+            const unsigned char *tab = trim + TRIM_STRIDE * ow;
+            int r = 0;
+#pragma unroll
+            for (int st = 8; st >= 1; st >>= 1) {
+                const int idx = r + st - 1;  // entries past the table count as full
+                if ((idx < TRIM_T0 ? (int)tab[idx] : 0xff) <= rem) r += st;
+            }
+            const int before = r > 0 ? (int)tab[r - 1] : 0;
+            const int nib = (int)tab[TRIM_T0 + (r >> 1)];
+            rr.t0 = o_lo0 + r;
+            rr.t1 = o_lo1 + ((r & 1) ? (nib >> 4) : (nib & 15)) + (rem - before);
+        } else {
+            // rem / n1 from an approximate quotient, corrected to the exact integer one
+            const int n1 = max(o_n1, 1);
+            int d0 = (int)__fdividef((float)rem, (float)n1);
+            while (d0 * n1 > rem) --d0;
+            while ((d0 + 1) * n1 <= rem) ++d0;
+            rr.t0 = o_lo0 + d0;
+            rr.t1 = o_lo1 + (rem - d0 * o_n1);
+        }
         // row base b = a + t0 L0 + t1 L1
         const float ft0 = (float)rr.t0, ft1 = (float)rr.t1;
         const float bx = __fmaf_rn(ft1, S.L[3], __fmaf_rn(ft0, S.L[0], ax));
@@ -227,8 +326,9 @@ __device__ __forceinline__ void visit_targets(const Source &S, const float Rk[3]
 template <class Visit>
 __device__ __forceinline__ void for_each_candidate(const Source &S, const float *__restrict__ frac,
                                                    const float4 *__restrict__ pos, const Cells &cells,
-                                                   bool use_cells, float rho, Visit &&visit) {
+                                                   bool use_cells, float rho, unsigned char *trim, Visit &&visit) {
     const int lane = lane_id();
+    const Trim T = make_trim(S, rho);
     float Rk[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) Rk[k] = rho * S.invd[k];
@@ -247,7 +347,7 @@ __device__ __forceinline__ void for_each_candidate(const Source &S, const float 
                 xj = make_float4(frac[3 * row + 0], frac[3 * row + 1], frac[3 * row + 2], 0.f);
                 pj = pos[row];
             }
-            visit_targets(S, Rk, rho2p, rho1, mu0, single, jl, vj, xj, pj, visit);
+            visit_targets(S, Rk, rho2p, rho1, mu0, single, jl, vj, xj, pj, T, trim, visit);
         }
         return;
     }
@@ -301,7 +401,7 @@ __device__ __forceinline__ void for_each_candidate(const Source &S, const float 
                 xj = cells.fx[ost + (q2 - oex)];
                 pj = cells.p[ost + (q2 - oex)];
             }
-            visit_targets(S, Rk, rho2p, rho1, mu0, single, va ? __float_as_int(xj.w) : 0, va, xj, pj, visit);
+            visit_targets(S, Rk, rho2p, rho1, mu0, single, va ? __float_as_int(xj.w) : 0, va, xj, pj, T, trim, visit);
         }
     }
 }
