@@ -341,8 +341,10 @@ def run_mine(args, rank, world, local_rank):
     # e2e: the step's library calls (both graph updates, forward, backward with the loss
     # gradient) from pinned host inputs to pinned host outputs.  Every step copies the
     # inputs in and every output back: both graphs' edges, status words, vectors and
-    # gradients.  Each graph's copies start as soon as it is final, so they overlap the
-    # rest of the step; the host waits once, at the end, then checks both status words.
+    # gradients.  Each graph's copy (one library call per graph) is issued right behind
+    # its build, on another stream, so the copies overlap the rest of the step; the step's
+    # outputs follow the backward.  The host waits once, at the end, then checks both
+    # status words.
     frac_h = torch.from_numpy(b.frac).pin_memory()
     lat_h = torch.from_numpy(b.lattice).pin_memory()
     ptr_h = torch.from_numpy(b.atom_ptr).pin_memory()
@@ -350,51 +352,42 @@ def run_mine(args, rank, world, local_rank):
     e2e_steps = max(5, min(args.steps, 50))
     copy_stream = torch.cuda.Stream(dev)
     ev_in, ev_cut = torch.cuda.Event(), torch.cuda.Event()
-    host_out = {}
-
-    def to_host(q, t):
-        if q not in host_out:
-            host_out[q] = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
-        host_out[q].copy_(t, non_blocking=True)
-        return t.numel() * t.element_size()
+    host_knn = mg.host_buffers(g_knn, E_knn, ("status", "src", "dst", "offset", "vec", "len"))
+    host_cut = mg.host_buffers(g_cut, E_cut, ("status", "src", "dst", "offset"))
+    step_out = (out_vec[:E_cut], out_len[:E_cut], grad_frac, grad_lat)
+    host_step = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in step_out]
+    d2h = sum(t.numel() * t.element_size() for t in list(host_knn.values()) + list(host_cut.values()) + host_step)
 
     def e2e_step():
         batch.frac.copy_(frac_h, non_blocking=True)
         batch.lattice.copy_(lat_h, non_blocking=True)
         batch.atom_ptr.copy_(ptr_h, non_blocking=True)
         ev_in.record(main_stream)
-        knn_stream.wait_event(ev_in)
-        d2h = 0
-        torch.cuda.set_stream(knn_stream)
-        mg.update_graph(g_knn, sync=False)
-        for q, t in enumerate((g_knn.status, g_knn.src[:E_knn], g_knn.dst[:E_knn], g_knn.offset[:E_knn],
-                               g_knn.vec[:E_knn], g_knn.len[:E_knn])):
-            d2h += to_host(("knn", q), t)
-        ev_join.record(knn_stream)
-        torch.cuda.set_stream(main_stream)
-        mg.update_graph(g_cut, sync=False)
+        mg.update_graph(g_cut, sync=False)  # the larger graph first: its copy starts earliest
         ev_cut.record(main_stream)
         copy_stream.wait_event(ev_cut)
-        torch.cuda.set_stream(copy_stream)
-        for q, t in enumerate((g_cut.status, g_cut.src[:E_cut], g_cut.dst[:E_cut], g_cut.offset[:E_cut])):
-            d2h += to_host(("cut", q), t)
+        torch.cuda.set_stream(copy_stream)  # behind the cutoff build, beside the rest
+        mg.graph_to_host(g_cut, host_cut, E_cut)
+        knn_stream.wait_event(ev_in)
+        torch.cuda.set_stream(knn_stream)
+        mg.update_graph(g_knn, sync=False)
+        mg.graph_to_host(g_knn, host_knn, E_knn)  # behind the KNN build
         torch.cuda.set_stream(main_stream)
         mg.edge_vectors_fwd(g_cut, out_vec=out_vec, out_len=out_len)
         mg.edge_vectors_bwd(g_cut, batch, None, w_dev, out_vec, out_len, grad_frac, grad_lat)
-        for q, t in enumerate((out_vec[:E_cut], out_len[:E_cut], grad_frac, grad_lat)):
-            d2h += to_host(("step", q), t)
+        for h, t in zip(host_step, step_out):  # behind the backward
+            h.copy_(t, non_blocking=True)
         torch.cuda.synchronize(dev)
-        for key, E in ((("cut", 0), E_cut), (("knn", 0), E_knn)):  # code 0, same edge count as the first build
-            st_h = host_out[key]
+        for st_h, E in ((host_cut["status"], E_cut), (host_knn["status"], E_knn)):  # code 0, same edge count
             assert int(st_h[0]) & 0xFFFFFFFF == 0 and int(st_h[1]) == E, st_h
         return E_cut + E_knn, d2h
 
     e2e_step()
-    e2e_t, e2e_units, d2h = 0.0, 0, 0
+    e2e_t, e2e_units = 0.0, 0
     for _ in range(e2e_steps):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        u_, d2h = e2e_step()
+        u_, _ = e2e_step()
         e2e_t += time.perf_counter() - t0
         e2e_units += u_
     mg.profile_enable(True, dev)

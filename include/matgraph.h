@@ -250,13 +250,39 @@ mg_status_t mg_autotune(mg_context_t ctx, const mg_batch_t *batch, int32_t kind,
                         int32_t k, mg_graph_t *graph, void *workspace, size_t workspace_bytes,
                         void *stream);
 
+/* Host buffers for mg_graph_to_host, all owned by the caller; any may be NULL (not
+ * copied).  Page-locked (pinned) memory lets the copies run asynchronously. */
+typedef struct {
+    mg_device_status_t *status; /* one status word */
+    int32_t *src;               /* [num_edges] */
+    int32_t *dst;               /* [num_edges] */
+    int32_t *offset;            /* [num_edges][3] */
+    float *vec;                 /* [num_edges][3]; needs graph->vec */
+    float *len;                 /* [num_edges]; needs graph->len */
+    int64_t *edge_ptr;          /* [B+1] */
+    int64_t *src_ptr;           /* [N+1]; needs graph->src_ptr */
+} mg_graph_host_t;
+
+/* Copy a built graph to host memory (data movement only, no counterpart in the paper):
+ * the first num_edges rows of src, dst, offset, vec and len, the pointer arrays and the
+ * status word, for every non-NULL field of `out`, as one cudaMemcpyAsync each on
+ * `stream` (asynchronous: synchronise the stream before reading).  num_edges is a host
+ * value, e.g. from an earlier status read; rows past the edge count the device holds
+ * are undefined.  MG_ERR_INVALID_ARGUMENT for num_edges outside [0, capacity], or a
+ * requested field whose device array the graph does not have; MG_ERR_CUDA if a copy
+ * cannot be issued. */
+mg_status_t mg_graph_to_host(mg_context_t ctx, const mg_batch_t *batch, const mg_graph_t *graph,
+                             int64_t num_edges, const mg_graph_host_t *out, void *stream);
+
 /* Number of kernel launches the last build/fwd/bwd call on this context issued
  * (graph replays count their kernel nodes). */
 int64_t mg_last_launch_count(mg_context_t ctx);
 
 /* Measurement support (not needed for results).  When on, the batched builds and the
  * edge-vector calls of this context record CUDA events on the caller's stream between
- * their kernel stages; plans captured while on contain the event records too.
+ * their kernel stages.  A plan is recorded again at its next replay when the switch has
+ * changed since it was recorded: with the event records when on, without them (and
+ * with kernels launched behind their predecessors) when off.
  * mg_stage_times waits for the events of the last call of kind `which`
  * (MG_PROF_CUTOFF, MG_PROF_KNN, MG_PROF_FWD, MG_PROF_BWD), then writes up to max_stages
  * stage names (static strings) and durations in milliseconds.  Returns the number of

@@ -39,6 +39,11 @@ class MgTriplets(ctypes.Structure):
                 ("status", c_void_p)]
 
 
+class MgGraphHost(ctypes.Structure):
+    _fields_ = [("status", c_void_p), ("src", c_void_p), ("dst", c_void_p), ("offset", c_void_p),
+                ("vec", c_void_p), ("len", c_void_p), ("edge_ptr", c_void_p), ("src_ptr", c_void_p)]
+
+
 class MgOpts(ctypes.Structure):
     _fields_ = [("band_rel", c_float), ("knn_keep_ties", c_int32), ("schedule", c_int32),
                 ("collect_stats", c_int32), ("fault_tile", c_int32)]
@@ -75,6 +80,8 @@ SIGNATURES = [
                               ctypes.POINTER(MgTriplets), c_void_p, c_size_t, c_void_p]),
     ("mg_symmetrize", c_int32, [c_void_p, ctypes.POINTER(MgBatch), ctypes.POINTER(MgGraph),
                                 ctypes.POINTER(MgGraph), c_void_p, c_size_t, c_void_p]),
+    ("mg_graph_to_host", c_int32, [c_void_p, ctypes.POINTER(MgBatch), ctypes.POINTER(MgGraph), c_int64,
+                                   ctypes.POINTER(MgGraphHost), c_void_p]),
     ("mg_profile_enable", c_int32, [c_void_p, c_int32]),
     ("mg_stage_times", c_int32, [c_void_p, c_int32, c_int32, ctypes.POINTER(ctypes.c_char_p),
                                  ctypes.POINTER(c_float)]),

@@ -839,6 +839,39 @@ mg_status_t mg_edge_vectors_bwd(mg_context_t ctx, const mg_batch_t *b, const mg_
     return MG_OK;
 }
 
+mg_status_t mg_graph_to_host(mg_context_t ctx, const mg_batch_t *b, const mg_graph_t *g, int64_t num_edges,
+                             const mg_graph_host_t *out, void *stream) {
+    if (!ctx || !out) return MG_ERR_INVALID_ARGUMENT;
+    mg_status_t r = check_batch(b);
+    if (r) return r;
+    if (!g || num_edges < 0 || num_edges > g->capacity) return MG_ERR_INVALID_ARGUMENT;
+    if ((out->status && !g->status) || (out->src && !g->src) || (out->dst && !g->dst) ||
+        (out->offset && !g->offset) || (out->vec && !g->vec) || (out->len && !g->len) ||
+        (out->edge_ptr && !g->edge_ptr) || (out->src_ptr && !g->src_ptr))
+        return MG_ERR_INVALID_ARGUMENT;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t E = (size_t)num_edges;
+    struct Copy {
+        void *dst;
+        const void *src;
+        size_t bytes;
+    };
+    const Copy copies[] = {
+        {out->status, g->status, sizeof(mg_device_status_t)},
+        {out->src, g->src, E * sizeof(int32_t)},
+        {out->dst, g->dst, E * sizeof(int32_t)},
+        {out->offset, g->offset, 3 * E * sizeof(int32_t)},
+        {out->vec, g->vec, 3 * E * sizeof(float)},
+        {out->len, g->len, E * sizeof(float)},
+        {out->edge_ptr, g->edge_ptr, ((size_t)b->num_structures + 1) * sizeof(int64_t)},
+        {out->src_ptr, g->src_ptr, ((size_t)b->total_atoms + 1) * sizeof(int64_t)},
+    };
+    for (const Copy &c : copies)
+        if (c.dst && c.bytes && cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return MG_ERR_CUDA;
+    return MG_OK;
+}
+
 mg_status_t mg_triplets(mg_context_t ctx, const mg_batch_t *b, const mg_graph_t *g, int32_t include_self,
                         mg_triplets_t *out, void *ws, size_t ws_bytes, void *stream) {
     if (!ctx || !out || !out->status || !out->edge_b || out->capacity < 0 || (include_self != 0 && include_self != 1))

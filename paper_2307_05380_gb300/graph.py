@@ -398,6 +398,33 @@ def symmetrize(g: Graph, *, with_vectors: bool = True, with_perm: bool = True,
     raise RuntimeError("mg_symmetrize: capacity retry failed")
 
 
+# ---------------------------------------------------------------------------- host copies
+
+HOST_FIELDS = ("status", "src", "dst", "offset", "vec", "len", "edge_ptr", "src_ptr")
+
+
+def host_buffers(g: Graph, num_edges: int, fields=HOST_FIELDS) -> dict:
+    """Pinned host tensors for graph_to_host: the first num_edges rows of each field."""
+    E = int(num_edges)
+    shapes = {"status": ((5,), torch.int64), "src": ((E,), torch.int32), "dst": ((E,), torch.int32),
+              "offset": ((E, 3), torch.int32), "vec": ((E, 3), torch.float32), "len": ((E,), torch.float32),
+              "edge_ptr": ((g.batch.B + 1,), torch.int64), "src_ptr": ((g.batch.N + 1,), torch.int64)}
+    return {f: torch.empty(shapes[f][0], dtype=shapes[f][1], pin_memory=True) for f in fields}
+
+
+def graph_to_host(g: Graph, out: dict, num_edges: Optional[int] = None) -> dict:
+    """Copy the graph's first num_edges rows (default: its last read edge count), pointers
+    and status word into the host tensors of `out` (from host_buffers; any subset of the
+    fields), asynchronously on the current stream: one library call for all of them."""
+    E = g.num_edges if num_edges is None else int(num_edges)
+    h = _capi.MgGraphHost(*[_ptr(out.get(f)) for f in HOST_FIELDS])
+    dev = g.batch.device
+    rc = _capi.load().mg_graph_to_host(context(dev), ctypes.byref(g.batch.c), ctypes.byref(g.c), E,
+                                       ctypes.byref(h), _stream(dev))
+    _capi.check(rc, "mg_graph_to_host")
+    return out
+
+
 # ---------------------------------------------------------------------------- edge vectors
 
 def edge_vectors_fwd(g: Graph, batch: Optional[Batch] = None, out_vec=None, out_len=None):

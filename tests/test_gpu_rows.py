@@ -455,3 +455,47 @@ def test_staged_build_replay_and_device_errors():
     assert st["code"] == 3 and st["first_bad_structure"] == 1
     want = oracle.cutoff(bad.lattice[:1], bad.frac[:bad.atom_ptr[1]], bad.atom_ptr[:2], 5.0)
     assert int(gb.edge_ptr[1].item()) == len(want["src"])
+
+
+# ------------------------------------------------------------------ host copies
+
+def test_graph_to_host_matches_device_arrays():
+    """mg_graph_to_host copies the first num_edges rows, the pointers and the status word
+    of each requested field (pinned buffers, asynchronous on the current stream)."""
+    b = synth.make_batch(2, B=48)
+    batch = to_device(b)
+    for g in (mg.cutoff_graph(batch, 6.0, with_perm=False), mg.knn_graph(batch, 12, with_perm=False)):
+        E = g.num_edges
+        out = mg.host_buffers(g, E)
+        mg.graph_to_host(g, out, E)
+        torch.cuda.current_stream().synchronize()
+        assert torch.equal(out["status"], g.status.cpu())
+        for f in ("src", "dst", "offset", "vec", "len"):
+            assert torch.equal(out[f], getattr(g, f)[:E].cpu()), f
+        assert torch.equal(out["edge_ptr"], g.edge_ptr.cpu()) and torch.equal(out["src_ptr"], g.src_ptr.cpu())
+        part = mg.host_buffers(g, 10, ("src", "len"))  # a subset, fewer rows
+        mg.graph_to_host(g, part, 10)
+        torch.cuda.current_stream().synchronize()
+        assert torch.equal(part["src"], g.src[:10].cpu()) and torch.equal(part["len"], g.len[:10].cpu())
+    with pytest.raises(RuntimeError, match="INVALID_ARGUMENT"):
+        mg.graph_to_host(g, part, g.capacity + 1)
+
+
+def test_plans_recorded_again_when_profiling_changes():
+    """A plan recorded without stage events is recorded again with them once profiling is
+    on (and the stage times appear), and again without them when it is off; the edges
+    stay identical."""
+    b = synth.make_batch(2, B=32)
+    batch = to_device(b)
+    mg.profile_enable(False)
+    g = mg.cutoff_graph(batch, 6.0, with_perm=False)
+    mg.update_graph(g)
+    want = graph_arrays(g)
+    mg.profile_enable(True)
+    mg.update_graph(g)
+    stages = mg.stage_times("cutoff")
+    assert "build" in stages and all(v >= 0 for v in stages.values()), stages
+    assert_same_edges(graph_arrays(g), want, "profiled replay")
+    mg.profile_enable(False)
+    mg.update_graph(g)
+    assert_same_edges(graph_arrays(g), want, "replay without events")
