@@ -72,6 +72,10 @@ def parse_args():
     p.add_argument("--sweep", action="store_true", help="batch-size sweep of the KNN k=32 build")
     p.add_argument("--rows", action="store_true",
                    help="per-atom cutoff, keep-ties KNN, symmetric closure and triplets on --config")
+    p.add_argument("--runs", action="store_true",
+                   help="cutoff r = 4, 6, 8 and KNN k = 8, 16, 32 on --config, batched vs per structure")
+    p.add_argument("--md", action="store_true",
+                   help="the 20-step perturbation loop of the 1024-structure workload")
     return p.parse_args()
 
 
@@ -236,6 +240,63 @@ def cpu_baseline_leg(args, b, wl, budget_s=12.0):
                       f"({dt:.1f} s, single thread)"}
 
 
+def cpu_info():
+    """nproc and the CPU model of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return os.cpu_count(), model
+
+
+def _oracle_worker(payload):
+    """One spawned process: passes of the oracle's step (cutoff + KNN + edge vectors +
+    gradient) over its share of the structures for about budget_s seconds."""
+    lat, frac, ptr, cutoff, k, budget_s = payload
+    import oracle
+    edges = passes = 0
+    t0 = time.perf_counter()
+    while True:
+        g = oracle.cutoff(lat, frac, ptr, cutoff)
+        h = oracle.knn(lat, frac, ptr, k)
+        vec, ln = oracle.edge_vectors(lat, frac, ptr, g["src"], g["dst"], g["offset"])
+        oracle.edge_grad(lat, frac, ptr, g["src"], g["dst"], g["offset"], None, ln)
+        edges += len(g["src"]) + len(h["src"])
+        passes += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    return edges, passes, time.perf_counter() - t0
+
+
+def cpu_baseline_threaded(sub, wl, budget_s=12.0):
+    """The same oracle step threaded across structures: one spawned process per core, each
+    on a contiguous range of structures of about equal cost (atoms squared); the rate is
+    the sum of the processes' rates over their concurrent windows."""
+    import multiprocessing as mp
+
+    import numpy as np
+    ncores = os.cpu_count() or 1
+    counts = np.diff(sub.atom_ptr).astype(np.int64)
+    cost = np.cumsum(counts * counts)
+    cuts = [0] + [int(np.searchsorted(cost, cost[-1] * q / ncores, side="right")) for q in range(1, ncores)] \
+        + [sub.num_structures]
+    payloads = []
+    for lo, hi in zip(cuts[:-1], cuts[1:]):
+        if hi <= lo:
+            continue
+        a0, a1 = int(sub.atom_ptr[lo]), int(sub.atom_ptr[hi])
+        payloads.append((sub.lattice[lo:hi].copy(), sub.frac[a0:a1].copy(),
+                         (sub.atom_ptr[lo:hi + 1] - a0).astype(np.int32), wl["cutoff"], wl["k"], budget_s))
+    with mp.get_context("spawn").Pool(len(payloads)) as pool:
+        res = pool.map(_oracle_worker, payloads)
+    return sum(e / dt for e, _, dt in res), len(payloads)
+
+
 def run_mine(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -265,6 +326,11 @@ def run_mine(args, rank, world, local_rank):
     g_knn = mg.knn_graph(batch, wl["k"], with_perm=False)
     E_cut, E_knn = g_cut.num_edges, g_knn.num_edges
     units = E_cut + E_knn
+    # share of the FP32 candidates re-tested in FP64 (a counting build, outside every timed region)
+    st_stats = mg.cutoff_graph(batch, wl["cutoff"], with_perm=False, capacity=g_cut.capacity,
+                               opts=mg.make_opts(collect_stats=True)).read_status()
+    fp64_recheck = {"graph": "cutoff", "candidates": st_stats["candidates"], "rechecked": st_stats["rechecked"],
+                    "fraction": st_stats["rechecked"] / max(1, st_stats["candidates"])}
     grad_len = torch.from_numpy(synth.normal(17, 0, g_cut.capacity)).to(dev)
     out_vec = torch.empty(g_cut.capacity, 3, device=dev)
     out_len = torch.empty(g_cut.capacity, device=dev)
@@ -471,7 +537,15 @@ def run_mine(args, rank, world, local_rank):
         cpu = None
         if world == 1 and not args.no_baselines:
             cpu = cpu_baseline_leg(args, b, wl)
+            nproc, model = cpu_info()
+            sub = b if args.config in (1, 2, 4) else b.subset(range(32))
+            rate, procs = cpu_baseline_threaded(sub, wl)
+            cpu.update({"nproc": nproc, "cpu_model": model,
+                        "threaded": {"value": rate, "unit": UNIT, "cores": procs,
+                                     "note": "the same oracle step, one spawned process per core on "
+                                             "cost-balanced structure ranges"}})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "fp64_recheck": fp64_recheck,
                 "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": wl["name"], "structures": b.num_structures, "atoms": b.total_atoms,
@@ -632,6 +706,129 @@ def run_rows(args, local_rank):
     return 0
 
 
+def run_runs(args, local_rank):
+    """The radius and k runs of the --config workload (cutoff r = 4, 6, 8 A; KNN k = 8, 16,
+    32), one JSON line each: the batched build (plan replay, CUDA events, median; L2
+    flushed between builds) against the same kernels launched once per structure (mean of
+    three), with the HBM roofline of 36 B per edge written."""
+    import torch
+
+    import paper_2307_05380_gb300 as mg
+    import synth
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    hbm_peak, _, peak_src = measured_peaks()
+    wl = WORKLOADS[args.config]
+    b = synth.make_batch(args.config)
+    batch = mg.Batch(torch.from_numpy(b.frac).to(dev), torch.from_numpy(b.lattice).to(dev),
+                     torch.from_numpy(b.atom_ptr).to(dev), max_atoms=b.max_atoms)
+    ap_host = b.atom_ptr.tolist()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    steps = max(5, min(args.steps, 50))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, n):
+        ms = []
+        for _ in range(n):
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    runs = [("cutoff", r, 0) for r in (4.0, 6.0, 8.0)] + [("knn", 0.0, k) for k in (8, 16, 32)]
+    for kind, r, k in runs:
+        g = mg.cutoff_graph(batch, r, with_perm=False) if kind == "cutoff" else mg.knn_graph(batch, k, with_perm=False)
+        for _ in range(max(3, args.warmup)):
+            mg.update_graph(g, sync=False)
+        t = statistics.median(timed(lambda: mg.update_graph(g, sync=False), steps))
+        assert g.read_status()["code"] == 0
+        E = g.num_edges
+        ps = mg.cutoff_graph(batch, r, with_perm=False, capacity=E) if kind == "cutoff" \
+            else mg.knn_graph(batch, k, with_perm=False)
+        tp = statistics.mean(timed(lambda: mg.rebuild(ps, sync=False, per_structure=True, atom_ptr_host=ap_host),
+                                   3))
+        assert ps.read_status()["num_edges"] == E
+        gbs = 36.0 * E / t / 1e6
+        print(json.dumps({"run": f"{kind} {'r = %g A' % r if kind == 'cutoff' else 'k = %d' % k}",
+                          "workload": wl["name"], "edges": E, "ms": t, "edges_per_s": E / t * 1e3,
+                          "per_structure_ms": tp, "speedup_batched": tp / t,
+                          "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                                       "frac": gbs / hbm_peak, "peak_source": peak_src,
+                                       "work_per_unit": "36 B written per edge"}, "steps": steps}), flush=True)
+        del g, ps
+    return 0
+
+
+def run_md(args, local_rank):
+    """The perturbation loop of the 1024-structure workload: 20 steps of (seeded
+    perturbation x += N(0, 0.02), 1% strain) -> graph update (plan replay) -> edge vectors
+    -> backward of the Gaussian edge loss sum_e w_e exp(-len_e^2 / 2 sigma^2), sigma = 1.5.
+    Every step's coordinates are generated on the host beforehand and held on the device;
+    each step copies its own into the batch buffers.  The edge count of every step is
+    kept on the device and read once, after the timed loop; CUDA events around the 20
+    steps (a loop: no L2 flush inside)."""
+    import torch
+
+    import paper_2307_05380_gb300 as mg
+    import synth
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    cfg, nsteps, sigma = 4, 20, 1.5
+    wl = WORKLOADS[cfg]
+    traj = [synth.make_batch(cfg)]
+    for t in range(1, nsteps + 1):
+        traj.append(synth.perturb(traj[-1], seed=41, step=t))
+    fr_d = torch.stack([torch.from_numpy(x.frac) for x in traj[1:]]).to(dev)
+    la_d = torch.stack([torch.from_numpy(x.lattice) for x in traj[1:]]).to(dev)
+    b0 = traj[0]
+    batch = mg.Batch(torch.from_numpy(b0.frac).to(dev), torch.from_numpy(b0.lattice).to(dev),
+                     torch.from_numpy(b0.atom_ptr).to(dev), max_atoms=b0.max_atoms)
+    E0 = mg.cutoff_graph(batch, wl["cutoff"], with_perm=False).num_edges
+    g = mg.cutoff_graph(batch, wl["cutoff"], with_perm=False, capacity=int(1.3 * E0))
+    w = torch.from_numpy(synth.normal(43, 0, g.capacity)).to(dev)
+    out_vec = torch.empty(g.capacity, 3, device=dev)
+    out_len = torch.empty(g.capacity, device=dev)
+    grad_frac = torch.empty(batch.N, 3, device=dev)
+    grad_lat = torch.empty(batch.B, 3, 3, device=dev)
+    counts = torch.zeros(nsteps, 2, dtype=torch.int64, device=dev)
+
+    def loop():
+        for t in range(nsteps):
+            batch.frac.copy_(fr_d[t])
+            batch.lattice.copy_(la_d[t])
+            mg.update_graph(g, sync=False)
+            mg.edge_vectors_fwd(g, out_vec=out_vec, out_len=out_len)
+            gl = -w * out_len / (sigma * sigma) * torch.exp(-out_len * out_len / (2 * sigma * sigma))
+            mg.edge_vectors_bwd(g, batch, None, gl, out_vec, out_len, grad_frac, grad_lat)
+            counts[t].copy_(g.status[:2])
+
+    for _ in range(max(1, args.warmup // 3)):
+        loop()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    loop()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    c = counts.cpu()
+    assert all(int(x) & 0xFFFFFFFF == 0 for x in c[:, 0]), c
+    edges = int(c[:, 1].sum())
+    print(json.dumps({"md": "perturbation loop: update -> edge vectors -> Gaussian-loss backward",
+                      "workload": wl["name"], "steps": nsteps, "edges_per_step_mean": edges / nsteps,
+                      "edges_min_max": [int(c[:, 1].min()), int(c[:, 1].max())], "ms_per_step": ms / nsteps,
+                      "edges_per_s": edges / ms * 1e3, "timing": "CUDA events around the 20 steps"}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     rank, world, local_rank = dist_env()
@@ -641,6 +838,10 @@ def main():
         return run_sweep(args, local_rank) if rank == 0 else 0
     if args.rows:
         return run_rows(args, local_rank) if rank == 0 else 0
+    if args.runs:
+        return run_runs(args, local_rank) if rank == 0 else 0
+    if args.md:
+        return run_md(args, local_rank) if rank == 0 else 0
     return run_mine(args, rank, world, local_rank)
 
 
