@@ -12,6 +12,43 @@ def to_device(b, dev="cuda:0"):
                     torch.from_numpy(b.atom_ptr).to(dev), max_atoms=b.max_atoms)
 
 
+_POOL_BATCH = None
+
+
+def _pool_init(lattice, frac, atom_ptr):
+    global _POOL_BATCH
+    _POOL_BATCH = (lattice, frac, atom_ptr)
+
+
+def _oracle_range(task):
+    kind, param, lo, hi = task
+    lattice, frac, atom_ptr = _POOL_BATCH
+    src = np.arange(lo, hi, dtype=np.int32)
+    g = oracle.cutoff(lattice, frac, atom_ptr, param, sources=src) if kind == "cutoff" \
+        else oracle.knn(lattice, frac, atom_ptr, param, sources=src)
+    return g["src"], g["dst"], g["offset"]
+
+
+def oracle_all_sources(kind, b, param, workers=None):
+    """The oracle's graph over every source atom of batch b ('cutoff' with radius param,
+    'knn' with k = param), computed by spawned processes on contiguous source ranges of
+    about equal cost (a source costs the atoms of its structure) and joined in source
+    order: the same edges as one call, in a fraction of the time."""
+    import multiprocessing as mp
+    import os
+    workers = workers or os.cpu_count() or 1
+    n = np.diff(b.atom_ptr).astype(np.float64)
+    cum = np.cumsum(np.repeat(n, np.diff(b.atom_ptr)))
+    pieces = 4 * workers
+    cuts = sorted({0, b.total_atoms} | {int(np.searchsorted(cum, cum[-1] * q / pieces)) for q in range(1, pieces)})
+    tasks = [(kind, param, lo, hi) for lo, hi in zip(cuts[:-1], cuts[1:]) if hi > lo]
+    with mp.get_context("spawn").Pool(workers, initializer=_pool_init,
+                                      initargs=(b.lattice, b.frac, b.atom_ptr)) as pool:
+        parts = pool.map(_oracle_range, tasks)
+    return dict(src=np.concatenate([p[0] for p in parts]), dst=np.concatenate([p[1] for p in parts]),
+                offset=np.concatenate([p[2] for p in parts]).reshape(-1, 3))
+
+
 def graph_arrays(g):
     E = g.num_edges
     out = dict(src=g.src[:E].cpu().numpy(), dst=g.dst[:E].cpu().numpy(), offset=g.offset[:E].cpu().numpy(),

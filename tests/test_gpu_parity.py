@@ -8,8 +8,8 @@ import pytest
 
 import oracle
 import synth
-from helpers import (assert_perm_dst, assert_same_edges, assert_vectors, grad_check, graph_arrays, pointers_ok,
-                     to_device)
+from helpers import (assert_perm_dst, assert_same_edges, assert_vectors, grad_check, graph_arrays,
+                     oracle_all_sources, pointers_ok, to_device)
 
 pytestmark = pytest.mark.gpu
 
@@ -97,6 +97,23 @@ def test_config3_sampled_structures_knn(k):
         part["dst"] = part["dst"] - b.atom_ptr[s]
         assert_same_edges(part, want, f"structure {s}")
         assert_vectors(sub, part)
+
+
+def test_config3_every_edge_against_the_oracle():
+    """The 8192-structure workload at full size: every edge of the cutoff graph (r = 6 A,
+    the staged build the bench times) and of the KNN graph (k = 16) bit-exact against the
+    oracle over all 295,952 sources (spawned processes on source ranges); every vector
+    and length within 1e-6."""
+    b = synth.make_batch(3)
+    batch = to_device(b)
+    got = graph_arrays(mg.cutoff_graph(batch, 6.0, with_perm=False))
+    assert_same_edges(got, oracle_all_sources("cutoff", b, 6.0), "cutoff r=6, all sources")
+    pointers_ok(got, b)
+    assert_vectors(b, got)
+    del got
+    got = graph_arrays(mg.knn_graph(batch, 16, with_perm=False))
+    assert_same_edges(got, oracle_all_sources("knn", b, 16), "knn k=16, all sources")
+    assert_vectors(b, got)
 
 
 def test_config5_supercells_sampled_sources():
