@@ -99,20 +99,25 @@ def test_config3_sampled_structures_knn(k):
         assert_vectors(sub, part)
 
 
-def test_config3_every_edge_against_the_oracle():
-    """The 8192-structure workload at full size: every edge of the cutoff graph (r = 6 A,
-    the staged build the bench times) and of the KNN graph (k = 16) bit-exact against the
-    oracle over all 295,952 sources (spawned processes on source ranges); every vector
-    and length within 1e-6."""
-    b = synth.make_batch(3)
+@pytest.mark.parametrize("cfg,r,k", [(3, 6.0, 16), (4, 5.0, 16)])
+def test_every_edge_against_the_oracle(cfg, r, k):
+    """A workload at full size (8192 structures with 295,952 atoms; 1024 structures with
+    37k atoms): every edge of the cutoff graph (the staged build the bench times) and of
+    the KNN graph bit-exact against the oracle over all sources (spawned processes on
+    source ranges); every vector and length within 1e-6.  On the 1024-structure
+    workload also the gradient of its Gaussian edge loss over the whole batch."""
+    b = synth.make_batch(cfg)
     batch = to_device(b)
-    got = graph_arrays(mg.cutoff_graph(batch, 6.0, with_perm=False))
-    assert_same_edges(got, oracle_all_sources("cutoff", b, 6.0), "cutoff r=6, all sources")
+    g = mg.cutoff_graph(batch, r, with_perm=False)
+    got = graph_arrays(g)
+    assert_same_edges(got, oracle_all_sources("cutoff", b, r), f"cutoff r={r}, all sources")
     pointers_ok(got, b)
     assert_vectors(b, got)
+    if cfg == 4:
+        grad_check(b, g, synth.normal(4, 2, g.num_edges))
     del got
-    got = graph_arrays(mg.knn_graph(batch, 16, with_perm=False))
-    assert_same_edges(got, oracle_all_sources("knn", b, 16), "knn k=16, all sources")
+    got = graph_arrays(mg.knn_graph(batch, k, with_perm=False))
+    assert_same_edges(got, oracle_all_sources("knn", b, k), f"knn k={k}, all sources")
     assert_vectors(b, got)
 
 
