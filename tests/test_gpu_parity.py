@@ -121,6 +121,24 @@ def test_every_edge_against_the_oracle(cfg, r, k):
     assert_vectors(b, got)
 
 
+def test_supercells_up_to_4096_atoms_every_edge():
+    """The supercell workload's parameters (cutoff 8 A, k = 32; cell list, staged build) on
+    its eleven smallest supercells (1,728-4,096 atoms, 34,912 atoms in all): every edge of
+    both graphs bit-exact against the oracle over all sources, vectors within 1e-6."""
+    b5 = synth.make_batch(5)
+    n = np.diff(b5.atom_ptr)
+    b = b5.subset(sorted(np.argsort(n, kind="stable")[:11].tolist()))
+    assert int(np.diff(b.atom_ptr).max()) <= 4096 and b.total_atoms >= 8192  # the staged build
+    batch = to_device(b)
+    got = graph_arrays(mg.cutoff_graph(batch, 8.0, with_perm=False))
+    assert_same_edges(got, oracle_all_sources("cutoff", b, 8.0), "cutoff r=8, all sources")
+    pointers_ok(got, b)
+    assert_vectors(b, got)
+    got = graph_arrays(mg.knn_graph(batch, 32, with_perm=False))
+    assert_same_edges(got, oracle_all_sources("knn", b, 32), "knn k=32, all sources")
+    assert_vectors(b, got)
+
+
 def test_config5_supercells_sampled_sources():
     """Supercells up to 21,952 atoms: sampled source atoms against the oracle, plus the
     symmetry property on whole structures."""
