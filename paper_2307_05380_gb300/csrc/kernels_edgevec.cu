@@ -394,7 +394,10 @@ __device__ __forceinline__ int64_t key_bound(const int32_t *__restrict__ keys, i
 // both edges with sign-symmetric float-float arithmetic), so only its incoming
 // gradients are gathered.
 // grad_frac[j] = sum_p (g_rev(p) - g_p) L^T; the lattice partial sums (x_i - x_j + t)^T g_p.
-// Fixed per-lane order and a fixed warp reduction: deterministic, no destination order.
+// Fixed per-lane order and a fixed warp reduction (the 12 sums of an atom in one
+// reduce-scatter): deterministic, no destination order.  A warp per source atom; its
+// chunks of 32 out-edges are software-pipelined (see the loop).  64 registers, 4 blocks
+// of 8 warps per SM: the measured best against deeper pipelining or more blocks.
 template <int PAIRS>
 __global__ void __launch_bounds__(256, 4) bwd_sym_kernel(EdgeVecArgs a, float2 *__restrict__ lpart) {
     pdl_wait();  // launched early behind the forward: its vectors must be complete
