@@ -23,8 +23,14 @@ def _dev_index(device: torch.device) -> int:
     return device.index if device.index is not None else torch.cuda.current_device()
 
 
+_CTX_BY_DEVICE: dict = {}  # torch.device with an index -> its context (the per-call fast path)
+
+
 def context(device=None) -> ctypes.c_void_p:
     """The library context of a CUDA device (created on first use)."""
+    h = _CTX_BY_DEVICE.get(device) if isinstance(device, torch.device) else None
+    if h is not None:
+        return h
     device = torch.device("cuda") if device is None else torch.device(device)
     idx = _dev_index(device)
     if idx not in _CTX:
@@ -32,10 +38,19 @@ def context(device=None) -> ctypes.c_void_p:
         h = ctypes.c_void_p()
         _capi.check(lib.mg_create(ctypes.byref(h), idx), "mg_create")
         _CTX[idx] = h
+    if device.index is not None:  # an index-less device follows the current device: not cached
+        _CTX_BY_DEVICE[device] = _CTX[idx]
     return _CTX[idx]
 
 
+# the current stream's raw handle without building a Stream object (about 2 us less per
+# library call on the host); the public call when it is missing or the device has no index
+_RAW_STREAM = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
 def _stream(device) -> ctypes.c_void_p:
+    if _RAW_STREAM is not None and isinstance(device, torch.device) and device.index is not None:
+        return ctypes.c_void_p(_RAW_STREAM(device.index))
     return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
 
 
