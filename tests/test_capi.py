@@ -52,6 +52,21 @@ def test_struct_layout_matches_header(tmp_path):
     assert vals[6] == 32
 
 
+def test_output_struct_layouts_match_header(tmp_path):
+    """The triplet buffers and the host-copy buffers as the binding builds them."""
+    from paper_2307_05380_gb300._capi import MgGraphHost, MgTriplets
+    prog = tmp_path / "layout2.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "matgraph.h"\n'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(mg_triplets_t), '
+                    'offsetof(mg_triplets_t, trip_ptr), offsetof(mg_triplets_t, status), sizeof(mg_graph_host_t), '
+                    'offsetof(mg_graph_host_t, vec), offsetof(mg_graph_host_t, src_ptr));return 0;}\n')
+    exe = tmp_path / "layout2"
+    subprocess.check_call(["gcc", "-I" + os.path.dirname(HEADER), str(prog), "-o", str(exe)])
+    vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert vals == [ctypes.sizeof(MgTriplets), MgTriplets.trip_ptr.offset, MgTriplets.status.offset,
+                    ctypes.sizeof(MgGraphHost), MgGraphHost.vec.offset, MgGraphHost.src_ptr.offset], vals
+
+
 def test_status_strings(lib):
     for code in range(11):
         s = lib.mg_status_string(code).decode()
