@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(GROUP == 32 ? 128 : GROUP) prep_kernel(PrepArg
     R.atom_begin = begin;
     R.n_atoms = n;
     R.bad = bad;
-    R.pad = 0;
+    R.ax = 2;
     // Cell list for large structures: bins at least half the radius wide along each
     // plane normal (n_k = floor(2 d_k / c)), at most n_atoms bins in total; used when the
     // bins a source visits cover less than half the cell.
@@ -210,6 +210,17 @@ __global__ void __launch_bounds__(GROUP == 32 ? 128 : GROUP) prep_kernel(PrepArg
         for (int k = 0; k < 3; ++k) visited *= fminf(1.0f, (2.0f * c * invd[k] * nk[k] + 2.0f) / nk[k]);
         if (visited < 0.5f)
             for (int k = 0; k < 3; ++k) R.nb[k] = nk[k];
+    }
+    // Axis order of the staged cutoff scan: candidates along the axis of largest reach
+    // (the shortest interplanar spacing), where each row holds the most of them.  Moved
+    // only when that reach's box extent is at least 1.3 times the extent along L_2: the
+    // scan then puts the source's keys back into canonical order, which pays for itself
+    // only when the rows it saves are many (elongated or skewed cells).
+    if (!bad && R.nb[0] == 0) {
+        int ax = 2;
+        if (invd[0] > invd[ax]) ax = 0;
+        if (invd[1] > invd[ax]) ax = 1;
+        if (ax != 2 && 2.0f * c * invd[ax] + 1.0f >= 1.3f * (2.0f * c * invd[2] + 1.0f)) R.ax = ax;
     }
     recs[s] = R;  // a bad structure is reported by the kernel that scans its first atom
     if (a.pair_ok) a.pair_ok[s] = n <= PAIR_MAX ? 1 : 0;
@@ -737,15 +748,19 @@ struct SrcScan {
 };
 
 // Source constants; false when the structure is unusable (its first atom reports it).
+// `permute`: the scan may enumerate in the structure's axis order (the staged scan only:
+// where the scan is issue-bound the rows it saves outweigh the reordering of the keys;
+// in the one-pass build the reordering lengthens each warp's latency chain instead).
 template <bool PERSRC>
-__device__ __forceinline__ bool source_setup(const BuildArgs &a, const Work &w, int i, SrcScan &c) {
+__device__ __forceinline__ bool source_setup(const BuildArgs &a, const Work &w, int i, SrcScan &c,
+                                             bool permute = false) {
     c.s = w.atom_struct[i];
     const StructRec &R = w.recs[c.s];
     if (R.bad) {
         if (lane_id() == 0 && i == R.atom_begin) set_error(a.g.status, R.bad, c.s + a.struct_offset);
         return false;
     }
-    load_source(c.S, w.recs, c.s, a.frac, w.pos, i);
+    load_source(c.S, w.recs, c.s, a.frac, w.pos, i, permute);
     c.thr_lo = R.thr_lo;
     c.thr_hi = R.thr_hi;
     c.cut = R.cut;
@@ -763,8 +778,10 @@ __device__ __forceinline__ bool source_setup(const BuildArgs &a, const Work &w, 
 }
 
 // One scan of a source: FP32 test, FP64 re-test in the band, the edges' (j, t) keys
-// staged in `keys` (canonical order; sorted for cell-list sources).  Returns the edge
-// count; `spill` when the keys did not fit or an offset exceeds the packed key.
+// staged in `keys` (canonical order; sorted for cell-list sources and for sources
+// enumerated in another axis order, whose keys are first put back in lattice order).
+// Returns the edge count; `spill` when the keys did not fit or an offset exceeds the
+// packed key.
 template <bool PERSRC>
 __device__ __forceinline__ int scan_source(const BuildArgs &a, const Work &w, const SrcScan &c,
                                            unsigned long long *keys, unsigned char *trim, bool &spill) {
@@ -787,9 +804,17 @@ __device__ __forceinline__ int scan_source(const BuildArgs &a, const Work &w, co
             const int t0 = __shfl_sync(FULL, rw.t0, ow);
             const int t1 = __shfl_sync(FULL, rw.t1, ow);
             if (band) {
+                // the canonical distance in lattice axis order (the identity for ax == 2)
                 const int64_t jr = (int64_t)S.begin + jj;
-                const double d = canon_d2(S.L, S.xi0, S.xi1, S.xi2, a.frac[3 * jr], a.frac[3 * jr + 1],
-                                          a.frac[3 * jr + 2], t0, t1, t2);
+                float Lr[9];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) to_lattice_order(S.ax, S.L[q], S.L[3 + q], S.L[6 + q], Lr[q], Lr[3 + q], Lr[6 + q]);
+                float x0, x1, x2;
+                int T0, T1, T2;
+                to_lattice_order(S.ax, S.xi0, S.xi1, S.xi2, x0, x1, x2);
+                to_lattice_order(S.ax, t0, t1, t2, T0, T1, T2);
+                const double d = canon_d2(Lr, x0, x1, x2, a.frac[3 * jr], a.frac[3 * jr + 1], a.frac[3 * jr + 2],
+                                          T0, T1, T2);
                 in = incl ? d <= rr : d < rr;
             }
             if (a.collect_stats) nre += __popc(__ballot_sync(FULL, band));
@@ -805,10 +830,26 @@ __device__ __forceinline__ int scan_source(const BuildArgs &a, const Work &w, co
         if (a.collect_stats) ncand += __popc(__ballot_sync(FULL, cand));
     });
     spill = m > BUILD_CAP || __any_sync(FULL, range_bad);
-    if (!spill && S.nb[0] != 0 && m > 1) {
-        int P = 64;
-        while (P < m) P <<= 1;
-        warp_smem_sort_u64(keys, m, P);
+    if (!spill && S.ax != 2) {  // offsets back in lattice order
+        for (int q = lane_id(); q < m; q += 32) {
+            const unsigned long long k = keys[q];
+            int a0, a1, a2, t0, t1, t2;
+            unpack_t((uint32_t)(k & 0xffffffffull), a0, a1, a2);
+            to_lattice_order(S.ax, a0, a1, a2, t0, t1, t2);
+            keys[q] = (k & 0xffffffff00000000ull) | pack_t(t0, t1, t2);
+        }
+        __syncwarp();
+    }
+    if (!spill && (S.nb[0] != 0 || S.ax != 2) && m > 1) {
+        if (S.nb[0] == 0 && 2 * m <= BUILD_CAP) {
+            // all pairs: the keys are already in target order, only each target's run
+            // (its offsets) needs reordering
+            warp_smem_sort_runs_u64(keys, m);
+        } else {
+            int P = 64;
+            while (P < m) P <<= 1;
+            warp_smem_sort_u64(keys, m, P);
+        }
     }
     if (a.collect_stats && lane_id() == 0 && ncand) {
         Status *st = reinterpret_cast<Status *>(a.g.status);
@@ -993,7 +1034,7 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_stage_kernel(Build
     SrcScan c;
     int m = 0;
     bool spill = false;
-    if (source_setup<PERSRC>(a, w, i, c)) m = scan_source<PERSRC>(a, w, c, keys, nullptr, spill);
+    if (source_setup<PERSRC>(a, w, i, c, true)) m = scan_source<PERSRC>(a, w, c, keys, nullptr, spill);
     long long off = -1;
     if (!spill && m > 0) {
         if (lane == 0) off = (long long)atomicAdd(w.stage_ctr, (unsigned long long)m);

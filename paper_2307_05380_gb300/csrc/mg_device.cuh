@@ -34,7 +34,7 @@ struct StructRec {
     int32_t bad;       // mg_status_t for this structure (0 = usable)
     int32_t nb[3];     // cell-list bins per axis; nb[0] == 0: the structure uses all pairs
     int32_t bin_base;  // first bin of the structure: atom_begin + structure index
-    int32_t pad;
+    int32_t ax;        // lattice axis the cutoff scan runs its candidates along (2: none moved)
 };
 static_assert(sizeof(StructRec) == 144, "record layout");
 
@@ -211,6 +211,18 @@ __device__ __forceinline__ float vec_len(float3 v) {
     return __fsqrt_rn(__fmaf_rn(v.z, v.z, __fmaf_rn(v.y, v.y, __fmul_rn(v.x, v.x))));
 }
 
+// ------------------------------------------------------------------ axis order
+
+// A scan may enumerate a structure's offsets with lattice axis `ax` innermost: position q
+// of its (a0, a1, a2) then holds axis (p0, p1, ax)[q], p0 < p1 the other two.  Back to
+// lattice order (the identity for ax == 2):
+template <class T>
+__device__ __forceinline__ void to_lattice_order(int ax, T a0, T a1, T a2, T &t0, T &t1, T &t2) {
+    t0 = ax == 0 ? a2 : a0;
+    t1 = ax == 0 ? a0 : (ax == 1 ? a2 : a1);
+    t2 = ax == 2 ? a2 : a1;
+}
+
 // ------------------------------------------------------------------ packed offsets
 
 __device__ __forceinline__ uint32_t pack_t(int t0, int t1, int t2) {
@@ -244,6 +256,27 @@ __device__ __forceinline__ void warp_smem_sort_u64(unsigned long long *b, int n,
             __syncwarp();
         }
     }
+}
+
+// Sort n distinct 64-bit keys in shared memory with one warp when they are already
+// grouped into runs of equal high words in ascending order: each key moves to its run's
+// first position plus its rank within the run (a scan over the run, which is short where
+// this is used), through b[n, 2n) as scratch, so 2n must fit the buffer.
+__device__ __forceinline__ void warp_smem_sort_runs_u64(unsigned long long *b, int n) {
+    const int lane = lane_id();
+    for (int q = lane; q < n; q += 32) {
+        const unsigned long long k = b[q];
+        const unsigned hk = (unsigned)(k >> 32);
+        int lo = q, hi = q + 1;
+        while (lo > 0 && (unsigned)(b[lo - 1] >> 32) == hk) --lo;
+        while (hi < n && (unsigned)(b[hi] >> 32) == hk) ++hi;
+        int r = 0;
+        for (int p = lo; p < hi; ++p) r += b[p] < k ? 1 : 0;
+        b[n + lo + r] = k;
+    }
+    __syncwarp();
+    for (int q = lane; q < n; q += 32) b[q] = b[n + q];
+    __syncwarp();
 }
 
 // ------------------------------------------------------------------ error model

@@ -35,28 +35,46 @@ struct Source {
     int n;       // atoms in the structure
     int nb[3];   // bins per axis (nb[0] == 0: all-pairs structure)
     int bin_base;
+    int ax;      // lattice axis enumerated innermost (L, invd and xi are in the order (p0, p1, ax))
 };
 
+// With `permute`, an all-pairs structure whose record names another innermost axis is
+// enumerated in the axis order (p0, p1, ax): its rows along the shortest direction hold
+// more candidates each, so a skewed cell has fewer rows.  The offsets a visitor sees
+// are then in that order (to_lattice_order maps them back).
 __device__ __forceinline__ void load_source(Source &S, const StructRec *__restrict__ recs, int s,
                                             const float *__restrict__ frac,
-                                            const float4 *__restrict__ pos, int i) {
+                                            const float4 *__restrict__ pos, int i, bool permute = false) {
     const StructRec &R = recs[s];
+    const int ax = (permute && R.nb[0] == 0 && (R.ax == 0 || R.ax == 1)) ? R.ax : 2;
+    const int p0 = ax == 0 ? 1 : 0, p1 = ax == 2 ? 1 : 2;
+    S.ax = ax;
 #pragma unroll
-    for (int q = 0; q < 9; ++q) S.L[q] = R.L[q];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        S.invd[k] = R.invd[k];
-        S.nb[k] = R.nb[k];
+    for (int q = 0; q < 3; ++q) {
+        S.L[q] = R.L[3 * p0 + q];
+        S.L[3 + q] = R.L[3 * p1 + q];
+        S.L[6 + q] = R.L[3 * ax + q];
     }
+    S.invd[0] = R.invd[p0];
+    S.invd[1] = R.invd[p1];
+    S.invd[2] = R.invd[ax];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) S.nb[k] = R.nb[k];
     S.bin_base = R.bin_base;
-    S.inv_L2n2 = 1.0f / R.L2norm2;
-    S.L2norm = R.L2norm;
+    if (ax == 2) {
+        S.inv_L2n2 = 1.0f / R.L2norm2;
+        S.L2norm = R.L2norm;
+    } else {
+        const float n2 = S.L[6] * S.L[6] + S.L[7] * S.L[7] + S.L[8] * S.L[8];
+        S.inv_L2n2 = 1.0f / n2;
+        S.L2norm = sqrtf(n2);
+    }
     S.begin = R.atom_begin;
     S.n = R.n_atoms;
     S.i_loc = i - S.begin;
-    S.xi0 = frac[3 * (int64_t)i + 0];
-    S.xi1 = frac[3 * (int64_t)i + 1];
-    S.xi2 = frac[3 * (int64_t)i + 2];
+    S.xi0 = frac[3 * (int64_t)i + p0];
+    S.xi1 = frac[3 * (int64_t)i + p1];
+    S.xi2 = frac[3 * (int64_t)i + ax];
     float4 p = pos[i];
     S.pi = make_float3(p.x, p.y, p.z);
 }
@@ -338,13 +356,14 @@ __device__ __forceinline__ void for_each_candidate(const Source &S, const float 
     const bool single = fmaxf(Rk[0], fmaxf(Rk[1], Rk[2])) < 0.49f;
 
     if (!use_cells || S.nb[0] == 0) {
+        const int p0 = S.ax == 0 ? 1 : 0, p1 = S.ax == 2 ? 1 : 2;  // the source's axis order
         for (int jb = 0; jb < S.n; jb += 32) {
             const int jl = jb + lane;
             const bool vj = jl < S.n;
             float4 xj = make_float4(0.f, 0.f, 0.f, 0.f), pj = xj;
             if (vj) {
                 const int64_t row = (int64_t)S.begin + jl;
-                xj = make_float4(frac[3 * row + 0], frac[3 * row + 1], frac[3 * row + 2], 0.f);
+                xj = make_float4(frac[3 * row + p0], frac[3 * row + p1], frac[3 * row + S.ax], 0.f);
                 pj = pos[row];
             }
             visit_targets(S, Rk, rho2p, rho1, mu0, single, jl, vj, xj, pj, T, trim, visit);

@@ -360,6 +360,30 @@ def test_one_pass_and_staged_builds_match_the_oracle(schedule):
     grad_check(b, g, synth.normal(21, schedule, g.num_edges))
 
 
+@pytest.mark.parametrize("schedule", [3, 4])
+def test_elongated_cells_in_every_axis_order(schedule):
+    """Cells whose shortest direction is lattice axis 0, 1 or 2, and a skewed one: the
+    staged build (schedule 4) scans the first two with that axis innermost and restores
+    canonical order per target; the one-pass build (schedule 3) scans in lattice order.
+    Both give the oracle's edges, in canonical order, and the same gradients."""
+    kinds = np.array([
+        [[3.1, 0.0, 0.0], [1.0, 10.5, 0.0], [2.0, -1.5, 12.0]],    # shortest along L_0
+        [[10.5, 0.0, 0.0], [1.2, 3.2, 0.0], [2.1, 1.3, 11.8]],     # shortest along L_1
+        [[11.0, 0.0, 0.0], [1.0, 10.8, 0.0], [0.5, 0.7, 3.3]],     # shortest along L_2
+        [[4.29, 0.0, 0.0], [0.69, 5.02, 0.0], [6.39, -3.69, 11.62]],  # skewed, long L_2
+    ])
+    b0 = synth.make_batch(2, B=64)
+    lat = np.stack([kinds[s % len(kinds)] for s in range(b0.num_structures)])
+    b = synth.Batch(lat, b0.frac, b0.atom_ptr)
+    opts = mg.make_opts(schedule=schedule)
+    got = graph_arrays(mg.cutoff_graph(to_device(b), 6.0, opts=opts))
+    assert_same_edges(got, oracle.cutoff(b.lattice, b.frac, b.atom_ptr, 6.0), "elongated")
+    assert_vectors(b, got)
+    assert_perm_dst(got, b.total_atoms)
+    g = mg.cutoff_graph(to_device(b), 6.0, with_perm=False, opts=opts)
+    grad_check(b, g, synth.normal(23, schedule, g.num_edges))
+
+
 def test_fused_lattice_reduction_with_empty_structures():
     """The symmetric backward reduces each structure's lattice gradient in the last warp
     to finish it; empty structures (first, middle, last) still get a zero gradient, and
