@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -54,6 +55,12 @@ STAGE_MODEL = {
     ("bwd", "bwd_dst"): ("hbm", 24.0, "cut"),
     ("bwd", "bwd_lat"): ("hbm", 0.0, "cut"),
 }
+# The other roofline term of a build: FP32 distance flops over the candidates in the cube
+# around each atom's sphere (11 flops per candidate: 6 add/sub for v, 1 mul + 2 FMA for
+# d^2), with (2r)^3 / (4/3 pi r^3) = 6/pi candidates per edge.
+FLOPS_PER_CANDIDATE = 11.0
+CANDIDATES_PER_EDGE = 6.0 / math.pi
+
 # Stages that are one kernel launch; the roofline reports the slowest of these (the
 # others bundle several launches: prep, the cell-list binning, the destination sort's
 # histogram / scan / scatter / segment sort).
@@ -109,6 +116,15 @@ def kernel_source_hash() -> str:
         h.update(f.encode())
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
+
+
+def fp32_term(edges, seconds, peak_tflops):
+    """The distance-flop side of a build's roofline, beside its edge-byte side."""
+    per_edge = FLOPS_PER_CANDIDATE * CANDIDATES_PER_EDGE
+    achieved = per_edge * edges / seconds / 1e12
+    return {"achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+            "work_per_launch": f"{per_edge:.1f} flop/edge (11 per candidate, 6/pi candidates per edge) x {edges} edges",
+            "peak_source": "FP32 lanes x max SM clock"}
 
 
 def measured_peaks():
@@ -532,6 +548,8 @@ def run_mine(args, rank, world, local_rank):
     roof["peak_source"] = f"{peak_src} ({'MEASURED_PEAKS.json hbm_gbs' if bound == 'hbm' else 'FP32 lanes x clock'})"
     roof["traffic"] = recorded_traffic(args.config, dom)
     roof["work_per_launch"] = f"{per_unit:g} {'B' if bound == 'hbm' else 'flop'}/edge x {n_units} edges"
+    if dom in (("cutoff", "build"), ("knn", "knn")):
+        roof["fp32_term"] = fp32_term(n_units, t_launch, fp32_peak)
 
     if rank == 0:
         cpu = None

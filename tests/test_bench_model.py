@@ -1,0 +1,46 @@
+"""The benchmark's algorithmic work model, checked on CPU.
+
+The FP32 side of a build's roofline counts 11 flops per candidate and 6/pi candidates per
+edge: the candidates are the images in the cube of half-width r around each atom, the
+edges those inside the sphere of radius r, and (2r)^3 / (4/3 pi r^3) = 6/pi.  Here both
+are counted by brute force on the 16-structure workload; the sphere count is the
+oracle's edge count."""
+import math
+
+import numpy as np
+
+import bench
+import oracle
+import synth
+
+
+def test_candidates_per_edge_model_against_a_brute_force_count():
+    b = synth.make_batch(1)
+    r = 5.0
+    cube = sphere = 0
+    for s in range(b.num_structures):
+        lo, hi = b.atom_ptr[s], b.atom_ptr[s + 1]
+        L = b.lattice[s].astype(np.float64)
+        x = b.frac[lo:hi].astype(np.float64)
+        # every image with |v|_inf < r has |df_k| <= sqrt(3) r ||L^-1||_F
+        B = int(np.ceil(math.sqrt(3.0) * r * np.linalg.norm(np.linalg.inv(L)))) + 1
+        T = np.stack(np.meshgrid(*[np.arange(-B, B + 1)] * 3, indexing="ij"), -1).reshape(-1, 3)
+        for i in range(hi - lo):
+            df = x - x[i]
+            c = -np.round(df)
+            v = ((df + c)[:, None, :] + T[None, :, :]) @ L
+            self_img = np.zeros(v.shape[:2], bool)
+            self_img[i] = np.all(T + c[i] == 0, axis=1)
+            cube += int(((np.abs(v).max(-1) < r) & ~self_img).sum())
+            sphere += int((((v * v).sum(-1) < r * r) & ~self_img).sum())
+    edges = oracle.cutoff(b.lattice, b.frac, b.atom_ptr, r)["src"].shape[0]
+    assert sphere == edges
+    assert abs(cube / sphere - bench.CANDIDATES_PER_EDGE) < 0.03 * bench.CANDIDATES_PER_EDGE
+
+
+def test_fp32_term_arithmetic():
+    t = bench.fp32_term(1_000_000, 1e-3, 80.0)
+    per_edge = 11.0 * 6.0 / math.pi
+    assert math.isclose(t["achieved"], per_edge * 1e6 / 1e-3 / 1e12)
+    assert math.isclose(t["frac"], t["achieved"] / 80.0)
+    assert t["unit"] == "TFLOP/s"
