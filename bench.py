@@ -544,7 +544,7 @@ def run_mine(args, rank, world, local_rank):
                 "frac": achieved / fp32_peak}
     roof["kernel"] = f"{dom[0]}.{dom[1]}"
     if staged and dom == ("cutoff", "build"):
-        roof["kernel"] += " (staged: scan-and-stage, count scan, emit; 6 launches)"
+        roof["kernel"] += " (staged: scan-and-stage, count scan, emit; 7 launches)"
     roof["peak_source"] = f"{peak_src} ({'MEASURED_PEAKS.json hbm_gbs' if bound == 'hbm' else 'FP32 lanes x clock'})"
     roof["traffic"] = recorded_traffic(args.config, dom)
     roof["work_per_launch"] = f"{per_unit:g} {'B' if bound == 'hbm' else 'flop'}/edge x {n_units} edges"
