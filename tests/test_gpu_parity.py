@@ -276,6 +276,24 @@ def test_ragged_sizes_many_tiles():
     knn_parity(b, 9)
 
 
+def test_one_pass_build_across_waves():
+    """The one-pass build keeps 6 blocks of 4 source warps per SM resident; larger batches
+    run their last tiles in later waves, whose look-back reads tiles that have already
+    retired.  A batch just past one wave is compared with the oracle; the 1024-structure
+    workload (about ten waves) forced through the one-pass build gives the same arrays,
+    bit for bit, as the staged build."""
+    b = synth.make_batch(2, seed=0)  # 3,674 atoms: 919 tiles
+    assert b.total_atoms > 152 * 6 * 4
+    cutoff_parity(b, 6.0, opts=mg.make_opts(schedule=3))
+    b4 = synth.make_batch(4)
+    batch = to_device(b4)
+    onepass = graph_arrays(mg.cutoff_graph(batch, 5.0, opts=mg.make_opts(schedule=3)))
+    staged = graph_arrays(mg.cutoff_graph(batch, 5.0, opts=mg.make_opts(schedule=4)))
+    assert onepass.keys() == staged.keys()
+    for key in staged:
+        np.testing.assert_array_equal(onepass[key], staged[key], err_msg=key)
+
+
 def test_capacity_error_then_exact_rebuild():
     b = synth.make_batch(1)
     batch = to_device(b)
