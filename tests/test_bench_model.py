@@ -44,3 +44,21 @@ def test_fp32_term_arithmetic():
     assert math.isclose(t["achieved"], per_edge * 1e6 / 1e-3 / 1e12)
     assert math.isclose(t["frac"], t["achieved"] / 80.0)
     assert t["unit"] == "TFLOP/s"
+
+
+def test_recorded_traffic_only_for_the_sources_it_was_captured_on(monkeypatch):
+    """DRAM traffic from a committed ncu capture is reported only while the kernel
+    sources hash to the value stored with it; any other source gives null."""
+    entry = bench.recorded_traffic(2, ("cutoff", "build"))
+    current = bench.kernel_source_hash()
+    import json
+    import os
+    d = json.load(open(os.path.join(os.path.dirname(bench.__file__), "profiles", "traffic.json")))
+    stored = d["config2"]["cutoff.build"]
+    if stored["source_hash"] == current:
+        assert entry == stored["bytes_per_launch"]
+    else:
+        assert entry is None
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
+    assert bench.recorded_traffic(2, ("cutoff", "build")) is None
+    assert bench.recorded_traffic(9, ("cutoff", "build")) is None
