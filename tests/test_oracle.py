@@ -5,6 +5,7 @@ separate brute force on tiny inputs, and central finite differences for the grad
 """
 import itertools
 import json
+import math
 import os
 
 import numpy as np
@@ -90,6 +91,32 @@ def test_knn_tiebreak_sc():
     b = synth.crystal(np.eye(3), [[0.25, 0.5, 0.75]])
     g = knn(b, d["k"])
     assert g["offset"].tolist() == d["offsets"]
+
+
+@pytest.mark.parametrize("shape", ["needle", "rotated", "skewed"])
+def test_knn_needle_cell_closed_form(shape):
+    """One atom in a 1 x 10 x 10 A cell: every image off the L_0 line is at least 10 A away
+    (for the skewed cell too: its L_1 and L_2 move y by 10 t_1 + 4 t_2 and z by 10 t_2), so
+    for k <= 18 the k nearest are (+-m, 0, 0) at m A, m <= 9, the tie at each m broken
+    by t ((-m, 0, 0) first).  The search must grow far along L_0 alone (Alg. 1), and
+    Alg. 2's filter keeps both images of the k-th shell."""
+    L = {"needle": np.diag([1.0, 10.0, 10.0]),
+         "skewed": np.array([[1.0, 0.0, 0.0], [5.0, 10.0, 0.0], [3.0, 4.0, 10.0]])}.get(shape)
+    if shape == "rotated":
+        c, s_ = math.cos(0.7), math.sin(0.7)
+        R = np.array([[c, -s_, 0.0], [s_, c, 0.0], [0.0, 0.0, 1.0]]) @ np.array([[1.0, 0.0, 0.0], [0.0, c, -s_], [0.0, s_, c]])
+        L = np.diag([1.0, 10.0, 10.0]) @ R.T
+    b = synth.crystal(L, [[0.3, 0.6, 0.2]])
+    order = [(sgn * m, 0, 0) for m in range(1, 10) for sgn in (-1, 1)]
+    for k in (1, 5, 6, 17, 18):
+        g = knn(b, k)
+        assert g["offset"].tolist() == sorted(list(t) for t in order[:k])
+        l0 = np.linalg.norm(b.lattice[0][0].astype(np.float64))  # |L_0| of the stored FP32 lattice
+        np.testing.assert_allclose(np.sort(np.sqrt(g["d2"])), l0 * np.array(sorted(abs(t[0]) for t in order[:k])),
+                                   rtol=1e-12)
+        ties = oracle.knn(b.lattice, b.frac, b.atom_ptr, k, keep_ties=True)
+        shell = abs(order[k - 1][0])
+        assert ties["offset"].tolist() == sorted([s * m, 0, 0] for m in range(1, shell + 1) for s in (-1, 1))
 
 
 def test_triclinic_vectors_hand_computed():
