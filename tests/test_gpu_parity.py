@@ -294,6 +294,22 @@ def test_one_pass_build_across_waves():
         np.testing.assert_array_equal(onepass[key], staged[key], err_msg=key)
 
 
+def test_needle_cells_knn_radius_growth():
+    """One atom in 1 x 10 x 10 A cells (straight, rotated and skewed): the k nearest
+    images lie along L_0 up to 9 A away, so the KNN search grows its radius several times
+    along one axis; exact-k, keep-ties and a 9.5 A cutoff graph against the oracle."""
+    c, s_ = np.cos(0.7), np.sin(0.7)
+    R = np.array([[c, -s_, 0.0], [s_, c, 0.0], [0.0, 0.0, 1.0]]) @ np.array([[1.0, 0.0, 0.0], [0.0, c, -s_], [0.0, s_, c]])
+    lat = np.stack([np.diag([1.0, 10.0, 10.0]), np.diag([1.0, 10.0, 10.0]) @ R.T,
+                    np.array([[1.0, 0.0, 0.0], [5.0, 10.0, 0.0], [3.0, 4.0, 10.0]])])
+    b = synth.Batch(lat, np.array([[0.3, 0.6, 0.2]] * 3), np.array([0, 1, 2, 3], np.int32))
+    for k in (5, 18):
+        knn_parity(b, k)
+        got = graph_arrays(mg.knn_graph(to_device(b), k, keep_ties=True))
+        assert_same_edges(got, oracle.knn(b.lattice, b.frac, b.atom_ptr, k, keep_ties=True), f"ties k={k}")
+    cutoff_parity(b, 9.5)
+
+
 def test_capacity_error_then_exact_rebuild():
     b = synth.make_batch(1)
     batch = to_device(b)
