@@ -390,3 +390,8 @@ def test_gradient_invariants():
         # rotation invariance of a radial loss: L^T dLoss/dL is symmetric
         M = b.lattice[s].astype(np.float64).T @ gL[s]
         np.testing.assert_allclose(M, M.T, atol=1e-9 * np.abs(M).max())
+        # uniform strain L -> (1 + e) L with x fixed scales every length by (1 + e), so
+        # d Loss / d e = trace(L^T dLoss/dL) = sum_e (dLoss/dl_e) l_e over the structure
+        sel = (g["src"] >= lo) & (g["src"] < hi)
+        virial = float(np.sum(dlen[sel] * ln[sel]))
+        np.testing.assert_allclose(np.trace(M), virial, rtol=1e-9, atol=1e-12 * np.abs(dlen[sel] * ln[sel]).sum())
