@@ -303,8 +303,11 @@ int64_t mg_last_launch_count(mg_context_t ctx);
  *   - All calls on one device share the array, and the previous call's contents stay
  *     in it (the kernels clear what they need).  Calls whose work overlaps on the GPU
  *     (different streams, no ordering between them) race on the array: order them.
- * Output is identical to mg_cutoff_graph's; the build is not recorded for
- * mg_update_graph. */
+ * Output is identical to mg_cutoff_graph's.  The build is not recorded: mg_update_graph
+ * on these buffers returns MG_ERR_NOT_BUILT, and a plan of an earlier mg_cutoff_graph
+ * into the same buffers is dropped.  The graph is recorded as symmetric, so
+ * mg_edge_vectors_bwd needs only its src_ptr (no perm_dst) and any workspace that
+ * mg_workspace_size sizes for the batch; it finds reverse edges by binary search. */
 #define MG_NOALLOC_SCRATCH_BYTES (32u << 20)
 mg_status_t mg_cutoff_graph_noalloc(mg_context_t ctx, const mg_batch_t *batch, float cutoff,
                                     const mg_opts_t *opts, mg_graph_t *graph, void *stream);

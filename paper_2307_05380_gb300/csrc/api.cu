@@ -449,21 +449,15 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[MG_NOALLOC_SCRA
 
 namespace {
 
-constexpr int NOALLOC_MAX_DEVICES = 64;
-std::mutex g_noalloc_mu;
-void *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
-
-// Device address of the scratch array on the current device, looked up once per device.
+// Device address of the scratch array in the current device's context.  Looked up on
+// every call (a table lookup once the module is loaded): a cached address would go stale
+// when the context is torn down and created again (cudaDeviceReset), and kernels would
+// then write to memory that is no longer mapped.  The first lookup on a device loads the
+// library's module into its context.
 mg_status_t noalloc_scratch(void **out) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return MG_ERR_CUDA;
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MG_ERR_CUDA;
-        g_noalloc_addr[dev] = p;
-    }
-    *out = g_noalloc_addr[dev];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MG_ERR_CUDA;
+    *out = p;
     return MG_OK;
 }
 
@@ -947,6 +941,25 @@ mg_status_t mg_cutoff_graph_noalloc(mg_context_t ctx, const mg_batch_t *b, float
     if (r) return r;
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->last_launches = launches;
+    // The buffers now hold a graph that no recorded build describes: forget an earlier
+    // workspace build into them (its plan would replay another radius, and its pair table
+    // indexes another edge set), and record the graph as symmetric, so that the backward
+    // finds reverse edges by search rather than through a pair table.
+    const void *key = (const void *)g->src;
+    auto it = ctx->plans.find(key);
+    if (it != ctx->plans.end()) {
+        Plan &p = it->second;
+        if (p.exec) cudaGraphExecDestroy(p.exec);
+        const int which = p.kind == MG_KIND_KNN ? MG_PROF_KNN : MG_PROF_CUTOFF;
+        if (ctx->last_prof[which] == &p.prof) ctx->last_prof[which] = nullptr;
+        p.prof.destroy();
+        ctx->plans.erase(it);
+    }
+    for (auto po = ctx->pair_owner.begin(); po != ctx->pair_owner.end();) {
+        if (po->second == key) po = ctx->pair_owner.erase(po);
+        else ++po;
+    }
+    ctx->sym[key] = *g;
     return MG_OK;
 }
 
