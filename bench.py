@@ -8,8 +8,9 @@ edge-vector forward and backward passes on the cutoff graph.  Both builds replay
 captured CUDA-graph plans (mg_update_graph).  Units are edges built per step (cutoff +
 KNN).
 
-Default workload: 256 synthetic structures with 1..64 atoms (log-uniform), lengths
-U[2.5,12] A, angles U[50,130] deg, 0.9 A separation; cutoff 6 A, k = 16.
+Default workload: 8192 synthetic structures with a 70/25/5% mixture of 1-32, 33-128
+and 129-400 atoms, 10% highly skewed cells; cutoff 6 A, k = 16 (--config 2: 256
+structures with 1..64 atoms, log-uniform, lengths U[2.5,12] A, angles U[50,130] deg).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
 Prints one JSON line (rank 0).  With --sweep: the batch-size sweep of the KNN k = 32
@@ -74,7 +75,7 @@ def parse_args():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    p.add_argument("--config", type=int, default=2, choices=sorted(WORKLOADS))
+    p.add_argument("--config", type=int, default=3, choices=sorted(WORKLOADS))
     p.add_argument("--no-baselines", action="store_true", help="skip the CPU oracle and per-structure legs")
     p.add_argument("--sweep", action="store_true", help="batch-size sweep of the KNN k=32 build")
     p.add_argument("--rows", action="store_true",
@@ -313,6 +314,74 @@ def cpu_baseline_threaded(sub, wl, budget_s=12.0):
     return sum(e / dt for e, _, dt in res), len(payloads)
 
 
+def float_errors(b, g_cut, g_knn, grad_len, grad_frac, grad_lat, seed=7, edge_sample=1 << 20, struct_sample=64):
+    """Error of every float output against the FP64 oracle, outside every timed region:
+    vec and len of both graphs on a uniform sample of edges (relative to the exact
+    length), and grad_frac / grad_lattice of the step's backward on a sample of whole
+    structures (the gradient of a structure depends on its edges only).  Gradient errors
+    are given relative to the oracle's norm (per atom and per structure) and in units of
+    the condition-aware scale sum_e |contribution| per component."""
+    import numpy as np
+    import torch
+
+    import oracle
+    rng = np.random.default_rng(seed)
+    out = {}
+    for name, g in (("cutoff", g_cut), ("knn", g_knn)):
+        E = g.num_edges
+        idx = np.sort(rng.choice(E, min(E, edge_sample), replace=False)) if E else np.zeros(0, np.int64)
+        ti = torch.from_numpy(idx).to(g.src.device)
+        src, dst, off = g.src[ti].cpu().numpy(), g.dst[ti].cpu().numpy(), g.offset[ti].cpu().numpy()
+        vec, ln = g.vec[ti].cpu().numpy().astype(np.float64), g.len[ti].cpu().numpy().astype(np.float64)
+        ov, ol = oracle.edge_vectors(b.lattice, b.frac, b.atom_ptr, src, dst, off)
+        out[f"{name}_len_rel_max"] = float(np.max(np.abs(ln - ol) / ol, initial=0))
+        out[f"{name}_vec_rel_max"] = float(np.max(np.linalg.norm(vec - ov, axis=1) / ol, initial=0))
+        out[f"{name}_edges_sampled"] = int(len(idx))
+    B = b.num_structures
+    structs = np.sort(rng.choice(B, min(B, struct_sample), replace=False))
+    edge_ptr = g_cut.edge_ptr.cpu().numpy()
+    gl_all = grad_len.cpu().numpy().astype(np.float64)
+    gf_gpu = grad_frac.cpu().numpy().astype(np.float64)
+    gL_gpu = grad_lat.cpu().numpy().astype(np.float64).reshape(-1, 3, 3)
+    f_rel = L_rel = f_cond = L_cond = 0.0
+    for s in structs:
+        e0, e1 = int(edge_ptr[s]), int(edge_ptr[s + 1])
+        a0, a1 = int(b.atom_ptr[s]), int(b.atom_ptr[s + 1])
+        if e1 == e0:
+            continue
+        sub = b.subset([int(s)])
+        src = g_cut.src[e0:e1].cpu().numpy() - a0
+        dst = g_cut.dst[e0:e1].cpu().numpy() - a0
+        off = g_cut.offset[e0:e1].cpu().numpy()
+        gl = gl_all[e0:e1]
+        gf, gL = oracle.edge_grad(sub.lattice, sub.frac, sub.atom_ptr, src, dst, off, None, gl)
+        df_err = np.abs(gf_gpu[a0:a1] - gf)
+        dL_err = np.abs(gL_gpu[s] - gL[0])
+        nf = np.linalg.norm(gf, axis=1)
+        ok = nf > 0
+        if ok.any():
+            f_rel = max(f_rel, float(np.max(np.linalg.norm(gf_gpu[a0:a1] - gf, axis=1)[ok] / nf[ok])))
+        if np.linalg.norm(gL[0]) > 0:
+            L_rel = max(L_rel, float(np.linalg.norm(gL_gpu[s] - gL[0]) / np.linalg.norm(gL[0])))
+        # condition-aware scale: |g_e,c| <= |grad_len_e|, edge e adds +-g_e L^T and df^T g_e
+        Lt = np.abs(sub.lattice[0].astype(np.float64))
+        h = np.abs(gl)[:, None] * Lt.sum(axis=1)[None, :]
+        scale_f = np.zeros((a1 - a0, 3))
+        np.add.at(scale_f, src, h)
+        np.add.at(scale_f, dst, h)
+        dfr = np.abs(sub.frac[dst].astype(np.float64) - sub.frac[src] + off)
+        scale_L = (dfr[:, :, None] * np.abs(gl)[:, None, None] * np.ones((1, 1, 3))).sum(axis=0)
+        f_cond = max(f_cond, float(np.max(df_err / (scale_f + 1e-30))))
+        L_cond = max(L_cond, float(np.max(dL_err / (scale_L + 1e-30))))
+    out.update({"grad_frac_rel_max": f_rel, "grad_lattice_rel_max": L_rel,
+                "grad_frac_cond_max": f_cond, "grad_lattice_cond_max": L_cond,
+                "structures_sampled": int(len(structs)),
+                "how": "vec/len: |x - x64| / len64 over sampled edges of both graphs; gradients of the step's "
+                       "backward (loss sum w*len) on sampled structures: per-atom / per-structure norm-wise "
+                       "relative error, and max |err| / sum_e |contribution| per component (cond)"})
+    return out
+
+
 def run_mine(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -518,6 +587,10 @@ def run_mine(args, rank, world, local_rank):
                 stage_tot[(which, name)] = stage_tot.get((which, name), 0.0) + ms
 
     clocks = sampler.stop()
+    ferr = None
+    if rank == 0 and not args.no_baselines:
+        torch.cuda.synchronize(dev)
+        ferr = float_errors(b, g_cut, g_knn, grad_len[:E_cut], grad_frac, grad_lat)
 
     # roofline of the dominant stage
     hbm_peak, sm_max, peak_src = measured_peaks()
@@ -572,7 +645,7 @@ def run_mine(args, rank, world, local_rank):
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "step": "cutoff build + KNN build (CUDA-graph plans) + edge-vector fwd + bwd on the "
                                    "cutoff graph; destination orders not requested (unused by the step)"},
-                "roofline": roof, "cpu_baseline": cpu,
+                "roofline": roof, "cpu_baseline": cpu, "float_error": ferr,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": gpu_launches, "clocks": clocks, "per_structure": per_structure,
                 "stage_ms_per_step": stages, "wall_s_timed_region": t_wall}
@@ -829,21 +902,49 @@ def run_md(args, local_rank):
             mg.edge_vectors_bwd(g, batch, None, gl, out_vec, out_len, grad_frac, grad_lat)
             counts[t].copy_(g.status[:2])
 
-    for _ in range(max(1, args.warmup // 3)):
-        loop()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    loop()
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1)
+    # the plain comparison: the same loop with every graph built by the same kernels
+    # launched once per structure (a per-structure graph is not recorded as symmetric, so
+    # its backward goes through the destination order it also builds)
+    ap_host = b0.atom_ptr.tolist()
+    ps = mg.cutoff_graph(batch, wl["cutoff"], with_perm=True, capacity=int(1.3 * E0))
+    ps_counts = torch.zeros(nsteps, 2, dtype=torch.int64, device=dev)
+
+    def loop_per_structure():
+        for t in range(nsteps):
+            batch.frac.copy_(fr_d[t])
+            batch.lattice.copy_(la_d[t])
+            mg.rebuild(ps, sync=False, per_structure=True, atom_ptr_host=ap_host)
+            mg.edge_vectors_fwd(ps, out_vec=out_vec, out_len=out_len)
+            gl = -w * out_len / (sigma * sigma) * torch.exp(-out_len * out_len / (2 * sigma * sigma))
+            mg.edge_vectors_bwd(ps, batch, None, gl, out_vec, out_len, grad_frac, grad_lat)
+            ps_counts[t].copy_(ps.status[:2])
+
+    def timed(fn):
+        for _ in range(max(1, args.warmup // 3)):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    ms = timed(loop)
+    ms_ps = timed(loop_per_structure)
     c = counts.cpu()
+    cp = ps_counts.cpu()
     assert all(int(x) & 0xFFFFFFFF == 0 for x in c[:, 0]), c
+    assert torch.equal(c[:, 1], cp[:, 1]), (c, cp)  # the same edge count every step
     edges = int(c[:, 1].sum())
     print(json.dumps({"md": "perturbation loop: update -> edge vectors -> Gaussian-loss backward",
                       "workload": wl["name"], "steps": nsteps, "edges_per_step_mean": edges / nsteps,
                       "edges_min_max": [int(c[:, 1].min()), int(c[:, 1].max())], "ms_per_step": ms / nsteps,
-                      "edges_per_s": edges / ms * 1e3, "timing": "CUDA events around the 20 steps"}), flush=True)
+                      "edges_per_s": edges / ms * 1e3,
+                      "per_structure": {"ms_per_step": ms_ps / nsteps, "edges_per_s": edges / ms_ps * 1e3,
+                                        "speedup_batched": ms_ps / ms,
+                                        "how": "the same loop, every graph built by mg_build_per_structure "
+                                               "(one launch sequence per structure) with its destination order"},
+                      "timing": "CUDA events around the 20 steps"}), flush=True)
     return 0
 
 

@@ -23,7 +23,7 @@ def _pool_init(lattice, frac, atom_ptr):
 def _oracle_range(task):
     kind, param, lo, hi = task
     lattice, frac, atom_ptr = _POOL_BATCH
-    src = np.arange(lo, hi, dtype=np.int32)
+    src = np.arange(lo, hi, dtype=np.int32) if not isinstance(lo, np.ndarray) else lo
     g = oracle.cutoff(lattice, frac, atom_ptr, param, sources=src) if kind == "cutoff" \
         else oracle.knn(lattice, frac, atom_ptr, param, sources=src)
     return g["src"], g["dst"], g["offset"]
@@ -47,6 +47,35 @@ def oracle_all_sources(kind, b, param, workers=None):
         parts = pool.map(_oracle_range, tasks)
     return dict(src=np.concatenate([p[0] for p in parts]), dst=np.concatenate([p[1] for p in parts]),
                 offset=np.concatenate([p[2] for p in parts]).reshape(-1, 3))
+
+
+def oracle_sources(kind, b, param, sources, workers=None):
+    """The oracle's graph restricted to the given ascending source rows of batch b,
+    computed by spawned processes on pieces of the source list of about equal cost (a
+    source costs the atoms of its structure) and joined in source order."""
+    import multiprocessing as mp
+    import os
+    workers = workers or os.cpu_count() or 1
+    sources = np.asarray(sources, np.int32)
+    n = np.diff(b.atom_ptr).astype(np.float64)
+    atom_s = np.repeat(np.arange(b.num_structures), np.diff(b.atom_ptr))
+    cum = np.cumsum(n[atom_s[sources]])
+    pieces = 4 * workers
+    cuts = sorted({0, len(sources)} | {int(np.searchsorted(cum, cum[-1] * q / pieces)) for q in range(1, pieces)})
+    tasks = [(kind, param, sources[lo:hi], None) for lo, hi in zip(cuts[:-1], cuts[1:]) if hi > lo]
+    with mp.get_context("spawn").Pool(workers, initializer=_pool_init,
+                                      initargs=(b.lattice, b.frac, b.atom_ptr)) as pool:
+        parts = pool.map(_oracle_range, tasks)
+    return dict(src=np.concatenate([p[0] for p in parts]), dst=np.concatenate([p[1] for p in parts]),
+                offset=np.concatenate([p[2] for p in parts]).reshape(-1, 3))
+
+
+def rows_of_sources(src_ptr, sources):
+    """Edge rows of the given sources, concatenated in source order (CSR src_ptr)."""
+    lo = np.asarray(src_ptr)[sources]
+    hi = np.asarray(src_ptr)[np.asarray(sources) + 1]
+    return np.concatenate([np.arange(a, c, dtype=np.int64) for a, c in zip(lo, hi)]) if len(lo) else \
+        np.zeros(0, np.int64)
 
 
 def graph_arrays(g):
@@ -96,10 +125,48 @@ def pointers_ok(got, b):
     np.testing.assert_array_equal(got["src_ptr"], src_ptr)
 
 
-def grad_check(b, g, w, sigma=1.5):
-    """Autograd through the library's edge vectors for a Gaussian edge loss, against the
-    oracle's analytic gradient within a condition-aware bound (1e-5 of the summed
-    magnitudes of the contributions).  Returns the two gradients."""
+def assert_grad_bound(b, got, grad_vec, grad_len, gf_gpu, gL_gpu, rel=1e-5):
+    """GPU gradients w.r.t. frac and lattice against the oracle's FP64 analytic gradient
+    of the same incoming edge gradients, per component within rel times the summed
+    magnitudes of the contributions (a condition-aware bound).  Edge e contributes
+    g_e L^T to its destination and -g_e L^T to its source, and (x_j - x_i + t)^T g_e to
+    the lattice gradient, with g_e = grad_vec_e + grad_len_e vec_e / len_e; since
+    |vec_c / len| <= 1, |g_e,c| <= |grad_vec_e,c| + |grad_len_e| componentwise.  Either
+    incoming gradient may be None.  Returns the largest error in units of the bound."""
+    E = got["src"].shape[0]
+    gv = None if grad_vec is None else np.asarray(grad_vec, np.float64).reshape(E, 3)
+    gl = None if grad_len is None else np.asarray(grad_len, np.float64).reshape(E)
+    gf, gL = oracle.edge_grad(b.lattice, b.frac, b.atom_ptr, got["src"], got["dst"], got["offset"], gv, gl)
+    gabs = np.zeros((E, 3))
+    if gv is not None:
+        gabs += np.abs(gv)
+    if gl is not None:
+        gabs += np.abs(gl)[:, None]
+    Lt = np.abs(b.lattice.astype(np.float64))
+    atom_s = np.repeat(np.arange(b.num_structures), np.diff(b.atom_ptr))
+    s_e = atom_s[got["src"]]
+    # |g_e| |L|^T per edge and component k: sum_c |g_e,c| |L_kc|
+    h = np.einsum("ec,ekc->ek", gabs, Lt[s_e])
+    scale_f = np.zeros((b.total_atoms, 3))
+    np.add.at(scale_f, got["src"], h)
+    np.add.at(scale_f, got["dst"], h)
+    err_f = np.abs(np.asarray(gf_gpu, np.float64) - gf)
+    df = b.frac[got["dst"]].astype(np.float64) - b.frac[got["src"]] + got["offset"]
+    scale_L = np.zeros((b.num_structures, 3, 3))
+    np.add.at(scale_L, s_e, np.abs(df)[:, :, None] * gabs[:, None, :])
+    err_L = np.abs(np.asarray(gL_gpu, np.float64).reshape(-1, 3, 3) - gL)
+    bf = rel * scale_f + 1e-12
+    bL = rel * scale_L + 1e-12
+    assert np.all(err_f <= bf), f"grad_frac: max err {err_f.max()}, worst ratio {(err_f / bf).max()}"
+    assert np.all(err_L <= bL), f"grad_lattice: max err {err_L.max()}, worst ratio {(err_L / bL).max()}"
+    return max(float((err_f / bf).max(initial=0)), float((err_L / bL).max(initial=0)))
+
+
+def grad_check(b, g, w, sigma=1.5, c=None):
+    """Autograd through the library's edge vectors for the loss
+    sum_e w_e exp(-len_e^2 / 2 sigma^2) (+ sum_e c_e . vec_e when c [E, 3] is given, the
+    grad_vec path), against the oracle's analytic gradient within the condition-aware
+    bound of assert_grad_bound.  Returns the two gradients."""
     import torch
 
     import paper_2307_05380_gb300 as mg
@@ -109,25 +176,11 @@ def grad_check(b, g, w, sigma=1.5):
     vec, ln = mg.edge_vectors(frac, lat, g)
     wt = torch.from_numpy(w).to(batch.device)
     loss = (wt * torch.exp(-ln ** 2 / (2 * sigma ** 2))).sum()
+    if c is not None:
+        loss = loss + (vec * torch.from_numpy(np.asarray(c, np.float32)).to(batch.device)).sum()
     loss.backward()
     got = graph_arrays(g)
     ov, ol = oracle.edge_vectors(b.lattice, b.frac, b.atom_ptr, got["src"], got["dst"], got["offset"])
     _, dlen = oracle.gaussian_loss_grads(ov, ol, w, sigma)
-    gf, gL = oracle.edge_grad(b.lattice, b.frac, b.atom_ptr, got["src"], got["dst"], got["offset"], None, dlen)
-    # condition-aware bound: 1e-5 of the summed magnitudes of the contributions
-    gabs = np.abs(dlen)[:, None] * np.ones((1, 3))
-    scale_f = np.zeros_like(gf)
-    Lt = np.abs(b.lattice.astype(np.float64))
-    atom_s = np.repeat(np.arange(b.num_structures), np.diff(b.atom_ptr))
-    # |g_e| L^T magnitudes per edge and component (|dLoss/dlen| bounds |g_e| componentwise)
-    h = np.einsum("ec,ekc->ek", gabs, Lt[atom_s[got["src"]]])
-    np.add.at(scale_f, got["src"], h)
-    np.add.at(scale_f, got["dst"], h)
-    err_f = np.abs(frac.grad.cpu().numpy() - gf)
-    assert np.all(err_f <= 1e-5 * scale_f + 1e-12), err_f.max()
-    df = (b.frac[got["dst"]].astype(np.float64) - b.frac[got["src"]] + got["offset"])
-    scale_L = np.zeros((b.num_structures, 3, 3))
-    np.add.at(scale_L, atom_s[got["src"]], np.abs(df)[:, :, None] * gabs[:, None, :])
-    err_L = np.abs(lat.grad.cpu().numpy() - gL)
-    assert np.all(err_L <= 1e-5 * scale_L + 1e-12), err_L.max()
+    assert_grad_bound(b, got, c, dlen, frac.grad.cpu().numpy(), lat.grad.cpu().numpy())
     return frac.grad.clone(), lat.grad.clone()

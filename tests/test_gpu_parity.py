@@ -9,7 +9,7 @@ import pytest
 import oracle
 import synth
 from helpers import (assert_perm_dst, assert_same_edges, assert_vectors, grad_check, graph_arrays,
-                     oracle_all_sources, pointers_ok, to_device)
+                     oracle_all_sources, oracle_sources, pointers_ok, rows_of_sources, to_device)
 
 pytestmark = pytest.mark.gpu
 
@@ -139,25 +139,31 @@ def test_supercells_up_to_4096_atoms_every_edge():
     assert_vectors(b, got)
 
 
+def supercell_sources(b, per, seed):
+    """`per` seeded source rows of every structure of b (all of a smaller one), ascending."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for s in range(b.num_structures):
+        lo, hi = int(b.atom_ptr[s]), int(b.atom_ptr[s + 1])
+        out.append(np.sort(rng.choice(np.arange(lo, hi), min(per, hi - lo), replace=False)))
+    return np.concatenate(out).astype(np.int32)
+
+
 def test_config5_supercells_sampled_sources():
-    """Supercells up to 21,952 atoms: sampled source atoms against the oracle, plus the
-    symmetry property on whole structures."""
+    """Every supercell (1,728-21,952 atoms, cell list, staged build), 256 seeded sources
+    each, all their edges at cutoff 8 A bit-exact against the oracle; vectors of those
+    edges within 1e-6; in-degree equal to out-degree over the whole batch (a constant
+    cutoff gives a symmetric graph)."""
     b = synth.make_batch(5)
     g = mg.cutoff_graph(to_device(b), 8.0, with_perm=False)
     src_ptr = g.src_ptr.cpu().numpy()
-    rng = np.random.default_rng(5)
-    for s in range(0, b.num_structures, 4):
-        lo, hi = b.atom_ptr[s], b.atom_ptr[s + 1]
-        srcs = np.sort(rng.choice(np.arange(lo, hi), 3, replace=False)).astype(np.int32)
-        want = oracle.cutoff(b.lattice, b.frac, b.atom_ptr, 8.0, sources=srcs)
-        parts = []
-        for a in srcs:
-            e0, e1 = src_ptr[a], src_ptr[a + 1]
-            parts.append((g.src[e0:e1].cpu().numpy(), g.dst[e0:e1].cpu().numpy(), g.offset[e0:e1].cpu().numpy()))
-        got = dict(src=np.concatenate([p[0] for p in parts]), dst=np.concatenate([p[1] for p in parts]),
-                   offset=np.concatenate([p[2] for p in parts]))
-        assert_same_edges(got, want, f"supercell {s}")
-    # degree symmetry: in-degree equals out-degree for a constant cutoff
+    srcs = supercell_sources(b, 256, 5)
+    want = oracle_sources("cutoff", b, 8.0, srcs)
+    rows = torch.from_numpy(rows_of_sources(src_ptr, srcs)).to(g.src.device)
+    got = dict(src=g.src[rows].cpu().numpy(), dst=g.dst[rows].cpu().numpy(), offset=g.offset[rows].cpu().numpy(),
+               vec=g.vec[rows].cpu().numpy(), len=g.len[rows].cpu().numpy())
+    assert_same_edges(got, want, "supercells, 256 sources each")
+    assert_vectors(b, got)
     E = g.num_edges
     deg_out = np.diff(src_ptr)
     deg_in = np.bincount(g.dst[:E].cpu().numpy(), minlength=b.total_atoms)
@@ -165,18 +171,34 @@ def test_config5_supercells_sampled_sources():
 
 
 def test_config5_knn_sampled_sources():
+    """Every supercell, 256 seeded sources each: their k = 32 nearest images bit-exact
+    against the oracle, vectors within 1e-6."""
     b = synth.make_batch(5)
     k = 32
     g = mg.knn_graph(to_device(b), k, with_perm=False)
-    rng = np.random.default_rng(55)
-    for s in range(0, b.num_structures, 8):
-        lo, hi = b.atom_ptr[s], b.atom_ptr[s + 1]
-        srcs = np.sort(rng.choice(np.arange(lo, hi), 2, replace=False)).astype(np.int32)
-        want = oracle.knn(b.lattice, b.frac, b.atom_ptr, k, sources=srcs)
-        rows = np.concatenate([np.arange(a * k, a * k + k) for a in srcs])
-        idx = torch.from_numpy(rows).to(g.src.device)
-        got = dict(src=g.src[idx].cpu().numpy(), dst=g.dst[idx].cpu().numpy(), offset=g.offset[idx].cpu().numpy())
-        assert_same_edges(got, want, f"supercell {s}")
+    srcs = supercell_sources(b, 256, 55)
+    want = oracle_sources("knn", b, k, srcs)
+    rows = torch.from_numpy((srcs[:, None].astype(np.int64) * k + np.arange(k)).reshape(-1)).to(g.src.device)
+    got = dict(src=g.src[rows].cpu().numpy(), dst=g.dst[rows].cpu().numpy(), offset=g.offset[rows].cpu().numpy(),
+               vec=g.vec[rows].cpu().numpy(), len=g.len[rows].cpu().numpy())
+    assert_same_edges(got, want, "supercells knn k=32, 256 sources each")
+    assert_vectors(b, got)
+
+
+def test_config5_three_largest_supercells_every_edge():
+    """The three largest supercells (21,952, 21,952 and 17,576 atoms) at cutoff 8 A, built
+    inside the whole 32-structure batch: every edge of the three bit-exact against the
+    oracle over all their sources (about 1.3e9 atom pairs, spawned processes on source
+    ranges), so the edge count of each is exact too."""
+    b = synth.make_batch(5)
+    g = mg.cutoff_graph(to_device(b), 8.0, with_perm=False)
+    edge_ptr = g.edge_ptr.cpu().numpy()
+    big = sorted(np.argsort(np.diff(b.atom_ptr), kind="stable")[-3:].tolist())
+    srcs = np.concatenate([np.arange(b.atom_ptr[s], b.atom_ptr[s + 1]) for s in big]).astype(np.int32)
+    want = oracle_sources("cutoff", b, 8.0, srcs)
+    rows = torch.from_numpy(np.concatenate([np.arange(edge_ptr[s], edge_ptr[s + 1]) for s in big])).to(g.src.device)
+    got = dict(src=g.src[rows].cpu().numpy(), dst=g.dst[rows].cpu().numpy(), offset=g.offset[rows].cpu().numpy())
+    assert_same_edges(got, want, "three largest supercells, every edge")
 
 
 # ------------------------------------------------------------------ closed forms and edge cases
@@ -433,13 +455,7 @@ def test_symmetric_and_destination_order_backward_agree():
 def test_gradients_knn_graph_grad_vec_path():
     b = synth.make_batch(2, B=64)
     g = mg.knn_graph(to_device(b), 16)
-    frac = g.batch.frac.clone().requires_grad_(True)
-    lat = g.batch.lattice.clone().requires_grad_(True)
-    vec, ln = mg.edge_vectors(frac, lat, g)
-    c = torch.from_numpy(synth.normal(5, 1, 3 * g.num_edges).reshape(-1, 3)).cuda()
-    (vec * c).sum().backward()
-    got = graph_arrays(g)
-    gf, gL = oracle.edge_grad(b.lattice, b.frac, b.atom_ptr, got["src"], got["dst"], got["offset"],
-                              c.cpu().numpy().astype(np.float64), None)
-    np.testing.assert_allclose(frac.grad.cpu().numpy(), gf, rtol=1e-4, atol=1e-4 * np.abs(gf).max())
-    np.testing.assert_allclose(lat.grad.cpu().numpy(), gL, rtol=1e-4, atol=1e-4 * np.abs(gL).max())
+    E = g.num_edges
+    # grad_vec alone (zero loss weights on the lengths), then both paths together
+    grad_check(b, g, np.zeros(E, np.float32), c=synth.normal(5, 1, 3 * E).reshape(-1, 3))
+    grad_check(b, g, synth.normal(5, 2, E), c=synth.normal(5, 1, 3 * E).reshape(-1, 3))

@@ -13,8 +13,8 @@ import pytest
 
 import oracle
 import synth
-from helpers import (assert_perm_dst, assert_same_edges, assert_vectors, grad_check, graph_arrays, pointers_ok,
-                     to_device)
+from helpers import (assert_grad_bound, assert_perm_dst, assert_same_edges, assert_vectors, grad_check, graph_arrays,
+                     pointers_ok, to_device)
 
 pytestmark = pytest.mark.gpu
 
@@ -431,11 +431,8 @@ def test_symmetric_backward_large_structures_and_grad_vec():
     f2, L2 = mg.edge_vectors_bwd(g, batch, gv, gl, v, ln)
     assert torch.equal(f1, f2) and torch.equal(L1, L2)
     got = graph_arrays(g)
-    gf, gL = oracle.edge_grad(b.lattice, b.frac, b.atom_ptr, got["src"], got["dst"], got["offset"],
-                              gv.cpu().numpy().astype(np.float64), gl.cpu().numpy().astype(np.float64))
-    np.testing.assert_allclose(f1.cpu().numpy(), gf, rtol=1e-4, atol=1e-4 * np.abs(gf).max())
-    np.testing.assert_allclose(L1.cpu().numpy(), gL, rtol=1e-4, atol=1e-4 * np.abs(gL).max())
-    grad_check(b, g, synth.normal(41, 2, E))
+    assert_grad_bound(b, got, gv.cpu().numpy(), gl.cpu().numpy(), f1.cpu().numpy(), L1.cpu().numpy())
+    grad_check(b, g, synth.normal(41, 2, E), c=synth.normal(41, 3, 3 * E).reshape(-1, 3))
 
 
 @pytest.mark.parametrize("schedule", [3, 4])

@@ -218,6 +218,18 @@ def test_canonical_order_and_pointers(cfg1):
     assert edge_ptr[-1] == len(g["src"])
 
 
+def test_pointers_against_hand_counted_csr():
+    """oracle.pointers against CSR arrays counted by hand (tests/golden/pointers.json):
+    empty structures at either end and in the middle, atoms without edges, no edges at
+    all.  An off-by-one in the source index (counting at src instead of src + 1) shifts
+    every src_ptr entry and fails here."""
+    cases = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "pointers.json")))["cases"]
+    for c in cases:
+        edge_ptr, src_ptr = oracle.pointers(np.asarray(c["src"], np.int32), np.asarray(c["atom_ptr"], np.int32))
+        np.testing.assert_array_equal(src_ptr, c["src_ptr"], err_msg=c["what"])
+        np.testing.assert_array_equal(edge_ptr, c["edge_ptr"], err_msg=c["what"])
+
+
 def test_permutation_invariance(cfg1):
     rng = np.random.default_rng(0)
     g = cut(cfg1, 5.0)
