@@ -599,9 +599,10 @@ def run_mine(args, rank, world, local_rank):
     # the staged cutoff build (large batches) is three stages: scan and stage the keys,
     # scan the counts, write the edges; its edge emission is the unit of the roofline
     staged = ("cutoff", "stage") in stage_tot
+    pair_lane = ("cutoff", "plan") in stage_tot
     if staged:
         stage_tot[("cutoff", "build")] = sum(stage_tot.get(("cutoff", k), 0.0)
-                                             for k in ("stage", "count_scan", "emit"))
+                                             for k in ("plan", "stage", "count_scan", "emit"))
     singles = {k: v for k, v in stage_tot.items() if k in SINGLE_KERNEL_STAGES and k in STAGE_MODEL}
     dom = max(singles, key=singles.get)
     bound, per_unit, which_units = STAGE_MODEL.get(dom, ("hbm", 36.0, "cut"))
@@ -616,7 +617,9 @@ def run_mine(args, rank, world, local_rank):
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak}
     roof["kernel"] = f"{dom[0]}.{dom[1]}"
-    if staged and dom == ("cutoff", "build"):
+    if pair_lane and dom == ("cutoff", "build"):
+        roof["kernel"] += " (pair-lane: cost-sorted plan, stage, count scan, emit; 9 launches)"
+    elif staged and dom == ("cutoff", "build"):
         roof["kernel"] += " (staged: scan-and-stage, count scan, emit; 7 launches)"
     roof["peak_source"] = f"{peak_src} ({'MEASURED_PEAKS.json hbm_gbs' if bound == 'hbm' else 'FP32 lanes x clock'})"
     roof["traffic"] = recorded_traffic(args.config, dom)

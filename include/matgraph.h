@@ -111,10 +111,14 @@ typedef struct {
                               works as for a cutoff graph).  Other values: invalid argument */
     int32_t schedule;      /* 0 auto (tuned), 1 flat grid, 2 persistent work queue (KNN).
                               Cutoff builds: auto picks the one-pass build (decoupled
-                              look-back) below 8192 atoms and the staged build (scan and
-                              stage keys, scan the counts, write) from there when the
+                              look-back) below 8192 atoms; from there the pair-lane build
+                              (a cost-sorted work list pulled by a persistent grid: count
+                              pass, scan of the counts, write pass) for a constant radius
+                              when max_atoms is known and at most 1024, else the staged
+                              build (scan and stage keys, scan the counts, write) when the
                               workspace covers the capacity; 3 forces the one-pass build,
-                              4 the staged one (if the workspace covers the capacity) */
+                              4 the staged one (if the workspace covers the capacity), 5
+                              the pair-lane one (constant radius; other builds ignore it) */
     int32_t collect_stats; /* 1: count FP32 candidates and FP64 re-tests into status */
     int32_t fault_tile;    /* -1.  Testing only: the one-pass cutoff build's tile with this
                               index never publishes its offset, so the bounded waits of the

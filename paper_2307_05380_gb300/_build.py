@@ -19,7 +19,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIB_DIR, "libmatgraph.so")
 
-UNITS = ["kernels_graph", "kernels_knn", "kernels_edgevec", "kernels_ext", "api"]
+UNITS = ["kernels_graph", "kernels_pairs", "kernels_knn", "kernels_edgevec", "kernels_ext", "api"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -81,6 +81,7 @@ namespace {
 constexpr size_t ALIGN = 256;
 constexpr int KIND_CUTOFF_ATOMS = 3;  // plans only: a cutoff graph with per-atom radii
 constexpr int STAGED_MIN_ATOMS = 8192; // smallest batch built by the decoupled form by default
+constexpr int PAIR_AUTO_MAX_ATOMS = 1024;  // largest structure of a batch the pair-lane build takes by default
 
 // Stage marks: with profiling on, record the next event of `prof` (default: the
 // context's set for `which`) on the stream.
@@ -122,7 +123,7 @@ size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 struct Layout {
     size_t recs, pos, atom_struct, cnt, cursor, tile_sum, src_ptr, gpart, lpart, queue, bin_cnt, bin_cursor,
         cell_start, cell_fx, cell_p, atom_bin, tile_flags, rr_atom, pair_lo, pair_hi, pair_ok, lat_cnt, stage_off,
-        sort_tmp, total;
+        items, plan_items, plan_class, item_base, sort_tmp, total;
 };
 
 // Workspace regions, 256-byte aligned; the edge-sized sort scratch comes last so that
@@ -161,6 +162,10 @@ Layout layout(int B, int N, int64_t max_edges) {
     L.pair_ok = take(sizeof(int32_t) * (size_t)(B > 0 ? B : 1));
     L.lat_cnt = take(sizeof(int32_t) * (size_t)(B > 0 ? B : 1));
     L.stage_off = take(sizeof(long long) * n);
+    L.items = take(sizeof(int2) * n);
+    L.plan_items = take(sizeof(int32_t) * (size_t)(B > 0 ? B : 1));
+    L.plan_class = take(sizeof(int32_t) * (size_t)(B > 0 ? B : 1));
+    L.item_base = take(sizeof(int32_t) * (size_t)(B > 0 ? B : 1));
     L.sort_tmp = off;  // edge-sized region, 8 bytes per edge: staged keys, or sort scratch
     off += sizeof(unsigned long long) * (size_t)(max_edges > 0 ? max_edges : 0);
     L.total = align_up(off);
@@ -197,6 +202,10 @@ Work carve(void *ws, int B, int N, int64_t max_edges) {
     w.stage = reinterpret_cast<unsigned long long *>(b + L.sort_tmp);
     w.stage_off = reinterpret_cast<long long *>(b + L.stage_off);
     w.stage_ctr = reinterpret_cast<unsigned long long *>(w.queue + 4);
+    w.items = reinterpret_cast<int2 *>(b + L.items);
+    w.plan_items = reinterpret_cast<int32_t *>(b + L.plan_items);
+    w.plan_class = reinterpret_cast<int32_t *>(b + L.plan_class);
+    w.item_base = reinterpret_cast<int32_t *>(b + L.item_base);
     w.max_edges = max_edges;
     return w;
 }
@@ -278,6 +287,26 @@ mg_status_t enqueue_build(mg_context *ctx, int kind, const mg_batch_t *b, float 
                 0, (!knn || ties) ? 1 : 0, 1, src_ptr, (knn && !ties) ? g->edge_ptr : nullptr, b->max_atoms};
     pa.cutoff_atom = kind == KIND_CUTOFF_ATOMS ? cutoff_atom : nullptr;
     const bool pairs = kind == MG_KIND_CUTOFF;  // symmetric: record the pair table for the backward
+    // The cutoff build's form: the pair-lane build (a cost-sorted work list, count pass,
+    // scan, write pass; no keys staged in global memory) for constant-radius graphs of
+    // large batches, the staged build (scan and stage keys, scan of the counts, write)
+    // or the one-pass build (decoupled look-back) otherwise.  schedule 3 / 4 / 5 force
+    // the one-pass / staged / pair-lane form, as does a form mg_autotune measured for this
+    // size class; the one-pass form's testing hook forces it.
+    int csched = o.schedule;
+    if (csched == 0) csched = ctx->tuned[0][size_class(b)];
+    const bool can_stage = o.fault_tile < 0 && me >= g->capacity;
+    // auto: large batches of structures that are known to be small enough for the
+    // pair-lane scan (batches of supercells, whose sources use a cell list, keep the
+    // staged build, which enumerates them once)
+    const bool pair_auto = N >= STAGED_MIN_ATOMS && b->max_atoms > 0 && b->max_atoms <= PAIR_AUTO_MAX_ATOMS;
+    const bool pair_form = kind == MG_KIND_CUTOFF && can_stage &&
+                           (csched == 5 || (csched != 3 && csched != 4 && pair_auto));
+    const bool staged = !pair_form && can_stage && (csched == 4 || (csched != 3 && N >= STAGED_MIN_ATOMS));
+    if (pair_form) {
+        pa.plan_items = w.plan_items;
+        pa.plan_class = w.plan_class;
+    }
     pa.pair_ok = pairs ? w.pair_ok : nullptr;
     pa.lat_cnt = pairs ? w.lat_cnt : nullptr;
     if (launch_prep(pa, w, st)) return MG_ERR_CUDA;
@@ -306,16 +335,19 @@ mg_status_t enqueue_build(mg_context *ctx, int kind, const mg_batch_t *b, float 
     ba.band_rel = o.band_rel;
     ba.atom_lo = 0;
     ba.atom_hi = N;
-    // The decoupled build (scan and stage, scan of counts, write) when the workspace can
-    // stage every edge and the batch is large: measured 10-29% faster than the one-pass
-    // build from 37k atoms up, 17% slower at 3.6k atoms (its extra launches).  schedule 3
-    // / 4 force the one-pass / decoupled form, as does a schedule mg_autotune measured for
-    // this size class; the one-pass form's testing hook forces it.
-    int csched = o.schedule;
-    if (csched == 0) csched = ctx->tuned[0][size_class(b)];
-    const bool can_stage = o.fault_tile < 0 && me >= g->capacity;
-    const bool staged = can_stage && (csched == 4 || (csched != 3 && N >= STAGED_MIN_ATOMS));
     auto cutoff_build = [&](const BuildArgs &args) -> bool {  // false on a launch error
+        if (pair_form && !args.cut_atom && !args.rr_atom) {
+            if (launch_pair_plan(args, w, st)) return false;
+            mk.mark("plan");
+            if (launch_pair_stage(args, w, st)) return false;
+            mk.mark("stage");
+            if (launch_cutoff_counts(args, w, st)) return false;
+            mk.mark("count_scan");
+            if (launch_cutoff_emit(args, w, st)) return false;
+            mk.mark("emit");
+            n += 9;
+            return true;
+        }
         if (!staged) {  // one pass: scan, look-back offsets, write (also src_ptr, edge_ptr, count)
             if (launch_cutoff_build(args, w, st)) return false;
             ++n;
@@ -385,7 +417,7 @@ mg_status_t check_build_args(mg_context *ctx, const mg_batch_t *b, const mg_opts
     if (r) return r;
     r = check_graph(g, b);
     if (r) return r;
-    if (o.knn_keep_ties < 0 || o.knn_keep_ties > 1 || !(o.band_rel >= 0.f) || o.schedule < 0 || o.schedule > 4)
+    if (o.knn_keep_ties < 0 || o.knn_keep_ties > 1 || !(o.band_rel >= 0.f) || o.schedule < 0 || o.schedule > 5)
         return MG_ERR_INVALID_ARGUMENT;
     return MG_OK;
 }

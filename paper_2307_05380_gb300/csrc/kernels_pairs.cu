@@ -1,0 +1,448 @@
+// Pair-lane cutoff build (Def. 3, Sec. 2.1) for large batches on sm_103a.
+//
+// The evaluated area of Alg. 1 is, per pair of atoms (i, j), the box of cell offsets t
+// with |x_j,k - x_i,k + t_k| <= c / d_k on every axis (d_k the interplanar spacing): every
+// image closer than c lies in it.  In crystal batches almost every pair's box is small
+// (at most 64 cells), so here one lane owns one (source, target) pair and evaluates its
+// whole box: FP32 distance, FP64 canonical re-test in the band, the pair's edges marked
+// in a 64-bit mask.  Lanes are grouped G per source (G the smallest power of two >= the
+// structure's atom count, at most 32), so a warp covers 32 / G sources of one structure
+// and loops over its targets in chunks of G.  Lane order is target order and each lane's
+// mask is in offset order, so a scan of the mask counts gives every edge its canonical
+// position.
+//
+//   plan   each structure's work items (source groups; one item per source for
+//          structures scanned by the warp enumeration) are bucketed by cost class and
+//          laid out heaviest first (a cost-sorted work list)
+//   stage  a persistent grid pulls the items: masks, per-source counts, then the (j, t)
+//          keys of the item's sources at their canonical positions in one slot range of
+//          the staging area (one atomic add per item)
+//   scan   of the counts: src_ptr, edge_ptr, edge count and capacity check
+//   emit   a thread per edge row writes src, dst, t, vec and len from the staged key
+//          (the staged build's emit kernel), sources that did not fit are enumerated
+//          again
+//
+// Structures whose boxes are larger, that use a cell list or whose offsets exceed the
+// packed key are scanned by the warp enumeration of mg_enum.cuh inside the same passes.
+#include "mg_build.cuh"
+#include "mg_device.cuh"
+#include "mg_launch.h"
+
+namespace mg {
+
+constexpr int PAIR_WARPS = 4;
+constexpr int PLAN_THREADS = 1024;
+
+// ============================================================================ plan
+
+// One block: histogram of work items by cost class (classes 32..63 for structures of
+// the warp enumeration, 0..31 for pair-lane ones), class bases with the warp-enumeration
+// items first and each kind heaviest first, and the first slot of every structure's items
+// (within a class in arrival order: the order of equally costly items does not affect
+// any output).  queue[8] gets the total, queue[9] the number of warp-enumeration items.
+__global__ void __launch_bounds__(PLAN_THREADS) pair_plan_kernel(int B, const int32_t *__restrict__ plan_items,
+                                                                 const int32_t *__restrict__ plan_class,
+                                                                 int32_t *__restrict__ item_base,
+                                                                 unsigned int *__restrict__ queue) {
+    __shared__ int hist[64], base[64];
+    if (threadIdx.x < 64) hist[threadIdx.x] = 0;
+    __syncthreads();
+    for (int s = threadIdx.x; s < B; s += PLAN_THREADS) atomicAdd(&hist[plan_class[s]], plan_items[s]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int c = 63; c >= 0; --c) {
+            base[c] = run;
+            run += hist[c];
+            if (c == 32) queue[9] = (unsigned)run;
+        }
+        queue[8] = (unsigned)run;
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < B; s += PLAN_THREADS) item_base[s] = atomicAdd(&base[plan_class[s]], plan_items[s]);
+}
+
+// A warp per structure writes its items (structure, item index) at its slots.
+__global__ void __launch_bounds__(256) pair_fill_kernel(int B, const int32_t *__restrict__ plan_items,
+                                                        const int32_t *__restrict__ item_base, int2 *__restrict__ items) {
+    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s >= B) return;
+    const int n = plan_items[s], b0 = item_base[s];
+    for (int q = lane_id(); q < n; q += 32) items[b0 + q] = make_int2(s, q);
+}
+
+// ============================================================================ pair boxes
+
+// Constants of one structure that the lanes keep in registers.
+struct PairStruct {
+    float L[9];
+    float reach[3];       // c / d_k plus the structure's margin: reach of the box along each axis
+    float thr_lo, thr_hi; // FP32 d2 below thr_lo: edge; above thr_hi: not; between: FP64 test
+    double rr;            // canonical squared cutoff
+    int begin, n;
+    int G, spw;           // lanes per source, sources per warp
+};
+
+__device__ __forceinline__ void load_pair_struct(PairStruct &P, const StructRec &R) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) P.L[q] = R.L[q];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) P.reach[k] = R.reach[k];
+    P.thr_lo = R.thr_lo;
+    P.thr_hi = R.thr_hi;
+    P.rr = R.rr;
+    P.begin = R.atom_begin;
+    P.n = R.n_atoms;
+    int G = 1;
+    while (G < P.n && G < 32) G <<= 1;
+    P.G = G;
+    P.spw = 32 / G;
+}
+
+// The canonical FP64 test of one candidate in the band, out of line: inlined, the
+// compiler hoists its float-to-double conversions out of the branch into every pair,
+// and on this GPU the FP64 pipe runs at a small fraction of the FP32 rate.
+__device__ __noinline__ bool band_is_edge(const StructRec *__restrict__ rec, float xi0, float xi1, float xi2,
+                                          float xj0, float xj1, float xj2, float t0, float t1, float t2) {
+    return canon_d2(rec->L, xi0, xi1, xi2, xj0, xj1, xj2, (int)t0, (int)t1, (int)t2) < rec->rr;
+}
+
+// The offset box of pair (i, j): the integers t_k with |x_j,k - x_i,k + t_k| <= reach_k,
+// lo[k] .. lo[k] + nn[k] - 1 on axis k, and the mask of its edges, bit q0 nn1 nn2 + q1 nn2
+// + q2 for offset lo + (q0, q1, q2).  FP32 distances come from the same fused operations
+// in the same order as the warp enumeration, so the structure's FP32 error bound (the
+// re-test band) holds; candidates inside the band take the canonical FP64 test.  Bounds
+// and offsets stay in FP32 (exact for these small integers), so that the loop converts
+// nothing.  A box larger than the mask cannot occur for a structure marked pair-lane (its
+// record bounds every pair's box); if it did, the box would be left out and
+// MG_ERR_INTERNAL reported.
+struct PairBox {
+    float lo[3], nn[3];
+};
+
+__device__ __forceinline__ void pair_box(const PairStruct &P, bool ok, float xi0, float xi1, float xi2, float xj0,
+                                         float xj1, float xj2, PairBox &bx) {
+    const float dx[3] = {__fsub_rn(xj0, xi0), __fsub_rn(xj1, xi1), __fsub_rn(xj2, xi2)};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        bx.lo[k] = ceilf(__fsub_rn(-P.reach[k], dx[k]));
+        const float hi = floorf(__fsub_rn(P.reach[k], dx[k]));
+        bx.nn[k] = ok ? fmaxf(0.0f, __fadd_rn(__fsub_rn(hi, bx.lo[k]), 1.0f)) : 0.0f;
+    }
+}
+
+// The cells of one row (t0, t1) of a pair's box: U offsets t2 = lo2 + q, q < nn2 (U the
+// structure's largest extent along L_2, so every lane unrolls the same code), FP32
+// distances from the row base b, then the edges' bits (bit q) with the band's candidates
+// decided by the canonical FP64 test and (i, i, 0) left out.
+template <int U>
+__device__ __forceinline__ unsigned row_bits(const PairStruct &P, const StructRec *__restrict__ rec, float bx_,
+                                             float by_, float bz_, float lo2, float nn2, bool row0, float xi0,
+                                             float xi1, float xi2, float xj0, float xj1, float xj2, float ft0,
+                                             float ft1, unsigned long long &nre) {
+    unsigned bits = 0u, band = 0u;
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+        const float ft2 = __fadd_rn(lo2, (float)q);
+        const float vx = __fmaf_rn(ft2, P.L[6], bx_);
+        const float vy = __fmaf_rn(ft2, P.L[7], by_);
+        const float vz = __fmaf_rn(ft2, P.L[8], bz_);
+        const float d2 = __fmaf_rn(vz, vz, __fmaf_rn(vy, vy, __fmul_rn(vx, vx)));
+        const bool valid = (float)q < nn2;
+        bits |= (valid && d2 < P.thr_lo) ? (1u << q) : 0u;
+        band |= (valid && d2 >= P.thr_lo && d2 <= P.thr_hi) ? (1u << q) : 0u;
+    }
+    while (band) {  // the band: canonical FP64 distance decides (rare)
+        const int q = __ffs(band) - 1;
+        band &= band - 1;
+        if (band_is_edge(rec, xi0, xi1, xi2, xj0, xj1, xj2, ft0, ft1, __fadd_rn(lo2, (float)q))) bits |= 1u << q;
+        ++nre;
+    }
+    if (row0 && lo2 <= 0.0f && -lo2 < nn2) bits &= ~(1u << (int)(-lo2));  // not (i, i, 0)
+    return bits;
+}
+
+// U beyond the unrolled sizes: the same cells in a loop.
+__device__ __forceinline__ unsigned row_bits_loop(const PairStruct &P, const StructRec *__restrict__ rec, float bx_,
+                                                  float by_, float bz_, float lo2, float nn2, bool row0, float xi0,
+                                                  float xi1, float xi2, float xj0, float xj1, float xj2, float ft0,
+                                                  float ft1, unsigned long long &nre, unsigned long long &hi_bits) {
+    unsigned long long bits = 0ull;
+    int q = 0;
+    for (float ft2 = lo2; ft2 < lo2 + nn2; ft2 += 1.0f, ++q) {
+        const float vx = __fmaf_rn(ft2, P.L[6], bx_);
+        const float vy = __fmaf_rn(ft2, P.L[7], by_);
+        const float vz = __fmaf_rn(ft2, P.L[8], bz_);
+        const float d2 = __fmaf_rn(vz, vz, __fmaf_rn(vy, vy, __fmul_rn(vx, vx)));
+        bool in = d2 < P.thr_lo;
+        if (!in && d2 <= P.thr_hi) {
+            in = band_is_edge(rec, xi0, xi1, xi2, xj0, xj1, xj2, ft0, ft1, ft2);
+            ++nre;
+        }
+        if (in && !(row0 && ft2 == 0.0f)) bits |= 1ull << q;
+    }
+    hi_bits = bits;
+    return (unsigned)bits;
+}
+
+// The pair's box and the mask of its edges: rows (t0, t1) in order as one flat loop (a
+// warp runs as many rows as its busiest lane), bit position = row * nn2 + q.
+template <int U>
+__device__ __forceinline__ unsigned long long pair_box_mask(const PairStruct &P, const StructRec *__restrict__ rec,
+                                                            bool ok, int i_loc, int j_loc, float xi0, float xi1,
+                                                            float xi2, float3 pi, float xj0, float xj1, float xj2,
+                                                            float4 pj, PairBox &bx, mg_device_status_t *status,
+                                                            unsigned long long &nre) {
+    pair_box(P, ok, xi0, xi1, xi2, xj0, xj1, xj2, bx);
+    if (bx.nn[0] * bx.nn[1] * bx.nn[2] > (float)PL_BOX_MAX || (U > 0 && bx.nn[2] > (float)U)) {
+        set_error(status, MG_ERR_INTERNAL, -1);
+        bx.nn[0] = 0.0f;
+    }
+    const float ax = __fsub_rn(pj.x, pi.x), ay = __fsub_rn(pj.y, pi.y), az = __fsub_rn(pj.z, pi.z);
+    const bool same = i_loc == j_loc;
+    const int rows = (int)(bx.nn[0] * bx.nn[1]);
+    const int n2 = (int)bx.nn[2];
+    const float e1 = bx.lo[1] + bx.nn[1];
+    unsigned long long mask = 0ull;
+    float ft0 = bx.lo[0], ft1 = bx.lo[1];
+    int shift = 0;
+    for (int r = 0; r < rows; ++r, shift += n2) {
+        // row base b = a + t0 L0 + t1 L1, then v = b + t2 L2
+        const float bx_ = __fmaf_rn(ft1, P.L[3], __fmaf_rn(ft0, P.L[0], ax));
+        const float by_ = __fmaf_rn(ft1, P.L[4], __fmaf_rn(ft0, P.L[1], ay));
+        const float bz_ = __fmaf_rn(ft1, P.L[5], __fmaf_rn(ft0, P.L[2], az));
+        const bool row0 = same && ft0 == 0.0f && ft1 == 0.0f;
+        if (U > 0) {
+            const unsigned b = row_bits<(U > 0 ? U : 1)>(P, rec, bx_, by_, bz_, bx.lo[2], bx.nn[2], row0, xi0, xi1,
+                                                          xi2, xj0, xj1, xj2, ft0, ft1, nre);
+            mask |= (unsigned long long)b << shift;
+        } else {
+            unsigned long long b64;
+            row_bits_loop(P, rec, bx_, by_, bz_, bx.lo[2], bx.nn[2], row0, xi0, xi1, xi2, xj0, xj1, xj2, ft0, ft1,
+                          nre, b64);
+            mask |= b64 << shift;
+        }
+        ft1 += 1.0f;
+        if (ft1 >= e1) {
+            ft1 = bx.lo[1];
+            ft0 += 1.0f;
+        }
+    }
+    return mask;
+}
+
+// A pair's box as one word: lo_k + 512 in 10 bits each, then nn_k in 7 bits each.
+__device__ __forceinline__ unsigned long long pack_box(const PairBox &bx) {
+    return (unsigned long long)pack_t((int)bx.lo[0], (int)bx.lo[1], (int)bx.lo[2]) |
+           ((unsigned long long)((unsigned)bx.nn[0] | ((unsigned)bx.nn[1] << 7) | ((unsigned)bx.nn[2] << 14)) << 30);
+}
+
+// The next work item of this warp's pass (queue word `which`), or -1 when the list is done.
+__device__ __forceinline__ int next_item(unsigned int *queue, int which, int total) {
+    unsigned int v = 0;
+    if (lane_id() == 0) v = atomicAdd(&queue[which], 1u);
+    v = __shfl_sync(FULL, v, 0);
+    return (int)v < total ? (int)v : -1;
+}
+
+// Structures outside the pair-lane scan: one source by the warp enumeration (an unusable
+// structure reports its error at its first atom and counts zero), its keys staged in
+// shared memory and then copied to the staging area at a slot taken with one atomic add
+// (-1: the keys did not fit, and the spill kernel enumerates the source again).
+__device__ __forceinline__ void warp_source_stage(const BuildArgs &a, const Work &w, int i, unsigned long long *keys) {
+    const int lane = lane_id();
+    SrcScan c;
+    int m = 0;
+    bool spill = false;
+    if (source_setup<false>(a, w, i, c)) m = scan_source<false>(a, w, c, keys, nullptr, spill);
+    long long off = -1;
+    if (!spill && m > 0) {
+        if (lane == 0) off = (long long)atomicAdd(w.stage_ctr, (unsigned long long)m);
+        off = __shfl_sync(FULL, off, 0);
+        if (off + m <= w.max_edges) {
+            for (int q = lane; q < m; q += 32) w.stage[off + q] = keys[q];
+        } else {
+            spill = true;  // staging area full (more edges than the workspace covers)
+            if (a.write_pairs && lane == 0) w.pair_ok[c.s] = 0;
+        }
+    }
+    if (lane == 0) {
+        w.cnt[i] = m;
+        w.stage_off[i] = spill ? -1 : off;
+    }
+    __syncwarp();
+}
+
+// ============================================================================ stage pass
+
+// The warp-enumeration items (the front of the work list), one source each.
+__global__ void __launch_bounds__(PAIR_WARPS * 32, 2) pair_legacy_kernel(const __grid_constant__ BuildArgs a,
+                                                                          const __grid_constant__ Work w) {
+    __shared__ unsigned long long keys_all[PAIR_WARPS][BUILD_CAP];
+    unsigned long long *keys = keys_all[threadIdx.x >> 5];
+    const int total = (int)w.queue[9];
+    for (int it = next_item(w.queue, 6, total); it >= 0; it = next_item(w.queue, 6, total)) {
+        const int2 item = w.items[it];
+        warp_source_stage(a, w, w.recs[item.x].atom_begin + item.y, keys);
+    }
+}
+
+constexpr int MASK_CHUNKS = PL_MAX_ATOMS / 32;  // target chunks of a source: masks and boxes kept in shared memory
+
+// Phase 1 of a pair-lane item: every chunk of G targets, each lane's pair mask and packed
+// box into shared memory; returns the lane's edge count and the number of chunks.
+template <int U>
+__device__ __forceinline__ int pair_masks(const PairStruct &P, const StructRec *__restrict__ rec, const BuildArgs &a,
+                                          const Work &w, int jg, int i_loc, bool src_ok, float xi0, float xi1,
+                                          float xi2, float3 pi, unsigned long long *buf, unsigned long long *boxes,
+                                          int &nchunks, unsigned long long &nre, unsigned long long &ncand) {
+    const int lane = lane_id();
+    int cnt = 0;
+    nchunks = 0;
+    for (int jb = 0; jb < P.n; jb += P.G, ++nchunks) {
+        const int j_loc = jb + jg;
+        const bool ok = src_ok && j_loc < P.n;
+        const int64_t jr = (int64_t)P.begin + (ok ? j_loc : 0);
+        PairBox bx;
+        const unsigned long long mask =
+            pair_box_mask<U>(P, rec, ok, i_loc, j_loc, xi0, xi1, xi2, pi, a.frac[3 * jr], a.frac[3 * jr + 1],
+                             a.frac[3 * jr + 2], w.pos[jr], bx, a.g.status, nre);
+        buf[32 * nchunks + lane] = mask;
+        boxes[32 * nchunks + lane] = mask ? pack_box(bx) : 0ull;
+        cnt += __popcll(mask);
+        if (a.collect_stats) ncand += (unsigned long long)(bx.nn[0] * bx.nn[1] * bx.nn[2]);
+    }
+    return cnt;
+}
+
+// A persistent grid pulls the work items.  A pair-lane item: every lane evaluates its
+// pair's box for each target chunk (mask and box kept in shared memory), each source's
+// count is summed over its lanes, the item's keys take one slot range of the staging
+// area (one atomic add), and every lane writes its pairs' keys there at their canonical
+// positions: the source's start, plus its edges in earlier chunks, plus the edges of
+// the pairs before it in this chunk.  cnt[i] and stage_off[i] go to every source, as
+// from the staged build, whose count scan and emit kernel finish the graph.
+__global__ void __launch_bounds__(PAIR_WARPS * 32, 6) pair_stage_kernel(const __grid_constant__ BuildArgs a,
+                                                                         const __grid_constant__ Work w) {
+    __shared__ unsigned long long buf_all[PAIR_WARPS][BUILD_CAP];  // legacy keys, or pair masks and boxes
+    static_assert(2 * 32 * MASK_CHUNKS <= BUILD_CAP, "mask buffer");
+    const int wid = threadIdx.x >> 5, lane = lane_id();
+    unsigned long long *buf = buf_all[wid];
+    unsigned long long *boxes = buf + 32 * MASK_CHUNKS;
+    const int first = (int)w.queue[9], total = (int)w.queue[8] - first;
+    unsigned long long nre = 0, ncand = 0;
+    for (int it = next_item(w.queue, 7, total); it >= 0; it = next_item(w.queue, 7, total)) {
+        const int2 item = w.items[first + it];
+        const StructRec &R = w.recs[item.x];
+        PairStruct P;
+        load_pair_struct(P, R);
+        const int G = P.G;
+        const int g = lane / G, jg = lane % G;
+        const int i_loc = item.y * P.spw + g;
+        const bool src_ok = i_loc < P.n;
+        const int64_t ir = (int64_t)P.begin + (src_ok ? i_loc : 0);
+        const float xi0 = a.frac[3 * ir], xi1 = a.frac[3 * ir + 1], xi2 = a.frac[3 * ir + 2];
+        const float4 pi4 = w.pos[ir];
+        const float3 pi = make_float3(pi4.x, pi4.y, pi4.z);
+        // ---- masks and counts (at most MASK_CHUNKS chunks: n <= PL_MAX_ATOMS), the cells
+        // along L_2 unrolled to the structure's extent
+        int cnt = 0, nchunks = 0;
+#define MG_PAIR_MASKS(U_)                                                                                    \
+    cnt = pair_masks<U_>(P, &R, a, w, jg, i_loc, src_ok, xi0, xi1, xi2, pi, buf, boxes, nchunks, nre, ncand)
+        switch (R.pl) {
+        case 1: MG_PAIR_MASKS(1); break;
+        case 2: MG_PAIR_MASKS(2); break;
+        case 3: MG_PAIR_MASKS(3); break;
+        case 4: MG_PAIR_MASKS(4); break;
+        case 5: MG_PAIR_MASKS(5); break;
+        case 6: MG_PAIR_MASKS(6); break;
+        case 7: MG_PAIR_MASKS(7); break;
+        case 8: MG_PAIR_MASKS(8); break;
+        default: MG_PAIR_MASKS(0); break;
+        }
+#undef MG_PAIR_MASKS
+        // ---- one slot range for the item; each source's start within it
+        const int incl = warp_incl_scan(cnt);
+        const int T = __shfl_sync(FULL, incl, 31);
+        const int lead = g * G;
+        const int src_first = __shfl_sync(FULL, incl - cnt, lead);  // edges of earlier sources
+        const int src_count = __shfl_sync(FULL, incl, lead + G - 1) - src_first;
+        long long off = 0;
+        if (lane == 0 && T > 0) off = (long long)atomicAdd(w.stage_ctr, (unsigned long long)T);
+        off = __shfl_sync(FULL, off, 0);
+        const bool spill = off + T > w.max_edges;  // staging area full: the spill kernel takes them
+        if (jg == 0 && src_ok) {
+            w.cnt[ir] = src_count;
+            w.stage_off[ir] = spill ? -1ll : off + src_first;
+        }
+        if (spill) {
+            if (a.write_pairs && lane == 0 && T > 0) w.pair_ok[item.x] = 0;
+            __syncwarp();
+            continue;
+        }
+        // ---- keys at their canonical positions, from the stored masks and boxes
+        long long pos_src = off + src_first;  // this lane's source: its next free slot
+        const long long item_end = off + T;
+        __syncwarp();
+        for (int c = 0; c < nchunks; ++c) {
+            unsigned long long mask = buf[32 * c + lane];
+            const unsigned long long bw = boxes[32 * c + lane];
+            const int m = __popcll(mask);
+            const int ci = warp_incl_scan(m);
+            const int cfirst = __shfl_sync(FULL, ci - m, lead);
+            const int ccount = __shfl_sync(FULL, ci, lead + G - 1) - cfirst;
+            long long p = pos_src + (ci - m - cfirst);
+            const unsigned long long jkey = (unsigned long long)(unsigned)(c * G + jg) << 32;
+            int t0, t1, t2l;
+            unpack_t((uint32_t)(bw & 0x3fffffffull), t0, t1, t2l);
+            const int n0 = (int)((bw >> 30) & 127u), n1 = (int)((bw >> 37) & 127u), n2 = (int)((bw >> 44) & 127u);
+            // walk the box in offset order, one key per set bit
+            for (int q0 = 0; q0 < n0 && mask; ++q0, ++t0) {
+                int tt1 = t1;
+                for (int q1 = 0; q1 < n1 && mask; ++q1, ++tt1) {
+                    int t2 = t2l;
+                    for (int q2 = 0; q2 < n2; ++q2, ++t2, mask >>= 1)
+                        if ((mask & 1ull) && p < item_end) w.stage[p++] = jkey | pack_t(t0, tt1, t2);
+                }
+            }
+            pos_src += ccount;
+        }
+        __syncwarp();
+    }
+    if (a.collect_stats) {
+        nre = warp_sum(nre);
+        ncand = warp_sum(ncand);
+        if (lane == 0 && ncand) {
+            Status *st = reinterpret_cast<Status *>(a.g.status);
+            atomicAdd(&st->rechecked, nre);
+            atomicAdd(&st->candidates, ncand);
+        }
+    }
+}
+
+// ============================================================================ launch
+
+static int g_pair_blocks = 0;  // resident blocks per SM of the stage pass
+
+cudaError_t launch_pair_plan(const BuildArgs &a, const Work &w, cudaStream_t s) {
+    pair_plan_kernel<<<1, PLAN_THREADS, 0, s>>>(a.B, w.plan_items, w.plan_class, w.item_base, w.queue);
+    pair_fill_kernel<<<(a.B + 7) / 8, 256, 0, s>>>(a.B, w.plan_items, w.item_base, w.items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_stage(const BuildArgs &a, const Work &w, cudaStream_t s) {
+    if (a.N <= 0) return cudaSuccess;
+    if (!g_pair_blocks) {
+        int c = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, pair_stage_kernel, PAIR_WARPS * 32, 0);
+        g_pair_blocks = max(1, c);
+    }
+    // persistent grids; never more warps than sources (items never outnumber them).  The
+    // warp-enumeration items are usually few: two blocks per SM pull them.
+    const int cap = (a.N + PAIR_WARPS - 1) / PAIR_WARPS;
+    pair_legacy_kernel<<<max(1, min(cap, 2 * num_sms())), PAIR_WARPS * 32, 0, s>>>(a, w);
+    pair_stage_kernel<<<max(1, min(cap, g_pair_blocks * num_sms())), PAIR_WARPS * 32, 0, s>>>(a, w);
+    return cudaGetLastError();
+}
+
+}  // namespace mg

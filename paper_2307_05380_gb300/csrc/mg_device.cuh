@@ -35,8 +35,16 @@ struct StructRec {
     int32_t nb[3];     // cell-list bins per axis; nb[0] == 0: the structure uses all pairs
     int32_t bin_base;  // first bin of the structure: atom_begin + structure index
     int32_t ax;        // lattice axis the cutoff scan runs its candidates along (2: none moved)
+    int32_t pl;        // > 0: every (source, target) pair's offset box holds at most
+                       // PL_BOX_MAX cells and its offsets fit the packed key (pair-lane
+                       // scan); the value bounds a pair's box extent along L_2
+    float reach[3];    // pair-lane scan: c / d_k plus the structure's margin; a pair's box
+                       // along axis k is ceil(-reach_k - dx_k) .. floor(reach_k - dx_k)
 };
-static_assert(sizeof(StructRec) == 144, "record layout");
+static_assert(sizeof(StructRec) == 160, "record layout");
+
+constexpr int PL_BOX_MAX = 64;  // offset-box cells one lane evaluates for its pair (a 64-bit mask)
+constexpr int PL_MAX_ATOMS = 512;  // largest structure of the pair-lane scan (16 chunks of 32 targets)
 
 constexpr int CELL_MIN_ATOMS = 128;  // smallest structure that may use a cell list
 constexpr int WRITE_CAP = 1024;      // edges of one source sorted in shared memory

@@ -39,6 +39,10 @@ struct Work {
     uint16_t *pair_hi;        //   one-past-last position (structures of <= PAIR_MAX atoms)
     int32_t *pair_ok;         // [B] 1: the pair table of the structure is complete
     int32_t *lat_cnt;         // [B] atoms of the structure whose lattice partial is stored
+    int2 *items;              // [N] pair-lane build: work items (structure, item within it)
+    int32_t *plan_items;      // [B] work items of each structure
+    int32_t *plan_class;      // [B] cost class of each structure's items
+    int32_t *item_base;       // [B] first slot of each structure's items in `items`
     int64_t max_edges;
 };
 
@@ -64,6 +68,8 @@ struct PrepArgs {
     const float *cutoff_atom = nullptr;  // per-atom radii [N]: the structure's reach is their maximum
     int32_t *pair_ok = nullptr;          // [B] set to (n <= PAIR_MAX) when a pair table is written
     int32_t *lat_cnt = nullptr;          // [B] zeroed with the pair table (backward's counters)
+    int32_t *plan_items = nullptr;       // [B] pair-lane build: work items of each structure
+    int32_t *plan_class = nullptr;       // [B] pair-lane build: cost class of its items (0..31)
 };
 
 cudaError_t launch_prep(const PrepArgs &a, const Work &w, cudaStream_t s);
@@ -106,6 +112,13 @@ struct BuildArgs {
                                        // stream serialization (it directly follows prep)
 };
 
+// Pair-lane cutoff build (batched, constant radius): a cost-sorted work list of the
+// structures' source groups (plan: 2 launches), then a stage pass over the list that
+// counts every source and stages its keys like the staged build's stage kernel; the
+// staged build's count scan and emit finish it.  Structures whose pair boxes are too
+// large or that use a cell list are scanned by the warp enumeration inside the pass.
+cudaError_t launch_pair_plan(const BuildArgs &a, const Work &w, cudaStream_t s);
+cudaError_t launch_pair_stage(const BuildArgs &a, const Work &w, cudaStream_t s);
 // One-pass cutoff build (batched): scan once, stage keys, look-back offsets, write.
 cudaError_t launch_cutoff_build(const BuildArgs &a, const Work &w, cudaStream_t s);
 // Staged cutoff build: scan and stage keys globally (stage), scan the counts and write

@@ -358,6 +358,91 @@ def test_bad_inputs_reported_on_device():
     assert E0 == len(want["src"])
 
 
+# ------------------------------------------------------------------ pair-lane build
+
+def pair_opts(**kw):
+    return mg.make_opts(schedule=5, **kw)
+
+
+def test_pair_lane_build_small_batches_against_the_oracle():
+    """The pair-lane build (work list, count pass, scan, write pass) forced on the
+    16- and 256-structure workloads and on the edge cases (one-atom cells, a 25 degree
+    skew, unwrapped coordinates, a long cell, an empty structure): edges, pointers,
+    vectors and destination order against the oracle."""
+    for b, r in ((synth.make_batch(1), 5.0), (synth.make_batch(2), 6.0), (edge_case_batch(), 3.0),
+                 (edge_case_batch(), 5.5)):
+        cutoff_parity(b, r, opts=pair_opts())
+
+
+def test_pair_lane_build_with_warp_enumerated_structures():
+    """Structures outside the pair-lane scan (cell lists, boxes of more than 64 cells,
+    a source with more than 1024 edges) are scanned by the warp enumeration inside the
+    pair-lane passes, next to pair-lane structures."""
+    b = synth.concat([cell_list_batch(), synth.crystal(np.eye(3), [[0.1, 0.2, 0.3]]), synth.make_batch(2, B=16)])
+    for r in (2.5, 4.0):
+        cutoff_parity(b, r, opts=pair_opts())
+    cutoff_parity(b, 7.3, opts=pair_opts())  # the unit cube's source: ~1600 edges, re-enumerated
+
+
+@pytest.mark.parametrize("r", [4.0, 6.0, 8.0])
+def test_pair_lane_build_identical_to_staged_build_8192_structures(r):
+    """The 8192-structure mixture (skewed cells included) at every radius of the
+    workload: the pair-lane build (the default there) and the staged build give the same
+    arrays bit for bit, destination order included; the staged build is checked against
+    the oracle edge by edge elsewhere, and here sampled structures are too."""
+    b = synth.make_batch(3)
+    batch = to_device(b)
+    pair = graph_arrays(mg.cutoff_graph(batch, r, opts=pair_opts()))
+    staged = graph_arrays(mg.cutoff_graph(batch, r, opts=mg.make_opts(schedule=4)))
+    assert pair.keys() == staged.keys()
+    for key in staged:
+        np.testing.assert_array_equal(pair[key], staged[key], err_msg=key)
+    rng = np.random.default_rng(100 + int(r))
+    for s in sorted(rng.choice(b.num_structures, 16, replace=False).tolist()):
+        lo, hi = pair["edge_ptr"][s], pair["edge_ptr"][s + 1]
+        sub = b.subset([s])
+        part = {key: pair[key][lo:hi] for key in ("src", "dst", "offset")}
+        part["src"] = part["src"] - b.atom_ptr[s]
+        part["dst"] = part["dst"] - b.atom_ptr[s]
+        assert_same_edges(part, oracle.cutoff(sub.lattice, sub.frac, sub.atom_ptr, r), f"structure {s}")
+
+
+def test_pair_lane_build_capacity_bad_inputs_and_gradient():
+    """Too small a capacity: MG_ERR_CAPACITY with the exact requirement, nothing written;
+    a singular and a non-finite structure reported while the others are built; the
+    gradient through the pair table the write pass records, against the oracle."""
+    b = synth.make_batch(4, B=256)
+    batch = to_device(b)
+    want = oracle.cutoff(b.lattice, b.frac, b.atom_ptr, 5.0)
+    g = mg.cutoff_graph(batch, 5.0, capacity=1000, opts=pair_opts(), sync=False)
+    st = g.read_status()
+    assert st["code"] == 4 and st["required_capacity"] == len(want["src"]), st
+    g = mg.cutoff_graph(batch, 5.0, opts=pair_opts(), with_perm=False)
+    got = graph_arrays(g)
+    assert_same_edges(got, want, "pair-lane, 256 structures")
+    pointers_ok(got, b)
+    grad_check(b, g, synth.normal(8, 1, g.num_edges), c=synth.normal(8, 2, 3 * g.num_edges).reshape(-1, 3))
+    lat = b.lattice.copy()
+    lat[3] = 0.0
+    frac = b.frac.copy()
+    frac[b.atom_ptr[7] + 1] = np.inf
+    gb = mg.cutoff_graph(to_device(synth.Batch(lat, frac, b.atom_ptr)), 5.0, opts=pair_opts(), sync=False)
+    st = gb.read_status()
+    assert st["code"] in (2, 3) and st["first_bad_structure"] == 3, st
+    ep = gb.edge_ptr.cpu().numpy()
+    assert ep[4] - ep[3] == 0 and ep[8] - ep[7] == 0
+    for s in (0, 5, 9):
+        assert ep[s + 1] - ep[s] == int(np.sum((want["src"] >= b.atom_ptr[s]) & (want["src"] < b.atom_ptr[s + 1])))
+
+
+def test_pair_lane_build_stats():
+    b = synth.make_batch(3, B=512)
+    g = mg.cutoff_graph(to_device(b), 6.0, opts=pair_opts(collect_stats=True))
+    st = g.last_status
+    assert st["candidates"] >= g.num_edges > 0
+    assert 0 <= st["rechecked"] < st["candidates"] * 1e-2
+
+
 # ------------------------------------------------------------------ schedules, per-structure, update
 
 def test_schedules_and_per_structure_identical():
