@@ -248,7 +248,8 @@ __global__ void __launch_bounds__(GROUP == 32 ? 128 : GROUP) prep_kernel(PrepArg
             box[k] = fits ? (int)ext : 0;
             prod *= fits ? (int)ext : 1;
         }
-        R.pl = (fits && prod <= PL_BOX_MAX) ? box[2] : 0;
+        // a row's cells fit one word; the extents, B2 | B1 << 8 | B0 << 16, are the mask's strides
+        R.pl = (fits && prod <= PL_BOX_MAX && box[2] <= 32) ? box[2] | (box[1] << 8) | (box[0] << 16) : 0;
     }
     if (a.plan_items) {
         // work items and their cost class: a pair-lane structure is split into groups of

@@ -81,6 +81,7 @@ struct PairStruct {
     double rr;            // canonical squared cutoff
     int begin, n;
     int G, spw;           // lanes per source, sources per warp
+    int B1, B2;           // largest box extents along L_1 and L_2: the strides of a pair's mask
 };
 
 __device__ __forceinline__ void load_pair_struct(PairStruct &P, const StructRec &R) {
@@ -97,6 +98,8 @@ __device__ __forceinline__ void load_pair_struct(PairStruct &P, const StructRec 
     while (G < P.n && G < 32) G <<= 1;
     P.G = G;
     P.spw = 32 / G;
+    P.B2 = R.pl & 255;
+    P.B1 = (R.pl >> 8) & 255;
 }
 
 // The canonical FP64 test of one candidate in the band, out of line: inlined, the
@@ -120,27 +123,42 @@ struct PairBox {
     float lo[3], nn[3];
 };
 
+// Small integers in floats by exponent alignment (adding 1.5 * 2^23 moves the value's
+// integer part into the low mantissa bits, rounded to nearest): exact for |v| < 2^22.
+// Conversions and float rounding to integers run on a low-rate pipe of this GPU; these
+// use additions and compares only.
+__device__ __forceinline__ float frnd(float v) { return __fsub_rn(__fadd_rn(v, 12582912.0f), 12582912.0f); }
+__device__ __forceinline__ float ffloor(float v) {
+    const float r = frnd(v);
+    return r > v ? __fsub_rn(r, 1.0f) : r;
+}
+__device__ __forceinline__ float fceil(float v) {
+    const float r = frnd(v);
+    return r < v ? __fadd_rn(r, 1.0f) : r;
+}
+__device__ __forceinline__ int fint(float v) { return __float_as_int(__fadd_rn(v, 12582912.0f)) - 0x4B400000; }
+
 __device__ __forceinline__ void pair_box(const PairStruct &P, bool ok, float xi0, float xi1, float xi2, float xj0,
                                          float xj1, float xj2, PairBox &bx) {
     const float dx[3] = {__fsub_rn(xj0, xi0), __fsub_rn(xj1, xi1), __fsub_rn(xj2, xi2)};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        bx.lo[k] = ceilf(__fsub_rn(-P.reach[k], dx[k]));
-        const float hi = floorf(__fsub_rn(P.reach[k], dx[k]));
+        bx.lo[k] = fceil(__fsub_rn(-P.reach[k], dx[k]));
+        const float hi = ffloor(__fsub_rn(P.reach[k], dx[k]));
         bx.nn[k] = ok ? fmaxf(0.0f, __fadd_rn(__fsub_rn(hi, bx.lo[k]), 1.0f)) : 0.0f;
     }
 }
 
-// The cells of one row (t0, t1) of a pair's box: U offsets t2 = lo2 + q, q < nn2 (U the
-// structure's largest extent along L_2, so every lane unrolls the same code), FP32
-// distances from the row base b, then the edges' bits (bit q) with the band's candidates
-// decided by the canonical FP64 test and (i, i, 0) left out.
+
+// The cells of one row (t0, t1) of a pair's box: U offsets t2 = lo2 + q (U the
+// structure's largest extent along L_2, so every lane runs the same unrolled code), FP32
+// distances from the row base b.  Returns the bits of the cells certainly inside and
+// sets `le` to the bits of those at most at the band's upper threshold; cells past the
+// pair's extent are masked by the caller.
 template <int U>
-__device__ __forceinline__ unsigned row_bits(const PairStruct &P, const StructRec *__restrict__ rec, float bx_,
-                                             float by_, float bz_, float lo2, float nn2, bool row0, float xi0,
-                                             float xi1, float xi2, float xj0, float xj1, float xj2, float ft0,
-                                             float ft1, unsigned long long &nre) {
-    unsigned bits = 0u, band = 0u;
+__device__ __forceinline__ unsigned row_cells(const PairStruct &P, float bx_, float by_, float bz_, float lo2,
+                                              unsigned &le) {
+    unsigned in = 0u, lo_hi = 0u;
 #pragma unroll
     for (int q = 0; q < U; ++q) {
         const float ft2 = __fadd_rn(lo2, (float)q);
@@ -148,45 +166,35 @@ __device__ __forceinline__ unsigned row_bits(const PairStruct &P, const StructRe
         const float vy = __fmaf_rn(ft2, P.L[7], by_);
         const float vz = __fmaf_rn(ft2, P.L[8], bz_);
         const float d2 = __fmaf_rn(vz, vz, __fmaf_rn(vy, vy, __fmul_rn(vx, vx)));
-        const bool valid = (float)q < nn2;
-        bits |= (valid && d2 < P.thr_lo) ? (1u << q) : 0u;
-        band |= (valid && d2 >= P.thr_lo && d2 <= P.thr_hi) ? (1u << q) : 0u;
+        if (d2 < P.thr_lo) in |= 1u << q;
+        if (d2 <= P.thr_hi) lo_hi |= 1u << q;
     }
-    while (band) {  // the band: canonical FP64 distance decides (rare)
-        const int q = __ffs(band) - 1;
-        band &= band - 1;
-        if (band_is_edge(rec, xi0, xi1, xi2, xj0, xj1, xj2, ft0, ft1, __fadd_rn(lo2, (float)q))) bits |= 1u << q;
-        ++nre;
-    }
-    if (row0 && lo2 <= 0.0f && -lo2 < nn2) bits &= ~(1u << (int)(-lo2));  // not (i, i, 0)
-    return bits;
+    le = lo_hi;
+    return in;
 }
 
-// U beyond the unrolled sizes: the same cells in a loop.
-__device__ __forceinline__ unsigned row_bits_loop(const PairStruct &P, const StructRec *__restrict__ rec, float bx_,
-                                                  float by_, float bz_, float lo2, float nn2, bool row0, float xi0,
-                                                  float xi1, float xi2, float xj0, float xj1, float xj2, float ft0,
-                                                  float ft1, unsigned long long &nre, unsigned long long &hi_bits) {
-    unsigned long long bits = 0ull;
-    int q = 0;
-    for (float ft2 = lo2; ft2 < lo2 + nn2; ft2 += 1.0f, ++q) {
+// U beyond the unrolled sizes: the same cells in a loop (up to 32 cells per row).
+__device__ __forceinline__ unsigned row_cells_loop(const PairStruct &P, float bx_, float by_, float bz_, float lo2,
+                                                   int n2, unsigned &le) {
+    unsigned in = 0u, lo_hi = 0u;
+    float ft2 = lo2;
+    for (int q = 0; q < n2; ++q, ft2 = __fadd_rn(ft2, 1.0f)) {
         const float vx = __fmaf_rn(ft2, P.L[6], bx_);
         const float vy = __fmaf_rn(ft2, P.L[7], by_);
         const float vz = __fmaf_rn(ft2, P.L[8], bz_);
         const float d2 = __fmaf_rn(vz, vz, __fmaf_rn(vy, vy, __fmul_rn(vx, vx)));
-        bool in = d2 < P.thr_lo;
-        if (!in && d2 <= P.thr_hi) {
-            in = band_is_edge(rec, xi0, xi1, xi2, xj0, xj1, xj2, ft0, ft1, ft2);
-            ++nre;
-        }
-        if (in && !(row0 && ft2 == 0.0f)) bits |= 1ull << q;
+        if (d2 < P.thr_lo) in |= 1u << q;
+        if (d2 <= P.thr_hi) lo_hi |= 1u << q;
     }
-    hi_bits = bits;
-    return (unsigned)bits;
+    le = lo_hi;
+    return in;
 }
 
 // The pair's box and the mask of its edges: rows (t0, t1) in order as one flat loop (a
-// warp runs as many rows as its busiest lane), bit position = row * nn2 + q.
+// warp runs as many rows as its busiest lane); the cell lo + (q0, q1, q2) is bit
+// (q0 B1 + q1) B2 + q2, with the structure's largest extents as strides, so that the
+// decode divides by warp-uniform numbers.  Cells in the band take the canonical FP64
+// test (rare); the source's own cell (i, i, 0) is cleared once per pair.
 template <int U>
 __device__ __forceinline__ unsigned long long pair_box_mask(const PairStruct &P, const StructRec *__restrict__ rec,
                                                             bool ok, int i_loc, int j_loc, float xi0, float xi1,
@@ -194,47 +202,59 @@ __device__ __forceinline__ unsigned long long pair_box_mask(const PairStruct &P,
                                                             float4 pj, PairBox &bx, mg_device_status_t *status,
                                                             unsigned long long &nre) {
     pair_box(P, ok, xi0, xi1, xi2, xj0, xj1, xj2, bx);
-    if (bx.nn[0] * bx.nn[1] * bx.nn[2] > (float)PL_BOX_MAX || (U > 0 && bx.nn[2] > (float)U)) {
+    // more cells than the mask holds, or a row longer than the unrolled code: cannot
+    // happen for a pair-lane structure (its record bounds them)
+    const int B2 = U > 0 ? U : P.B2, B1 = P.B1;
+    if (bx.nn[2] > (float)B2 || bx.nn[1] > (float)B1 || __fmul_rn(bx.nn[0], (float)(B1 * B2)) > (float)PL_BOX_MAX) {
         set_error(status, MG_ERR_INTERNAL, -1);
         bx.nn[0] = 0.0f;
     }
     const float ax = __fsub_rn(pj.x, pi.x), ay = __fsub_rn(pj.y, pi.y), az = __fsub_rn(pj.z, pi.z);
-    const bool same = i_loc == j_loc;
-    const int rows = (int)(bx.nn[0] * bx.nn[1]);
-    const int n2 = (int)bx.nn[2];
-    const float e1 = bx.lo[1] + bx.nn[1];
+    const int n2 = fint(bx.nn[2]);
+    const unsigned rowmask = n2 >= 32 ? ~0u : (1u << n2) - 1u;
+    const float rows = __fmul_rn(bx.nn[0], bx.nn[1]);
+    const float e1 = __fadd_rn(bx.lo[1], bx.nn[1]);
+    const int skip = (B1 - fint(bx.nn[1])) * B2;  // stride from a row's end to the next t0
     unsigned long long mask = 0ull;
     float ft0 = bx.lo[0], ft1 = bx.lo[1];
     int shift = 0;
-    for (int r = 0; r < rows; ++r, shift += n2) {
+    for (float r = 0.0f; r < rows; r = __fadd_rn(r, 1.0f), shift += B2) {
         // row base b = a + t0 L0 + t1 L1, then v = b + t2 L2
         const float bx_ = __fmaf_rn(ft1, P.L[3], __fmaf_rn(ft0, P.L[0], ax));
         const float by_ = __fmaf_rn(ft1, P.L[4], __fmaf_rn(ft0, P.L[1], ay));
         const float bz_ = __fmaf_rn(ft1, P.L[5], __fmaf_rn(ft0, P.L[2], az));
-        const bool row0 = same && ft0 == 0.0f && ft1 == 0.0f;
-        if (U > 0) {
-            const unsigned b = row_bits<(U > 0 ? U : 1)>(P, rec, bx_, by_, bz_, bx.lo[2], bx.nn[2], row0, xi0, xi1,
-                                                          xi2, xj0, xj1, xj2, ft0, ft1, nre);
-            mask |= (unsigned long long)b << shift;
-        } else {
-            unsigned long long b64;
-            row_bits_loop(P, rec, bx_, by_, bz_, bx.lo[2], bx.nn[2], row0, xi0, xi1, xi2, xj0, xj1, xj2, ft0, ft1,
-                          nre, b64);
-            mask |= b64 << shift;
+        unsigned le;
+        unsigned in = U > 0 ? row_cells<(U > 0 ? U : 1)>(P, bx_, by_, bz_, bx.lo[2], le)
+                            : row_cells_loop(P, bx_, by_, bz_, bx.lo[2], n2, le);
+        in &= rowmask;
+        unsigned band = (le & rowmask) & ~in;
+        while (band) {  // the band: canonical FP64 distance decides
+            const int q = __ffs(band) - 1;
+            band &= band - 1;
+            if (band_is_edge(rec, xi0, xi1, xi2, xj0, xj1, xj2, ft0, ft1, __fadd_rn(bx.lo[2], (float)q)))
+                in |= 1u << q;
+            ++nre;
         }
-        ft1 += 1.0f;
+        mask |= (unsigned long long)in << shift;
+        ft1 = __fadd_rn(ft1, 1.0f);
         if (ft1 >= e1) {
             ft1 = bx.lo[1];
-            ft0 += 1.0f;
+            ft0 = __fadd_rn(ft0, 1.0f);
+            shift += skip;
         }
+    }
+    if (i_loc == j_loc && mask) {  // (i, i, 0) is not an edge: the cell of offset 0, if in the box
+        const int z0 = -fint(bx.lo[0]), z1 = -fint(bx.lo[1]), z2 = -fint(bx.lo[2]);
+        if (z0 >= 0 && z0 < fint(bx.nn[0]) && z1 >= 0 && z1 < fint(bx.nn[1]) && z2 >= 0 && z2 < n2)
+            mask &= ~(1ull << ((z0 * B1 + z1) * B2 + z2));
     }
     return mask;
 }
 
-// A pair's box as one word: lo_k + 512 in 10 bits each, then nn_k in 7 bits each.
+// A pair's box origin as one word: lo_k + 512 in 10 bits each (the extents are the
+// structure's strides).
 __device__ __forceinline__ unsigned long long pack_box(const PairBox &bx) {
-    return (unsigned long long)pack_t((int)bx.lo[0], (int)bx.lo[1], (int)bx.lo[2]) |
-           ((unsigned long long)((unsigned)bx.nn[0] | ((unsigned)bx.nn[1] << 7) | ((unsigned)bx.nn[2] << 14)) << 30);
+    return (unsigned long long)pack_t(fint(bx.lo[0]), fint(bx.lo[1]), fint(bx.lo[2]));
 }
 
 // The next work item of this warp's pass (queue word `which`), or -1 when the list is done.
@@ -349,7 +369,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 6) pair_stage_kernel(const __
         int cnt = 0, nchunks = 0;
 #define MG_PAIR_MASKS(U_)                                                                                    \
     cnt = pair_masks<U_>(P, &R, a, w, jg, i_loc, src_ok, xi0, xi1, xi2, pi, buf, boxes, nchunks, nre, ncand)
-        switch (R.pl) {
+        switch (R.pl & 255) {
         case 1: MG_PAIR_MASKS(1); break;
         case 2: MG_PAIR_MASKS(2); break;
         case 3: MG_PAIR_MASKS(3); break;
@@ -381,6 +401,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 6) pair_stage_kernel(const __
             continue;
         }
         // ---- keys at their canonical positions, from the stored masks and boxes
+        const unsigned mB2 = (65536u + P.B2 - 1) / P.B2, mB1 = (65536u + P.B1 - 1) / P.B1;
         long long pos_src = off + src_first;  // this lane's source: its next free slot
         const long long item_end = off + T;
         __syncwarp();
@@ -393,17 +414,18 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 6) pair_stage_kernel(const __
             const int ccount = __shfl_sync(FULL, ci, lead + G - 1) - cfirst;
             long long p = pos_src + (ci - m - cfirst);
             const unsigned long long jkey = (unsigned long long)(unsigned)(c * G + jg) << 32;
-            int t0, t1, t2l;
-            unpack_t((uint32_t)(bw & 0x3fffffffull), t0, t1, t2l);
-            const int n0 = (int)((bw >> 30) & 127u), n1 = (int)((bw >> 37) & 127u), n2 = (int)((bw >> 44) & 127u);
-            // walk the box in offset order, one key per set bit
-            for (int q0 = 0; q0 < n0 && mask; ++q0, ++t0) {
-                int tt1 = t1;
-                for (int q1 = 0; q1 < n1 && mask; ++q1, ++tt1) {
-                    int t2 = t2l;
-                    for (int q2 = 0; q2 < n2; ++q2, ++t2, mask >>= 1)
-                        if ((mask & 1ull) && p < item_end) w.stage[p++] = jkey | pack_t(t0, tt1, t2);
-                }
+            int t0, t1, t2;
+            unpack_t((uint32_t)bw, t0, t1, t2);
+            // set bit b is offset lo + (r / B1, r % B1, b % B2) with r = b / B2; the quotients
+            // of these small numbers (b < 64, B <= 64) by multiply and shift: floor(b / d) =
+            // (b ceil(2^16 / d)) >> 16
+            while (mask) {
+                const unsigned b = (unsigned)(__ffsll((long long)mask) - 1);
+                mask &= mask - 1;
+                const unsigned r = (b * mB2) >> 16;
+                const unsigned q0 = (r * mB1) >> 16;
+                const int q2 = (int)(b - r * (unsigned)P.B2), q1 = (int)(r - q0 * (unsigned)P.B1);
+                if (p < item_end) w.stage[p++] = jkey | pack_t(t0 + (int)q0, t1 + q1, t2 + q2);
             }
             pos_src += ccount;
         }

@@ -35,9 +35,9 @@ struct StructRec {
     int32_t nb[3];     // cell-list bins per axis; nb[0] == 0: the structure uses all pairs
     int32_t bin_base;  // first bin of the structure: atom_begin + structure index
     int32_t ax;        // lattice axis the cutoff scan runs its candidates along (2: none moved)
-    int32_t pl;        // > 0: every (source, target) pair's offset box holds at most
-                       // PL_BOX_MAX cells and its offsets fit the packed key (pair-lane
-                       // scan); the value bounds a pair's box extent along L_2
+    int32_t pl;        // > 0: the pair-lane scan takes the structure: B0 B1 B2 <= PL_BOX_MAX
+                       // for the largest extents B_k of any pair's offset box, whose offsets
+                       // fit the packed key; pl = B2 | B1 << 8 | B0 << 16
     float reach[3];    // pair-lane scan: c / d_k plus the structure's margin; a pair's box
                        // along axis k is ceil(-reach_k - dx_k) .. floor(reach_k - dx_k)
 };
