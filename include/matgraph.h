@@ -109,8 +109,13 @@ typedef struct {
                               image whose canonical d2 is <= the k-th one (ties at the k-th
                               distance all kept, so >= k edges per atom; the capacity then
                               works as for a cutoff graph).  Other values: invalid argument */
-    int32_t schedule;      /* 0 auto (tuned), 1 flat grid, 2 persistent work queue (KNN).
-                              Cutoff builds: auto picks the one-pass build (decoupled
+    int32_t schedule;      /* 0 auto (tuned where mg_autotune ran for the size class).
+                              KNN graphs (exact k): auto / 5 the pair-lane KNN (a warp per
+                              source, a lane per target evaluating that pair's offset box,
+                              candidates sorted in shared memory; sources whose boxes are too
+                              large go to the warp-enumeration KNN), 1 the warp-enumeration
+                              KNN on a flat grid for every source, 2 on a persistent work
+                              queue.  Cutoff builds: auto picks the one-pass build (decoupled
                               look-back) below 8192 atoms; from there the pair-lane build
                               (a cost-sorted work list pulled by a persistent grid: count
                               pass, scan of the counts, write pass) for a constant radius
@@ -246,8 +251,8 @@ mg_status_t mg_symmetrize(mg_context_t ctx, const mg_batch_t *batch, const mg_gr
 
 /* Time the available schedules for this batch shape on the caller's buffers and keep
  * the fastest per size class (largest structure: <= 32, <= 128, <= 512 atoms, larger)
- * in the context: KNN flat grid or persistent work queue; cutoff graphs the one-pass or
- * the staged build (the latter only when the workspace covers graph->capacity).
+ * in the context: KNN schedules 1, 2 and 5; cutoff graphs the one-pass build, and the
+ * staged and pair-lane builds when the workspace covers graph->capacity.
  * Synchronises; results are identical for every schedule.  kind/cutoff/k as in
  * mg_build_per_structure. */
 mg_status_t mg_autotune(mg_context_t ctx, const mg_batch_t *batch, int32_t kind, float cutoff,

@@ -253,10 +253,13 @@ int size_class(const mg_batch_t *b) {
     return 3;
 }
 
+// KNN schedule: 1 / 2 the warp-enumeration KNN on a flat or persistent grid, 5 the
+// pair-lane KNN (the default), as requested or as mg_autotune measured for the size class.
 int pick_schedule(mg_context *ctx, int kind, const mg_batch_t *b, const mg_opts_t &o) {
-    if (o.schedule == 1 || o.schedule == 2) return o.schedule;
+    if (o.schedule == 1 || o.schedule == 2 || (kind == MG_KIND_KNN && o.schedule == 5)) return o.schedule;
     const int t = ctx->tuned[kind == MG_KIND_KNN ? 1 : 0][size_class(b)];
-    return t ? t : 1;
+    if (kind == MG_KIND_KNN) return t ? t : 5;
+    return t == 1 || t == 2 ? t : 1;
 }
 
 __global__ void status_init_kernel(mg_device_status_t *st) {
@@ -377,9 +380,17 @@ mg_status_t enqueue_build(mg_context *ctx, int kind, const mg_batch_t *b, float 
         ba.rr_atom = w.rr_atom;
         ba.inclusive = 1;
         if (!cutoff_build(ba)) return MG_ERR_CUDA;
-    } else {
+    } else if (ba.schedule == 1 || ba.schedule == 2) {  // the warp-enumeration KNN for every source
         if (launch_knn(ba, w, st)) return MG_ERR_CUDA;
         n += 1 + (ba.schedule == 2);
+        mk.mark("knn");
+    } else {  // the pair-lane KNN; the sources it leaves go to the warp-enumeration KNN
+        if (launch_knn_pairs(ba, w, st)) return MG_ERR_CUDA;
+        BuildArgs bl = ba;
+        bl.knn_list = 1;
+        bl.pdl = 0;
+        if (launch_knn(bl, w, st)) return MG_ERR_CUDA;
+        n += 2;
         mk.mark("knn");
     }
     if (g->perm_dst) {
@@ -1001,15 +1012,25 @@ mg_status_t mg_autotune(mg_context_t ctx, const mg_batch_t *b, int32_t kind, flo
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) return MG_ERR_CUDA;
-    // KNN: flat grid (1) or persistent queue (2); cutoff graphs: the one-pass build (3)
-    // or the staged build (4), the latter only when the workspace can stage the capacity
-    const int first = kind == MG_KIND_KNN ? 1 : 3;
-    int last = kind == MG_KIND_KNN ? 2 : 4;
-    if (kind == MG_KIND_CUTOFF && (!g || ws_max_edges(b->num_structures, b->total_atoms, ws_bytes) < g->capacity))
-        last = 3;
+    // KNN: the warp enumeration on a flat grid (1) or a persistent queue (2), or the
+    // pair-lane KNN (5); cutoff graphs: the one-pass build (3), the staged build (4) or the
+    // pair-lane build (5), the last two only when the workspace can stage the capacity
+    int cands[3], nc = 0;
+    if (kind == MG_KIND_KNN) {
+        cands[nc++] = 1;
+        cands[nc++] = 2;
+        cands[nc++] = 5;
+    } else {
+        cands[nc++] = 3;
+        if (g && ws_max_edges(b->num_structures, b->total_atoms, ws_bytes) >= g->capacity) {
+            cands[nc++] = 4;
+            cands[nc++] = 5;
+        }
+    }
     float best = 1e30f;
-    int best_s = first;
-    for (int sched = first; sched <= last; ++sched) {
+    int best_s = cands[0];
+    for (int ci = 0; ci < nc; ++ci) {
+        const int sched = cands[ci];
         mg_opts_t o = defaults(nullptr);
         o.schedule = sched;
         float tot = 0.f;

@@ -44,9 +44,13 @@ __global__ void __launch_bounds__(GROUP == 32 ? 128 : GROUP) prep_kernel(PrepArg
             queue[3] = 0;
             queue[4] = 0;  // queue[4..5]: 64-bit slot counter of the staged build
             queue[5] = 0;
-            queue[6] = 0;  // queue[6], queue[7]: work-list cursors of the pair-lane count and write passes
+            queue[6] = 0;  // queue[6], queue[7]: work-list cursors of the pair-lane build's passes
             queue[7] = 0;
         }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {  // queue[10], queue[11]: the KNN fallback list and its cursor
+        queue[10] = 0;
+        queue[11] = 0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && (a.init_status || (a.knn_k > 0 && a.edge_ptr))) {
         // nothing else writes the status word before the kernels that follow prep
@@ -236,7 +240,8 @@ __global__ void __launch_bounds__(GROUP == 32 ? 128 : GROUP) prep_kernel(PrepArg
     R.pl = 0;
     for (int k = 0; k < 3; ++k) {
         const float Rk = c * invd[k];
-        R.reach[k] = Rk + 1e-5f * (1.0f + 2.0f * xm[k] + Rk);
+        // KNN graphs: the margin's constant part only (the search radius varies per source)
+        R.reach[k] = a.knn_k > 0 ? 1e-5f * (1.0f + 2.0f * xm[k]) : Rk + 1e-5f * (1.0f + 2.0f * xm[k] + Rk);
     }
     if (!bad && R.nb[0] == 0 && n > 0 && n <= PL_MAX_ATOMS && a.knn_k == 0 && !a.cutoff_atom) {
         bool fits = true;

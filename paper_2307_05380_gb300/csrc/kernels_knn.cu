@@ -138,11 +138,15 @@ struct TopK {
     }
 };
 
-// Work distribution over source atoms (same scheme as the cutoff kernels).
+// Work distribution over source atoms (same scheme as the cutoff kernels): a flat grid
+// (1), a persistent grid pulling atoms from a counter (2), or a persistent grid pulling
+// the atoms of the pair-lane KNN's fallback list (3: list[0 .. queue[10]), cursor
+// queue[11]).
 template <int SCHED>
 struct KnnLoop {
     int lo, hi;
     unsigned int *queue;
+    const int *list = nullptr;
     __device__ __forceinline__ int first() {
         if (SCHED == 1) return lo + (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
         return next();
@@ -150,8 +154,9 @@ struct KnnLoop {
     __device__ __forceinline__ int next() {
         if (SCHED == 1) return hi;
         unsigned int v = 0;
-        if (lane_id() == 0) v = atomicAdd(queue + 1, 1u);
+        if (lane_id() == 0) v = atomicAdd(queue + (SCHED == 3 ? 11 : 1), 1u);
         v = __shfl_sync(FULL, v, 0);
+        if (SCHED == 3) return v < queue[10] ? list[v] : hi;
         return lo + (int)v;
     }
 };
@@ -180,7 +185,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 6) knn_kernel(BuildArgs a, Wor
     const int k = a.knn_k;
     const unsigned lt = (1u << lane) - 1u;
     const mg_graph_t g = a.g;
-    KnnLoop<SCHED> loop{a.atom_lo, a.atom_hi, w.queue};
+    KnnLoop<SCHED> loop{a.atom_lo, a.atom_hi, w.queue, reinterpret_cast<const int *>(w.items)};
     const Cells cells{w.cell_start, w.cell_fx, w.cell_p};
     unsigned long long nre = 0, ncand = 0;
 
@@ -529,7 +534,9 @@ static cudaError_t launch_knn_s(const BuildArgs &a, const Work &w, cudaStream_t 
     const int atoms = a.atom_hi - a.atom_lo;
     const int threads = KNN_WARPS * 32;
     const int flat_blocks = (atoms + KNN_WARPS - 1) / KNN_WARPS;
-    if (a.schedule == 2) {
+    if (a.knn_list) {  // the sources the pair-lane KNN left: usually few, two blocks per SM
+        knn_kernel<S, 3, ONEPASS><<<max(1, min(flat_blocks, 2 * num_sms())), threads, 0, s>>>(a, w);
+    } else if (a.schedule == 2) {
         cudaError_t e = launch_reset_queue(w, s);
         if (e) return e;
         int per_sm = 0;

@@ -137,6 +137,7 @@ __device__ __forceinline__ float fceil(float v) {
     return r < v ? __fadd_rn(r, 1.0f) : r;
 }
 __device__ __forceinline__ int fint(float v) { return __float_as_int(__fadd_rn(v, 12582912.0f)) - 0x4B400000; }
+__device__ __forceinline__ float ifloat(int v) { return __fsub_rn(__int_as_float(v + 0x4B400000), 12582912.0f); }
 
 __device__ __forceinline__ void pair_box(const PairStruct &P, bool ok, float xi0, float xi1, float xi2, float xj0,
                                          float xj1, float xj2, PairBox &bx) {
@@ -442,9 +443,282 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 6) pair_stage_kernel(const __
     }
 }
 
+// ============================================================================ pair-lane KNN
+
+constexpr int KNN_CAP = 256;  // candidates one warp collects for its source
+
+// Canonical FP64 squared distance of one candidate, out of line (see band_is_edge).
+__device__ __noinline__ double canon_pair_d2(const StructRec *__restrict__ rec, float xi0, float xi1, float xi2,
+                                             float xj0, float xj1, float xj2, int t0, int t1, int t2) {
+    return canon_d2(rec->L, xi0, xi1, xi2, xj0, xj1, xj2, t0, t1, t2);
+}
+
+// 64-bit keys, one per lane, sorted ascending across the warp (bitonic network).
+__device__ __forceinline__ unsigned long long warp_sort_u64(unsigned long long v) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+        const bool desc = (lane & size) != 0;
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(FULL, v, stride);
+            const bool lower = (lane & stride) == 0;
+            v = (lower != desc) ? (v < y ? v : y) : (v < y ? y : v);
+        }
+    }
+    return v;
+}
+
+// Sort n (<= KNN_CAP) 64-bit keys in shared memory with one warp: in registers up to 32,
+// by the shared-memory network beyond (padded to a power of two >= 64).
+__device__ __forceinline__ void warp_sort_n(unsigned long long *b, int n) {
+    if (n <= 32) {
+        const int lane = lane_id();
+        unsigned long long v = lane < n ? b[lane] : ~0ull;
+        v = warp_sort_u64(v);
+        __syncwarp();
+        if (lane < n) b[lane] = v;
+        __syncwarp();
+        return;
+    }
+    int P = 64;
+    while (P < n) P <<= 1;
+    warp_smem_sort_u64(b, n, P);
+}
+
+// A warp per source atom.  Alg. 1's loop with a radius rho that starts from the number
+// density: every lane evaluates its target's offset box for rho (at most 64 cells; a
+// source whose boxes grow past that, or whose offsets exceed the packed key, goes to the
+// fallback list) and the images with FP32 d2 < rho^2 are collected in shared memory (a
+// warp scan of the lanes' counts places them).  Sorted by FP32 d2, the k-th is tau; rho
+// grows until tau + 3 delta < rho^2 (delta the FP32 error bound plus the band), so every
+// image whose canonical d2 can reach tau + 2 delta is among the candidates.  Then the
+// selection of the warp-enumeration KNN: certain members below tau - 2 delta, the band
+// ranked by (canonical FP64 d2, j, t) when it holds more candidates than the slots left,
+// the k winners sorted by (j, t) and written at rows i k .. i k + k - 1.
+__global__ void __launch_bounds__(PAIR_WARPS * 32, 6) knn_pairs_kernel(const __grid_constant__ BuildArgs a,
+                                                                        const __grid_constant__ Work w) {
+    __shared__ unsigned long long ord_all[PAIR_WARPS][KNN_CAP];  // (FP32 d2 bits << 32 | slot)
+    __shared__ unsigned long long key_all[PAIR_WARPS][KNN_CAP];  // (j << 32 | packed t) by slot
+    __shared__ unsigned long long aux_all[PAIR_WARPS][KNN_CAP];  // FP64 d2 bits of the band
+    __shared__ unsigned long long win_all[PAIR_WARPS][KNN_CAP];  // the k winners' keys
+    const int wid = threadIdx.x >> 5, lane = lane_id();
+    unsigned long long *ord = ord_all[wid], *keys = key_all[wid], *aux = aux_all[wid], *win = win_all[wid];
+    pdl_wait();  // prep's records and positions (a no-op unless launched behind prep)
+    const int i = a.atom_lo + blockIdx.x * PAIR_WARPS + wid;
+    if (i >= a.atom_hi) return;
+    const mg_graph_t &g = a.g;
+    const int s = w.atom_struct[i];
+    const StructRec &R = w.recs[s];
+    if (R.bad) {
+        if (lane == 0 && i == R.atom_begin) set_error(g.status, R.bad, s + a.struct_offset);
+        return;
+    }
+    const int k = a.knn_k;
+    const int n = R.n_atoms, begin = R.atom_begin, i_loc = i - begin;
+    float L[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) L[q] = R.L[q];
+    const float xi0 = a.frac[3 * (int64_t)i], xi1 = a.frac[3 * (int64_t)i + 1], xi2 = a.frac[3 * (int64_t)i + 2];
+    const float4 pi4 = w.pos[i];
+    unsigned long long ncand = 0;
+    float rho = R.cut, tau = 0.f, delta = 0.f;
+    int C = 0;
+    bool ok = false, fallback = false;
+    for (int iter = 0; iter < 32 && !ok && !fallback; ++iter) {
+        const float rho2 = __fmul_rn(rho, rho);
+        float reach[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) reach[d] = __fadd_rn(__fmul_rn(__fmul_rn(rho, 1.00001f), R.invd[d]), R.reach[d]);
+        if (!(fmaxf(reach[0], fmaxf(reach[1], reach[2])) < 32.0f)) {  // no box of 64 cells reaches that far
+            fallback = true;
+            break;
+        }
+        C = 0;
+        bool over = false;
+        for (int jb = 0; jb < n; jb += 32) {
+            const int j_loc = jb + lane;
+            const bool okj = j_loc < n;
+            const int64_t jr = (int64_t)begin + (okj ? j_loc : 0);
+            const float xj0 = a.frac[3 * jr], xj1 = a.frac[3 * jr + 1], xj2 = a.frac[3 * jr + 2];
+            const float4 pj = w.pos[jr];
+            const float dx[3] = {__fsub_rn(xj0, xi0), __fsub_rn(xj1, xi1), __fsub_rn(xj2, xi2)};
+            float lo[3], nn[3];
+            bool big = false;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = fceil(__fsub_rn(-reach[d], dx[d]));
+                const float hi = ffloor(__fsub_rn(reach[d], dx[d]));
+                nn[d] = okj ? fmaxf(0.0f, __fadd_rn(__fsub_rn(hi, lo[d]), 1.0f)) : 0.0f;
+                big |= okj && (lo[d] < -(float)OFFSET_KEY_LIM || hi > (float)OFFSET_KEY_LIM);
+            }
+            big |= __fmul_rn(__fmul_rn(nn[0], nn[1]), nn[2]) > (float)PL_BOX_MAX;
+            if (__any_sync(FULL, big)) {
+                fallback = true;
+                break;
+            }
+            // the cells with FP32 d2 < rho^2, except (i, i, 0): same fused operations as
+            // the warp enumeration, so the structure's FP32 error bound holds
+            const float ax = __fsub_rn(pj.x, pi4.x), ay = __fsub_rn(pj.y, pi4.y), az = __fsub_rn(pj.z, pi4.z);
+            const bool same = j_loc == i_loc;
+            unsigned long long mask = 0ull, bit = 1ull;
+            for (float t0 = lo[0]; t0 < lo[0] + nn[0]; t0 = __fadd_rn(t0, 1.0f))
+                for (float t1 = lo[1]; t1 < lo[1] + nn[1]; t1 = __fadd_rn(t1, 1.0f)) {
+                    const float bx_ = __fmaf_rn(t1, L[3], __fmaf_rn(t0, L[0], ax));
+                    const float by_ = __fmaf_rn(t1, L[4], __fmaf_rn(t0, L[1], ay));
+                    const float bz_ = __fmaf_rn(t1, L[5], __fmaf_rn(t0, L[2], az));
+                    const bool row0 = same && t0 == 0.0f && t1 == 0.0f;
+                    for (float t2 = lo[2]; t2 < lo[2] + nn[2]; t2 = __fadd_rn(t2, 1.0f), bit <<= 1) {
+                        const float vx = __fmaf_rn(t2, L[6], bx_);
+                        const float vy = __fmaf_rn(t2, L[7], by_);
+                        const float vz = __fmaf_rn(t2, L[8], bz_);
+                        const float d2 = __fmaf_rn(vz, vz, __fmaf_rn(vy, vy, __fmul_rn(vx, vx)));
+                        if (d2 < rho2 && !(row0 && t2 == 0.0f)) mask |= bit;
+                    }
+                }
+            if (a.collect_stats) ncand += (unsigned long long)__fmul_rn(__fmul_rn(nn[0], nn[1]), nn[2]);
+            const int m = __popcll(mask);
+            const int incl = warp_incl_scan(m);
+            const int tot = __shfl_sync(FULL, incl, 31);
+            if (C + tot > KNN_CAP) {
+                over = true;
+                break;
+            }
+            // place this lane's candidates at C + (its exclusive prefix) + its order
+            int slot = C + incl - m;
+            const int t0i = fint(lo[0]), t1i = fint(lo[1]), t2i = fint(lo[2]);
+            const int n1 = fint(nn[1]), n2 = fint(nn[2]);
+            int q = 0;
+            for (int q0 = 0; q0 < fint(nn[0]) && mask; ++q0)
+                for (int q1 = 0; q1 < n1 && mask; ++q1) {
+                    const float ft0 = ifloat(t0i + q0), ft1 = ifloat(t1i + q1);
+                    const float bx_ = __fmaf_rn(ft1, L[3], __fmaf_rn(ft0, L[0], ax));
+                    const float by_ = __fmaf_rn(ft1, L[4], __fmaf_rn(ft0, L[1], ay));
+                    const float bz_ = __fmaf_rn(ft1, L[5], __fmaf_rn(ft0, L[2], az));
+                    for (int q2 = 0; q2 < n2; ++q2, ++q, mask >>= 1) {
+                        if (!(mask & 1ull)) continue;
+                        const float ft2 = ifloat(t2i + q2);
+                        const float vx = __fmaf_rn(ft2, L[6], bx_);
+                        const float vy = __fmaf_rn(ft2, L[7], by_);
+                        const float vz = __fmaf_rn(ft2, L[8], bz_);
+                        const float d2 = __fmaf_rn(vz, vz, __fmaf_rn(vy, vy, __fmul_rn(vx, vx)));
+                        ord[slot] = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)slot;
+                        keys[slot] = ((unsigned long long)(unsigned)j_loc << 32) | pack_t(t0i + q0, t1i + q1, t2i + q2);
+                        ++slot;
+                    }
+                }
+            C += tot;
+        }
+        __syncwarp();
+        if (fallback) break;
+        if (over) {  // more candidates than the buffer: a smaller radius
+            rho = __fmul_rn(rho, 0.8f);
+            continue;
+        }
+        if (C < k) {  // too few: a larger radius, by the expected count's cube root (at most 1.5)
+            rho = __fmul_rn(rho, C > 0 ? fminf(1.5f, fmaxf(1.1f, cbrtf(1.4f * (float)k / (float)C))) : 1.5f);
+            continue;
+        }
+        warp_sort_n(ord, C);
+        tau = __uint_as_float((unsigned)(ord[k - 1] >> 32));
+        delta = fp32_d2_error(R, rho, rho2) + 2.0f * a.band_rel * rho2;
+        if (tau + 3.0f * delta < rho2) ok = true;
+        else rho = sqrtf(tau + 3.0f * delta) * 1.0005f + 1e-6f;
+        if (!(rho < 1e6f)) break;
+    }
+    if (!ok) {  // the warp-enumeration KNN takes this source
+        if (lane == 0) {
+            const unsigned p = atomicAdd(&w.queue[10], 1u);
+            reinterpret_cast<int *>(w.items)[p] = i;
+        }
+        return;
+    }
+    // ---- selection: ord[0 .. m0) certain, ord[m0 .. m0 + nb) the band
+    const float lo_thr = tau - 2.0f * delta, hi_thr = tau + 2.0f * delta;
+    int m0 = 0, nb = 0;
+    for (int q = lane; q < C; q += 32) {
+        const float d = __uint_as_float((unsigned)(ord[q] >> 32));
+        m0 += d < lo_thr ? 1 : 0;
+        nb += (d >= lo_thr && d <= hi_thr) ? 1 : 0;
+    }
+    m0 = warp_sum(m0);
+    nb = warp_sum(nb);
+    if (m0 >= k || m0 + nb < k) {  // cannot happen: fewer than k FP32 distances lie below tau
+        if (lane == 0) set_error(g.status, MG_ERR_INTERNAL, s);
+        return;
+    }
+    const int need = k - m0;
+    for (int q = lane; q < m0; q += 32) win[q] = keys[(unsigned)ord[q]];
+    if (nb == need) {  // every band member fills a remaining slot
+        for (int q = lane; q < nb; q += 32) win[m0 + q] = keys[(unsigned)ord[m0 + q]];
+    } else {  // rank the band by (canonical FP64 d2, j, t)
+        for (int q = lane; q < nb; q += 32) {
+            const unsigned long long key = keys[(unsigned)ord[m0 + q]];
+            int t0, t1, t2;
+            unpack_t((uint32_t)(key & 0xffffffffull), t0, t1, t2);
+            const int64_t jr = (int64_t)begin + (int)(key >> 32);
+            aux[q] = (unsigned long long)__double_as_longlong(
+                canon_pair_d2(&R, xi0, xi1, xi2, a.frac[3 * jr], a.frac[3 * jr + 1], a.frac[3 * jr + 2], t0, t1, t2));
+            ord[m0 + q] = key;  // this lane's own band slot: now its key
+        }
+        __syncwarp();
+        for (int q = lane; q < nb; q += 32) {
+            const unsigned long long dq = aux[q], kq = ord[m0 + q];
+            int rank = 0;
+            for (int p = 0; p < nb; ++p) {
+                const unsigned long long dp = aux[p], kp = ord[m0 + p];
+                rank += (dp < dq || (dp == dq && kp < kq)) ? 1 : 0;
+            }
+            if (rank < need) win[m0 + rank] = kq;
+        }
+    }
+    __syncwarp();
+    // ---- the k winners in canonical (j, t) order, written at rows i k ..
+    warp_sort_n(win, k);
+    for (int q = lane; q < k; q += 32) {
+        const unsigned long long jt = win[q];
+        int t0, t1, t2;
+        unpack_t((uint32_t)(jt & 0xffffffffull), t0, t1, t2);
+        const int64_t jr = (int64_t)begin + (int)(jt >> 32);
+        const int64_t e = (int64_t)i * k + q;
+        g.src[e] = i;
+        g.dst[e] = (int32_t)jr;
+        g.offset[3 * e + 0] = t0;
+        g.offset[3 * e + 1] = t1;
+        g.offset[3 * e + 2] = t2;
+        if (g.vec || g.len) {
+            const float3 v = edge_vec_ff(L, xi0, xi1, xi2, a.frac[3 * jr], a.frac[3 * jr + 1], a.frac[3 * jr + 2], t0,
+                                         t1, t2);
+            if (g.vec) {
+                g.vec[3 * e + 0] = v.x;
+                g.vec[3 * e + 1] = v.y;
+                g.vec[3 * e + 2] = v.z;
+            }
+            if (g.len) g.len[e] = vec_len(v);
+        }
+    }
+    if (a.collect_stats) {
+        ncand = warp_sum(ncand);
+        if (lane == 0) {
+            Status *st = reinterpret_cast<Status *>(g.status);
+            atomicAdd(&st->candidates, ncand);
+            if (nb != need) atomicAdd(&st->rechecked, (unsigned long long)nb);
+        }
+    }
+}
+
 // ============================================================================ launch
 
 static int g_pair_blocks = 0;  // resident blocks per SM of the stage pass
+
+cudaError_t launch_knn_pairs(const BuildArgs &a, const Work &w, cudaStream_t s) {
+    const int atoms = a.atom_hi - a.atom_lo;
+    if (atoms <= 0) return cudaSuccess;
+    const int blocks = (atoms + PAIR_WARPS - 1) / PAIR_WARPS;
+    if (a.pdl) return launch_pdl(knn_pairs_kernel, dim3(blocks), dim3(PAIR_WARPS * 32), s, a, w);
+    knn_pairs_kernel<<<blocks, PAIR_WARPS * 32, 0, s>>>(a, w);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pair_plan(const BuildArgs &a, const Work &w, cudaStream_t s) {
     pair_plan_kernel<<<1, PLAN_THREADS, 0, s>>>(a.B, w.plan_items, w.plan_class, w.item_base, w.queue);

@@ -39,7 +39,8 @@ struct StructRec {
                        // for the largest extents B_k of any pair's offset box, whose offsets
                        // fit the packed key; pl = B2 | B1 << 8 | B0 << 16
     float reach[3];    // pair-lane scan: c / d_k plus the structure's margin; a pair's box
-                       // along axis k is ceil(-reach_k - dx_k) .. floor(reach_k - dx_k)
+                       // along axis k is ceil(-reach_k - dx_k) .. floor(reach_k - dx_k).
+                       // KNN graphs: the margin's constant part, 1e-5 (1 + 2 max|x_k|)
 };
 static_assert(sizeof(StructRec) == 160, "record layout");
 

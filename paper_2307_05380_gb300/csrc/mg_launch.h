@@ -108,6 +108,8 @@ struct BuildArgs {
     int inclusive = 0;                 // 1: edge iff d2 <= rr (Alg. 2's filter)
     double *knn_dk = nullptr;          // KNN: write the k-th canonical d2 per atom, no edges
     int write_pairs = 0;               // 1: record the pair table (symmetric cutoff graphs)
+    int knn_list = 0;                  // 1: the KNN kernel takes only the sources of the fallback
+                                       // list (w.items as int [queue[10]]) the pair-lane KNN left
     int pdl = 0;                       // host: launch the first build kernel with programmatic
                                        // stream serialization (it directly follows prep)
 };
@@ -133,6 +135,10 @@ cudaError_t launch_cutoff_count(const BuildArgs &a, const Work &w, cudaStream_t 
 cudaError_t launch_cutoff_finalize(const BuildArgs &a, const Work &w, cudaStream_t s);
 cudaError_t launch_cutoff_write(const BuildArgs &a, const Work &w, cudaStream_t s);
 cudaError_t launch_knn(const BuildArgs &a, const Work &w, cudaStream_t s);
+// Pair-lane KNN (exact k, batched): a warp per source, lanes over targets evaluating
+// their pairs' offset boxes at a growing search radius; sources it cannot take go to a
+// list that launch_knn (with knn_list = 1) builds afterwards.
+cudaError_t launch_knn_pairs(const BuildArgs &a, const Work &w, cudaStream_t s);
 cudaError_t launch_knn_pointers(const BuildArgs &a, const Work &w, cudaStream_t s);
 cudaError_t launch_dst_sort(const BuildArgs &a, const Work &w, cudaStream_t s, int *launches);
 // Destination order of a symmetric (cutoff) graph from its source order, one kernel.

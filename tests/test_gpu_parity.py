@@ -443,6 +443,26 @@ def test_pair_lane_build_stats():
     assert 0 <= st["rechecked"] < st["candidates"] * 1e-2
 
 
+@pytest.mark.parametrize("cfg,k", [(3, 8), (3, 16), (3, 32), (5, 32)])
+def test_pair_lane_knn_identical_to_warp_knn(cfg, k):
+    """The pair-lane KNN (the default: a lane per target, candidates sorted in shared
+    memory, sources with large boxes handed to the warp-enumeration KNN) against the
+    warp-enumeration KNN for every source (schedule 1): the same arrays bit for bit on
+    the 8192-structure mixture and on the supercells, plus sampled structures against
+    the oracle."""
+    b = synth.make_batch(cfg)
+    batch = to_device(b)
+    pl = graph_arrays(mg.knn_graph(batch, k, with_perm=False))
+    wk = graph_arrays(mg.knn_graph(batch, k, with_perm=False, opts=mg.make_opts(schedule=1)))
+    for key in wk:
+        np.testing.assert_array_equal(pl[key], wk[key], err_msg=key)
+    rng = np.random.default_rng(200 + k)
+    srcs = np.sort(rng.choice(b.total_atoms, 512, replace=False)).astype(np.int32)
+    rows = (srcs[:, None].astype(np.int64) * k + np.arange(k)).reshape(-1)
+    got = {key: pl[key][rows] for key in ("src", "dst", "offset")}
+    assert_same_edges(got, oracle_sources("knn", b, k, srcs), f"knn k={k}, 512 sources")
+
+
 # ------------------------------------------------------------------ schedules, per-structure, update
 
 def test_schedules_and_per_structure_identical():
