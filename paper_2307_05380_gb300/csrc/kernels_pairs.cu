@@ -486,6 +486,135 @@ __device__ __forceinline__ void warp_sort_n(unsigned long long *b, int n) {
     warp_smem_sort_u64(b, n, P);
 }
 
+// The KNN candidates of one chunk of targets: every lane's cells with FP32 d2 < rho^2
+// (not (i, i, 0)) are placed in shared memory after the C candidates already there, in
+// lane order (a warp scan of the counts); ord gets (d2 bits << 32 | slot), keys the
+// slot's (j << 32 | packed t).  Returns false (and sets over) when they would pass
+// KNN_CAP.  knn_small_cells: boxes of at most E cells per axis, unrolled with the cells'
+// distances kept in registers; knn_box_cells: any box (at most PL_BOX_MAX cells).
+template <int E>
+__device__ __forceinline__ bool knn_small_cells(const float L[9], float ax, float ay, float az, const float lo[3],
+                                                const float nn[3], float rho2, bool same, int j_loc, int &C,
+                                                unsigned long long *ord, unsigned long long *keys, bool &over) {
+    // cell c = (q0 E + q1) E + q2; the cells inside the pair's box, from its extents
+    // (0 .. E per axis) as per-axis bit patterns
+    unsigned valid;
+    if (E == 1) {
+        valid = (nn[0] > 0.0f && nn[1] > 0.0f && nn[2] > 0.0f) ? 1u : 0u;
+    } else {
+        const unsigned v0 = nn[0] >= 2.0f ? 0xFFu : (nn[0] >= 1.0f ? 0x0Fu : 0u);
+        const unsigned v1 = nn[1] >= 2.0f ? 0xFFu : (nn[1] >= 1.0f ? 0x33u : 0u);
+        const unsigned v2 = nn[2] >= 2.0f ? 0xFFu : (nn[2] >= 1.0f ? 0x55u : 0u);
+        valid = v0 & v1 & v2;
+    }
+    unsigned mask = 0u;
+#pragma unroll
+    for (int q0 = 0; q0 < E; ++q0) {
+        const float t0 = __fadd_rn(lo[0], (float)q0);
+#pragma unroll
+        for (int q1 = 0; q1 < E; ++q1) {
+            const float t1 = __fadd_rn(lo[1], (float)q1);
+            const float bx_ = __fmaf_rn(t1, L[3], __fmaf_rn(t0, L[0], ax));
+            const float by_ = __fmaf_rn(t1, L[4], __fmaf_rn(t0, L[1], ay));
+            const float bz_ = __fmaf_rn(t1, L[5], __fmaf_rn(t0, L[2], az));
+#pragma unroll
+            for (int q2 = 0; q2 < E; ++q2) {
+                const float t2 = __fadd_rn(lo[2], (float)q2);
+                const float vx = __fmaf_rn(t2, L[6], bx_);
+                const float vy = __fmaf_rn(t2, L[7], by_);
+                const float vz = __fmaf_rn(t2, L[8], bz_);
+                const float d2 = __fmaf_rn(vz, vz, __fmaf_rn(vy, vy, __fmul_rn(vx, vx)));
+                if (d2 < rho2) mask |= 1u << ((q0 * E + q1) * E + q2);
+            }
+        }
+    }
+    mask &= valid;
+    if (same && mask) {  // (i, i, 0) is not a candidate: the cell of offset 0, if in the box
+        const float z0 = -lo[0], z1 = -lo[1], z2 = -lo[2];
+        if (z0 >= 0.0f && z0 < (float)E && z1 >= 0.0f && z1 < (float)E && z2 >= 0.0f && z2 < (float)E)
+            mask &= ~(1u << ((fint(z0) * E + fint(z1)) * E + fint(z2)));
+    }
+    const int m = __popc(mask);
+    const int incl = warp_incl_scan(m);
+    const int tot = __shfl_sync(FULL, incl, 31);
+    if (C + tot > KNN_CAP) {
+        over = true;
+        return false;
+    }
+    int slot = C + incl - m;
+    const int t0i = fint(lo[0]), t1i = fint(lo[1]), t2i = fint(lo[2]);
+    while (mask) {  // the set cells, their distance again (the same operations)
+        const int c = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int q0 = c / (E * E), q1 = (c / E) % E, q2 = c % E;
+        const float t0 = __fadd_rn(lo[0], ifloat(q0)), t1 = __fadd_rn(lo[1], ifloat(q1)),
+                    t2 = __fadd_rn(lo[2], ifloat(q2));
+        const float bx_ = __fmaf_rn(t1, L[3], __fmaf_rn(t0, L[0], ax));
+        const float by_ = __fmaf_rn(t1, L[4], __fmaf_rn(t0, L[1], ay));
+        const float bz_ = __fmaf_rn(t1, L[5], __fmaf_rn(t0, L[2], az));
+        const float vx = __fmaf_rn(t2, L[6], bx_);
+        const float vy = __fmaf_rn(t2, L[7], by_);
+        const float vz = __fmaf_rn(t2, L[8], bz_);
+        const float d2 = __fmaf_rn(vz, vz, __fmaf_rn(vy, vy, __fmul_rn(vx, vx)));
+        ord[slot] = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)slot;
+        keys[slot] = ((unsigned long long)(unsigned)j_loc << 32) | pack_t(t0i + q0, t1i + q1, t2i + q2);
+        ++slot;
+    }
+    C += tot;
+    return true;
+}
+
+__device__ __forceinline__ bool knn_box_cells(const float L[9], float ax, float ay, float az, const float lo[3],
+                                              const float nn[3], float rho2, bool same, int j_loc, int &C,
+                                              unsigned long long *ord, unsigned long long *keys, bool &over) {
+    unsigned long long mask = 0ull, bit = 1ull;
+    for (float t0 = lo[0]; t0 < lo[0] + nn[0]; t0 = __fadd_rn(t0, 1.0f))
+        for (float t1 = lo[1]; t1 < lo[1] + nn[1]; t1 = __fadd_rn(t1, 1.0f)) {
+            const float bx_ = __fmaf_rn(t1, L[3], __fmaf_rn(t0, L[0], ax));
+            const float by_ = __fmaf_rn(t1, L[4], __fmaf_rn(t0, L[1], ay));
+            const float bz_ = __fmaf_rn(t1, L[5], __fmaf_rn(t0, L[2], az));
+            const bool row0 = same && t0 == 0.0f && t1 == 0.0f;
+            for (float t2 = lo[2]; t2 < lo[2] + nn[2]; t2 = __fadd_rn(t2, 1.0f), bit <<= 1) {
+                const float vx = __fmaf_rn(t2, L[6], bx_);
+                const float vy = __fmaf_rn(t2, L[7], by_);
+                const float vz = __fmaf_rn(t2, L[8], bz_);
+                const float d2 = __fmaf_rn(vz, vz, __fmaf_rn(vy, vy, __fmul_rn(vx, vx)));
+                if (d2 < rho2 && !(row0 && t2 == 0.0f)) mask |= bit;
+            }
+        }
+    const int m = __popcll(mask);
+    const int incl = warp_incl_scan(m);
+    const int tot = __shfl_sync(FULL, incl, 31);
+    if (C + tot > KNN_CAP) {
+        over = true;
+        return false;
+    }
+    // place this lane's candidates at C + (its exclusive prefix) + its order
+    int slot = C + incl - m;
+    const int t0i = fint(lo[0]), t1i = fint(lo[1]), t2i = fint(lo[2]);
+    const int n1 = fint(nn[1]), n2 = fint(nn[2]);
+    for (int q0 = 0; q0 < fint(nn[0]) && mask; ++q0)
+        for (int q1 = 0; q1 < n1 && mask; ++q1) {
+            const float ft0 = ifloat(t0i + q0), ft1 = ifloat(t1i + q1);
+            const float bx_ = __fmaf_rn(ft1, L[3], __fmaf_rn(ft0, L[0], ax));
+            const float by_ = __fmaf_rn(ft1, L[4], __fmaf_rn(ft0, L[1], ay));
+            const float bz_ = __fmaf_rn(ft1, L[5], __fmaf_rn(ft0, L[2], az));
+            for (int q2 = 0; q2 < n2; ++q2, mask >>= 1) {
+                if (!(mask & 1ull)) continue;
+                const float ft2 = ifloat(t2i + q2);
+                const float vx = __fmaf_rn(ft2, L[6], bx_);
+                const float vy = __fmaf_rn(ft2, L[7], by_);
+                const float vz = __fmaf_rn(ft2, L[8], bz_);
+                const float d2 = __fmaf_rn(vz, vz, __fmaf_rn(vy, vy, __fmul_rn(vx, vx)));
+                ord[slot] = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)slot;
+                keys[slot] = ((unsigned long long)(unsigned)j_loc << 32) | pack_t(t0i + q0, t1i + q1, t2i + q2);
+                ++slot;
+            }
+        }
+    C += tot;
+    return true;
+}
+
 // A warp per source atom.  Alg. 1's loop with a radius rho that starts from the number
 // density: every lane evaluates its target's offset box for rho (at most 64 cells; a
 // source whose boxes grow past that, or whose offsets exceed the packed key, goes to the
@@ -534,6 +663,10 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 6) knn_pairs_kernel(const __g
             fallback = true;
             break;
         }
+        // boxes of at most one or two cells per axis when the reach is below a half or a
+        // whole cell (an interval shorter than 1 or 2 holds at most 1 or 2 integers)
+        const float rmax = fmaxf(reach[0], fmaxf(reach[1], reach[2]));
+        const int E = rmax < 0.49f ? 1 : (rmax < 0.99f ? 2 : 0);
         C = 0;
         bool over = false;
         for (int jb = 0; jb < n; jb += 32) {
@@ -553,6 +686,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 6) knn_pairs_kernel(const __g
                 big |= okj && (lo[d] < -(float)OFFSET_KEY_LIM || hi > (float)OFFSET_KEY_LIM);
             }
             big |= __fmul_rn(__fmul_rn(nn[0], nn[1]), nn[2]) > (float)PL_BOX_MAX;
+            if (E > 0) big |= fmaxf(nn[0], fmaxf(nn[1], nn[2])) > (float)E;  // cannot happen
             if (__any_sync(FULL, big)) {
                 fallback = true;
                 break;
@@ -561,53 +695,15 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 6) knn_pairs_kernel(const __g
             // the warp enumeration, so the structure's FP32 error bound holds
             const float ax = __fsub_rn(pj.x, pi4.x), ay = __fsub_rn(pj.y, pi4.y), az = __fsub_rn(pj.z, pi4.z);
             const bool same = j_loc == i_loc;
-            unsigned long long mask = 0ull, bit = 1ull;
-            for (float t0 = lo[0]; t0 < lo[0] + nn[0]; t0 = __fadd_rn(t0, 1.0f))
-                for (float t1 = lo[1]; t1 < lo[1] + nn[1]; t1 = __fadd_rn(t1, 1.0f)) {
-                    const float bx_ = __fmaf_rn(t1, L[3], __fmaf_rn(t0, L[0], ax));
-                    const float by_ = __fmaf_rn(t1, L[4], __fmaf_rn(t0, L[1], ay));
-                    const float bz_ = __fmaf_rn(t1, L[5], __fmaf_rn(t0, L[2], az));
-                    const bool row0 = same && t0 == 0.0f && t1 == 0.0f;
-                    for (float t2 = lo[2]; t2 < lo[2] + nn[2]; t2 = __fadd_rn(t2, 1.0f), bit <<= 1) {
-                        const float vx = __fmaf_rn(t2, L[6], bx_);
-                        const float vy = __fmaf_rn(t2, L[7], by_);
-                        const float vz = __fmaf_rn(t2, L[8], bz_);
-                        const float d2 = __fmaf_rn(vz, vz, __fmaf_rn(vy, vy, __fmul_rn(vx, vx)));
-                        if (d2 < rho2 && !(row0 && t2 == 0.0f)) mask |= bit;
-                    }
-                }
             if (a.collect_stats) ncand += (unsigned long long)__fmul_rn(__fmul_rn(nn[0], nn[1]), nn[2]);
-            const int m = __popcll(mask);
-            const int incl = warp_incl_scan(m);
-            const int tot = __shfl_sync(FULL, incl, 31);
-            if (C + tot > KNN_CAP) {
-                over = true;
-                break;
-            }
-            // place this lane's candidates at C + (its exclusive prefix) + its order
-            int slot = C + incl - m;
-            const int t0i = fint(lo[0]), t1i = fint(lo[1]), t2i = fint(lo[2]);
-            const int n1 = fint(nn[1]), n2 = fint(nn[2]);
-            int q = 0;
-            for (int q0 = 0; q0 < fint(nn[0]) && mask; ++q0)
-                for (int q1 = 0; q1 < n1 && mask; ++q1) {
-                    const float ft0 = ifloat(t0i + q0), ft1 = ifloat(t1i + q1);
-                    const float bx_ = __fmaf_rn(ft1, L[3], __fmaf_rn(ft0, L[0], ax));
-                    const float by_ = __fmaf_rn(ft1, L[4], __fmaf_rn(ft0, L[1], ay));
-                    const float bz_ = __fmaf_rn(ft1, L[5], __fmaf_rn(ft0, L[2], az));
-                    for (int q2 = 0; q2 < n2; ++q2, ++q, mask >>= 1) {
-                        if (!(mask & 1ull)) continue;
-                        const float ft2 = ifloat(t2i + q2);
-                        const float vx = __fmaf_rn(ft2, L[6], bx_);
-                        const float vy = __fmaf_rn(ft2, L[7], by_);
-                        const float vz = __fmaf_rn(ft2, L[8], bz_);
-                        const float d2 = __fmaf_rn(vz, vz, __fmaf_rn(vy, vy, __fmul_rn(vx, vx)));
-                        ord[slot] = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)slot;
-                        keys[slot] = ((unsigned long long)(unsigned)j_loc << 32) | pack_t(t0i + q0, t1i + q1, t2i + q2);
-                        ++slot;
-                    }
-                }
-            C += tot;
+            bool placed;
+            if (E == 1)
+                placed = knn_small_cells<1>(L, ax, ay, az, lo, nn, rho2, same, j_loc, C, ord, keys, over);
+            else if (E == 2)
+                placed = knn_small_cells<2>(L, ax, ay, az, lo, nn, rho2, same, j_loc, C, ord, keys, over);
+            else
+                placed = knn_box_cells(L, ax, ay, az, lo, nn, rho2, same, j_loc, C, ord, keys, over);
+            if (!placed) break;
         }
         __syncwarp();
         if (fallback) break;
