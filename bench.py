@@ -119,13 +119,13 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def fp32_term(edges, seconds, peak_tflops):
+def fp32_term(edges, seconds, peak_tflops, peak_source):
     """The distance-flop side of a build's roofline, beside its edge-byte side."""
     per_edge = FLOPS_PER_CANDIDATE * CANDIDATES_PER_EDGE
     achieved = per_edge * edges / seconds / 1e12
     return {"achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
             "work_per_launch": f"{per_edge:.1f} flop/edge (11 per candidate, 6/pi candidates per edge) x {edges} edges",
-            "peak_source": "FP32 lanes x max SM clock"}
+            "peak_source": peak_source}
 
 
 def measured_peaks():
@@ -489,46 +489,36 @@ def run_mine(args, rank, world, local_rank):
         tot_units, max_ms = reduce_over_ranks(tot_units, max_ms, dev)
     value = tot_units / (max_ms / 1e3)
 
-    # e2e: the step's library calls (both graph updates, forward, backward with the loss
-    # gradient) from pinned host inputs to pinned host outputs.  Every step copies the
-    # inputs in and every output back: both graphs' edges, status words, vectors and
-    # gradients.  Each graph's copy (one library call per graph) is issued right behind
-    # its build, on another stream, so the copies overlap the rest of the step; the step's
-    # outputs follow the backward.  The host waits once, at the end, then checks both
-    # status words.
+    # e2e: the step (both graph updates, forward, backward with the loss gradient) from
+    # pinned host inputs to pinned host outputs.  Every step copies the inputs in and every
+    # output back: both graphs' edges, status words, vectors and gradients.  Each graph's
+    # copy is issued right behind its build, on another stream, so the copies overlap the
+    # rest of the step; the step's outputs follow the backward.  The host waits once, at
+    # the end, then checks both status words.
     frac_h = torch.from_numpy(b.frac).pin_memory()
     lat_h = torch.from_numpy(b.lattice).pin_memory()
     ptr_h = torch.from_numpy(b.atom_ptr).pin_memory()
     w_dev = grad_len  # dLoss/dlen of the loss sum(w * len)
     e2e_steps = max(5, min(args.steps, 50))
     copy_stream = torch.cuda.Stream(dev)
-    ev_in, ev_cut = torch.cuda.Event(), torch.cuda.Event()
     host_knn = mg.host_buffers(g_knn, E_knn, ("status", "src", "dst", "offset", "vec", "len"))
     host_cut = mg.host_buffers(g_cut, E_cut, ("status", "src", "dst", "offset"))
     step_out = (out_vec[:E_cut], out_len[:E_cut], grad_frac, grad_lat)
     host_step = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in step_out]
     d2h = sum(t.numel() * t.element_size() for t in list(host_knn.values()) + list(host_cut.values()) + host_step)
 
+    # the whole step through one library call (mg_graph_step): inputs in, both graphs
+    # rebuilt (KNN on its own stream) and copied out (the cutoff graph's copy on the copy
+    # stream), edge vectors and backward, results out; one synchronisation per step
+    out_host = {"vec": host_step[0], "len": host_step[1], "grad_frac": host_step[2], "grad_lattice": host_step[3]}
+    step_call = mg.Step([g_cut, g_knn], [main_stream, knn_stream, copy_stream], host=(host_cut, host_knn),
+                        inputs={"frac": frac_h, "lattice": lat_h, "atom_ptr": ptr_h}, grad_len=w_dev, vec=out_vec,
+                        ln=out_len, grad_frac=grad_frac, grad_lattice=grad_lat, outputs=out_host,
+                        host_edges=(E_cut, E_knn))
+
     def e2e_step():
-        batch.frac.copy_(frac_h, non_blocking=True)
-        batch.lattice.copy_(lat_h, non_blocking=True)
-        batch.atom_ptr.copy_(ptr_h, non_blocking=True)
-        ev_in.record(main_stream)
-        mg.update_graph(g_cut, sync=False)  # the larger graph first: its copy starts earliest
-        ev_cut.record(main_stream)
-        copy_stream.wait_event(ev_cut)
-        torch.cuda.set_stream(copy_stream)  # behind the cutoff build, beside the rest
-        mg.graph_to_host(g_cut, host_cut, E_cut)
-        knn_stream.wait_event(ev_in)
-        torch.cuda.set_stream(knn_stream)
-        mg.update_graph(g_knn, sync=False)
-        mg.graph_to_host(g_knn, host_knn, E_knn)  # behind the KNN build
-        torch.cuda.set_stream(main_stream)
-        mg.edge_vectors_fwd(g_cut, out_vec=out_vec, out_len=out_len)
-        mg.edge_vectors_bwd(g_cut, batch, None, w_dev, out_vec, out_len, grad_frac, grad_lat)
-        for h, t in zip(host_step, step_out):  # behind the backward
-            h.copy_(t, non_blocking=True)
-        torch.cuda.synchronize(dev)
+        step_call.run()
+        main_stream.synchronize()
         for st_h, E in ((host_cut["status"], E_cut), (host_knn["status"], E_knn)):  # code 0, same edge count
             assert int(st_h[0]) & 0xFFFFFFFF == 0 and int(st_h[1]) == E, st_h
         return E_cut + E_knn, d2h
@@ -594,7 +584,13 @@ def run_mine(args, rank, world, local_rank):
 
     # roofline of the dominant stage
     hbm_peak, sm_max, peak_src = measured_peaks()
-    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    # the FP32 peak measured by the library's own FMA kernel (CUDA events, no clock
+    # setting touched), the nominal lanes x clock beside it
+    fp_peaks = mg.measure_fp_peaks(dev)
+    fp32_nominal = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    fp32_peak = fp_peaks["fp32_tflops"]
+    fp32_src = (f"measured: library FFMA kernel, 16 chains per thread, full occupancy "
+                f"({fp32_peak:.1f} TFLOP/s; nominal 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz = {fp32_nominal:.1f})")
     stages = {f"{k[0]}.{k[1]}": v / n_roof for k, v in stage_tot.items()}
     # the staged cutoff build (large batches) is three stages: scan and stage the keys,
     # scan the counts, write the edges; its edge emission is the unit of the roofline
@@ -621,11 +617,11 @@ def run_mine(args, rank, world, local_rank):
         roof["kernel"] += " (pair-lane: cost-sorted plan, stage, count scan, emit; 9 launches)"
     elif staged and dom == ("cutoff", "build"):
         roof["kernel"] += " (staged: scan-and-stage, count scan, emit; 7 launches)"
-    roof["peak_source"] = f"{peak_src} ({'MEASURED_PEAKS.json hbm_gbs' if bound == 'hbm' else 'FP32 lanes x clock'})"
+    roof["peak_source"] = f"{peak_src} ({'MEASURED_PEAKS.json hbm_gbs' if bound == 'hbm' else fp32_src})"
     roof["traffic"] = recorded_traffic(args.config, dom)
     roof["work_per_launch"] = f"{per_unit:g} {'B' if bound == 'hbm' else 'flop'}/edge x {n_units} edges"
     if dom in (("cutoff", "build"), ("knn", "knn")):
-        roof["fp32_term"] = fp32_term(n_units, t_launch, fp32_peak)
+        roof["fp32_term"] = fp32_term(n_units, t_launch, fp32_peak, fp32_src)
 
     if rank == 0:
         cpu = None
@@ -648,7 +644,7 @@ def run_mine(args, rank, world, local_rank):
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "step": "cutoff build + KNN build (CUDA-graph plans) + edge-vector fwd + bwd on the "
                                    "cutoff graph; destination orders not requested (unused by the step)"},
-                "roofline": roof, "cpu_baseline": cpu, "float_error": ferr,
+                "roofline": roof, "cpu_baseline": cpu, "float_error": ferr, "fp_peaks_measured": fp_peaks,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": gpu_launches, "clocks": clocks, "per_structure": per_structure,
                 "stage_ms_per_step": stages, "wall_s_timed_region": t_wall}

@@ -27,7 +27,8 @@
  *   never allocates device memory: scratch comes from a caller workspace sized by
  *   mg_workspace_size.  All calls are ordered on the caller's stream (a cudaStream_t
  *   passed as void*; NULL = legacy default stream) and none synchronises the host,
- *   except mg_autotune.  The host-side mg_context_t owns only host state (device
+ *   except mg_autotune and mg_measure_fp_peaks.  The host-side mg_context_t owns only
+ *   host state (device
  *   properties, tuned schedules, captured CUDA graphs).
  *
  * Errors
@@ -320,6 +321,56 @@ int64_t mg_last_launch_count(mg_context_t ctx);
 #define MG_NOALLOC_SCRATCH_BYTES (32u << 20)
 mg_status_t mg_cutoff_graph_noalloc(mg_context_t ctx, const mg_batch_t *batch, float cutoff,
                                     const mg_opts_t *opts, mg_graph_t *graph, void *stream);
+
+/* One step of a generative loop in one call (no counterpart in the paper; it saves the
+ * host time of a call per stage): new geometry in, the graphs rebuilt, edge vectors and
+ * their gradients, results out.  Every pointer is caller-owned; NULL skips that part.
+ * In order, on the caller's streams:
+ *   1. frac_host / lattice_host / atom_ptr_host (pinned host memory, the batch's sizes)
+ *      are copied into the batch's device buffers on stream[0];
+ *   2. graph[1] (if not NULL) is rebuilt by mg_update_graph on stream[1] after the
+ *      copies, and copied out by mg_graph_to_host (graph_host[1], host_edges[1] rows)
+ *      behind it on the same stream;
+ *   3. graph[0] is rebuilt on stream[0]; its host copy runs on stream[2] behind it (or on
+ *      stream[0] when stream[2] is NULL), beside the rest of the step;
+ *   4. mg_edge_vectors_fwd into vec / len and mg_edge_vectors_bwd of grad_vec / grad_len
+ *      into grad_frac / grad_lattice on graph[0] (ws[0] as the backward's workspace), each
+ *      skipped when its outputs are NULL; vec_host, len_host (host_edges[0] rows),
+ *      grad_frac_host and grad_lattice_host are copied out behind them;
+ *   5. stream[0] waits for streams 1 and 2: synchronise stream[0] to read the results.
+ * Each graph must have been built before on this context (mg_update_graph's
+ * conditions); errors are those of the calls named.  Does not synchronise.
+ * capture = 1: the first call records all of the above as one CUDA graph and launches
+ * it; a later call whose arguments are identical (the same pointers, sizes and edge
+ * counts, compared byte for byte with the batch, the graphs and the host buffer lists)
+ * launches that graph again: one launch per step instead of about 25 calls.  Other
+ * arguments record a new graph.  The context keeps one recorded step. */
+typedef struct {
+    const mg_batch_t *batch;
+    const float *frac_host, *lattice_host;   /* [N][3], [B][3][3] pinned host, or NULL */
+    const int32_t *atom_ptr_host;             /* [B+1] pinned host, or NULL */
+    mg_graph_t *graph[2];                     /* graph[1] may be NULL */
+    void *ws[2];
+    size_t ws_bytes[2];
+    void *stream[3];                          /* stream[1], stream[2] may be NULL (= stream[0]) */
+    const mg_graph_host_t *graph_host[2];     /* host copies of the graphs, or NULL */
+    int64_t host_edges[2];                    /* rows to copy (e.g. the last read edge count) */
+    const float *grad_vec, *grad_len;         /* device [E][3], [E] incoming gradients, or NULL */
+    float *vec, *len;                         /* device forward outputs, or NULL (no forward) */
+    float *grad_frac, *grad_lattice;          /* device backward outputs, or NULL (no backward) */
+    float *vec_host, *len_host, *grad_frac_host, *grad_lattice_host;  /* pinned host, or NULL */
+    int32_t capture;                          /* 1: record once, replay (see above) */
+} mg_step_t;
+mg_status_t mg_graph_step(mg_context_t ctx, const mg_step_t *step);
+
+/* Measurement support (no counterpart in the paper): the FP32 and FP64 fused
+ * multiply-add issue rates of this GPU, in TFLOP/s (2 flops per FMA), from the library's
+ * own kernel: every thread runs 16 independent FMA chains, a full-occupancy grid, CUDA
+ * events around each launch, the best of three timed launches after one warm-up.  No
+ * clock or power setting is read or changed.  sink: 16 bytes of device memory the
+ * kernels may write (they never do for these inputs).  Synchronises the stream. */
+mg_status_t mg_measure_fp_peaks(mg_context_t ctx, void *sink, double *fp32_tflops, double *fp64_tflops,
+                                void *stream);
 
 #define MG_PROF_CUTOFF 0
 #define MG_PROF_KNN 1

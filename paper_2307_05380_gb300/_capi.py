@@ -44,6 +44,15 @@ class MgGraphHost(ctypes.Structure):
                 ("vec", c_void_p), ("len", c_void_p), ("edge_ptr", c_void_p), ("src_ptr", c_void_p)]
 
 
+class MgStep(ctypes.Structure):
+    _fields_ = [("batch", c_void_p), ("frac_host", c_void_p), ("lattice_host", c_void_p),
+                ("atom_ptr_host", c_void_p), ("graph", c_void_p * 2), ("ws", c_void_p * 2), ("ws_bytes", c_size_t * 2),
+                ("stream", c_void_p * 3), ("graph_host", c_void_p * 2), ("host_edges", c_int64 * 2),
+                ("grad_vec", c_void_p), ("grad_len", c_void_p), ("vec", c_void_p), ("len", c_void_p),
+                ("grad_frac", c_void_p), ("grad_lattice", c_void_p), ("vec_host", c_void_p), ("len_host", c_void_p),
+                ("grad_frac_host", c_void_p), ("grad_lattice_host", c_void_p), ("capture", c_int32)]
+
+
 class MgOpts(ctypes.Structure):
     _fields_ = [("band_rel", c_float), ("knn_keep_ties", c_int32), ("schedule", c_int32),
                 ("collect_stats", c_int32), ("fault_tile", c_int32)]
@@ -82,6 +91,9 @@ SIGNATURES = [
                                 ctypes.POINTER(MgGraph), c_void_p, c_size_t, c_void_p]),
     ("mg_graph_to_host", c_int32, [c_void_p, ctypes.POINTER(MgBatch), ctypes.POINTER(MgGraph), c_int64,
                                    ctypes.POINTER(MgGraphHost), c_void_p]),
+    ("mg_graph_step", c_int32, [c_void_p, ctypes.POINTER(MgStep)]),
+    ("mg_measure_fp_peaks", c_int32, [c_void_p, c_void_p, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), c_void_p]),
     ("mg_profile_enable", c_int32, [c_void_p, c_int32]),
     ("mg_stage_times", c_int32, [c_void_p, c_int32, c_int32, ctypes.POINTER(ctypes.c_char_p),
                                  ctypes.POINTER(c_float)]),

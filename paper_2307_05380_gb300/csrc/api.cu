@@ -74,6 +74,14 @@ struct mg_context {
     std::map<const void *, const void *> pair_owner;  // workspace -> graph (src) whose pair table it holds
     int tuned[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};  // [kind-1][size class] -> schedule
     int64_t last_launches = 0;
+    cudaEvent_t step_ev[3] = {};  // mg_graph_step's fork and join events (no timing)
+    struct StepRec {              // the step mg_graph_step recorded as a CUDA graph
+        mg_step_t st{};
+        mg_batch_t batch{};
+        mg_graph_t g[2]{};
+        mg_graph_host_t h[2]{};
+        cudaGraphExec_t exec = nullptr;
+    } step;
 };
 
 namespace {
@@ -506,6 +514,26 @@ mg_status_t noalloc_scratch(void **out) {
 
 }  // namespace
 
+// Issue-rate probes for mg_measure_fp_peaks: every thread runs PEAK_CHAINS independent
+// fused multiply-add chains (enough to cover the pipe latency) for `iters` steps; the
+// result is stored only under a condition the data never meets, so the chains are kept.
+constexpr int PEAK_CHAINS = 16;
+
+template <class T>
+__global__ void __launch_bounds__(256) fma_peak_kernel(int iters, T b, T c, T *sink) {
+    T acc[PEAK_CHAINS];
+#pragma unroll
+    for (int q = 0; q < PEAK_CHAINS; ++q) acc[q] = (T)(threadIdx.x + q) * (T)1e-3;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int q = 0; q < PEAK_CHAINS; ++q) acc[q] = fma(acc[q], b, c);
+    }
+    T sum = 0;
+#pragma unroll
+    for (int q = 0; q < PEAK_CHAINS; ++q) sum += acc[q];
+    if (sum == (T)-1.2345e30) *sink = sum;
+}
+
 extern "C" {
 
 mg_status_t mg_create(mg_context_t *ctx, int device) {
@@ -529,6 +557,9 @@ mg_status_t mg_destroy(mg_context_t ctx) {
         kv.second.prof.destroy();
     }
     for (auto &p : ctx->prof) p.destroy();
+    for (auto &e : ctx->step_ev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->step.exec) cudaGraphExecDestroy(ctx->step.exec);
     delete ctx;
     return MG_OK;
 }
@@ -1062,6 +1093,185 @@ mg_status_t mg_autotune(mg_context_t ctx, const mg_batch_t *b, int32_t kind, flo
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->tuned[kind - 1][size_class(b)] = best_s;
     return MG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+bool same_step(const mg_context::StepRec &r, const mg_step_t &p) {
+    const mg_step_t &q = r.st;
+    bool same = q.frac_host == p.frac_host && q.lattice_host == p.lattice_host && q.atom_ptr_host == p.atom_ptr_host &&
+                q.grad_vec == p.grad_vec && q.grad_len == p.grad_len && q.vec == p.vec && q.len == p.len &&
+                q.grad_frac == p.grad_frac && q.grad_lattice == p.grad_lattice && q.vec_host == p.vec_host &&
+                q.len_host == p.len_host && q.grad_frac_host == p.grad_frac_host &&
+                q.grad_lattice_host == p.grad_lattice_host && q.capture == p.capture && same_batch(r.batch, *p.batch);
+    for (int k = 0; k < 3; ++k) same = same && q.stream[k] == p.stream[k];
+    for (int g = 0; g < 2; ++g) {
+        same = same && (q.graph[g] != nullptr) == (p.graph[g] != nullptr) && q.ws[g] == p.ws[g] &&
+               q.ws_bytes[g] == p.ws_bytes[g] && q.host_edges[g] == p.host_edges[g] &&
+               (q.graph_host[g] != nullptr) == (p.graph_host[g] != nullptr);
+        if (same && p.graph[g]) same = same_graph(r.g[g], *p.graph[g]);
+        if (same && p.graph_host[g]) same = std::memcmp(&r.h[g], p.graph_host[g], sizeof(mg_graph_host_t)) == 0;
+    }
+    return same;
+}
+
+mg_status_t enqueue_step(mg_context_t ctx, const mg_step_t *p) {
+    const mg_batch_t *b = p->batch;
+    mg_status_t r = MG_OK;
+    cudaStream_t s0 = static_cast<cudaStream_t>(p->stream[0]);
+    cudaStream_t s1 = p->stream[1] ? static_cast<cudaStream_t>(p->stream[1]) : s0;
+    cudaStream_t s2 = p->stream[2] ? static_cast<cudaStream_t>(p->stream[2]) : s0;
+    cudaEvent_t ev_in = ctx->step_ev[0], ev_g0 = ctx->step_ev[1], ev_done = ctx->step_ev[2];
+    // 1. inputs
+    const size_t N = (size_t)b->total_atoms, B = (size_t)b->num_structures;
+    if (p->frac_host && N &&
+        cudaMemcpyAsync(const_cast<float *>(b->frac), p->frac_host, 12 * N, cudaMemcpyHostToDevice, s0) != cudaSuccess)
+        return MG_ERR_CUDA;
+    if (p->lattice_host && cudaMemcpyAsync(const_cast<float *>(b->lattice), p->lattice_host, 36 * B,
+                                           cudaMemcpyHostToDevice, s0) != cudaSuccess)
+        return MG_ERR_CUDA;
+    if (p->atom_ptr_host && cudaMemcpyAsync(const_cast<int32_t *>(b->atom_ptr), p->atom_ptr_host, 4 * (B + 1),
+                                            cudaMemcpyHostToDevice, s0) != cudaSuccess)
+        return MG_ERR_CUDA;
+    // 2. the second graph on its own stream, its copy behind it
+    if (p->graph[1]) {
+        if (s1 != s0) {
+            if (cudaEventRecord(ev_in, s0) != cudaSuccess || cudaStreamWaitEvent(s1, ev_in, 0) != cudaSuccess)
+                return MG_ERR_CUDA;
+        }
+        r = mg_update_graph(ctx, b, p->graph[1], p->ws[1], p->ws_bytes[1], s1);
+        if (r) return r;
+        if (p->graph_host[1]) {
+            r = mg_graph_to_host(ctx, b, p->graph[1], p->host_edges[1], p->graph_host[1], s1);
+            if (r) return r;
+        }
+    }
+    // 3. the first graph; its copy beside the rest of the step
+    r = mg_update_graph(ctx, b, p->graph[0], p->ws[0], p->ws_bytes[0], s0);
+    if (r) return r;
+    if (p->graph_host[0]) {
+        if (s2 != s0) {
+            if (cudaEventRecord(ev_g0, s0) != cudaSuccess || cudaStreamWaitEvent(s2, ev_g0, 0) != cudaSuccess)
+                return MG_ERR_CUDA;
+        }
+        r = mg_graph_to_host(ctx, b, p->graph[0], p->host_edges[0], p->graph_host[0], s2);
+        if (r) return r;
+    }
+    // 4. edge vectors and their backward, results out
+    const size_t E = p->host_edges[0] > 0 ? (size_t)p->host_edges[0] : 0;
+    if (p->vec || p->len) {
+        r = mg_edge_vectors_fwd(ctx, b, p->graph[0], p->vec, p->len, s0);
+        if (r) return r;
+    }
+    if (p->grad_frac && p->grad_lattice) {
+        r = mg_edge_vectors_bwd(ctx, b, p->graph[0], p->grad_vec, p->grad_len, p->vec, p->len, p->grad_frac,
+                                p->grad_lattice, p->ws[0], p->ws_bytes[0], s0);
+        if (r) return r;
+    }
+    struct Out {
+        void *dst;
+        const void *src;
+        size_t bytes;
+    };
+    const Out outs[] = {{p->vec_host, p->vec, 12 * E},
+                        {p->len_host, p->len, 4 * E},
+                        {p->grad_frac_host, p->grad_frac, 12 * N},
+                        {p->grad_lattice_host, p->grad_lattice, 36 * B}};
+    for (const Out &o : outs)
+        if (o.dst && o.src && o.bytes && cudaMemcpyAsync(o.dst, o.src, o.bytes, cudaMemcpyDeviceToHost, s0) != cudaSuccess)
+            return MG_ERR_CUDA;
+    // 5. join
+    for (cudaStream_t sx : {s1, s2}) {
+        if (sx == s0) continue;
+        if (cudaEventRecord(ev_done, sx) != cudaSuccess || cudaStreamWaitEvent(s0, ev_done, 0) != cudaSuccess)
+            return MG_ERR_CUDA;
+    }
+    return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mg_status_t mg_graph_step(mg_context_t ctx, const mg_step_t *p) {
+    if (!ctx || !p || !p->batch || !p->graph[0] || (p->capture != 0 && p->capture != 1)) return MG_ERR_INVALID_ARGUMENT;
+    mg_status_t r = check_batch(p->batch);
+    if (r) return r;
+    cudaStream_t s0 = static_cast<cudaStream_t>(p->stream[0]);
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (auto &e : ctx->step_ev)
+            if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return MG_ERR_CUDA;
+        if (p->capture && ctx->step.exec && same_step(ctx->step, *p))
+            return cudaGraphLaunch(ctx->step.exec, s0) == cudaSuccess ? MG_OK : MG_ERR_CUDA;
+    }
+    if (!p->capture || !s0) return enqueue_step(ctx, p);  // the legacy stream cannot be captured
+    // record the step as one CUDA graph (the streams it forks to join the capture through
+    // its events), then launch it
+    if (cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MG_ERR_CUDA;
+    r = enqueue_step(ctx, p);
+    cudaGraph_t cg = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s0, &cg);
+    if (r || ce != cudaSuccess || !cg) {
+        if (cg) cudaGraphDestroy(cg);
+        return r ? r : MG_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, cg, 0);
+    cudaGraphDestroy(cg);
+    if (ie != cudaSuccess) return MG_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->step.exec) cudaGraphExecDestroy(ctx->step.exec);
+    ctx->step = mg_context::StepRec();
+    ctx->step.st = *p;
+    ctx->step.batch = *p->batch;
+    for (int g = 0; g < 2; ++g) {
+        if (p->graph[g]) ctx->step.g[g] = *p->graph[g];
+        if (p->graph_host[g]) ctx->step.h[g] = *p->graph_host[g];
+    }
+    ctx->step.exec = exec;
+    return cudaGraphLaunch(exec, s0) == cudaSuccess ? MG_OK : MG_ERR_CUDA;
+}
+
+mg_status_t mg_measure_fp_peaks(mg_context_t ctx, void *sink, double *fp32_tflops, double *fp64_tflops,
+                                void *stream) {
+    if (!ctx || !sink || !fp32_tflops || !fp64_tflops) return MG_ERR_INVALID_ARGUMENT;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return MG_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return MG_ERR_CUDA;
+    }
+    int per_sm = 0;
+    const int blocks_f = (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fma_peak_kernel<float>, 256, 0) ==
+                          cudaSuccess && per_sm > 0 ? per_sm : 8) * ctx->sms;
+    const int blocks_d = (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fma_peak_kernel<double>, 256, 0) ==
+                          cudaSuccess && per_sm > 0 ? per_sm : 8) * ctx->sms;
+    auto best_rate = [&](bool dbl, int iters, int blocks, double *out) -> bool {
+        float best = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {  // the first repetition warms up
+            cudaEventRecord(e0, st);
+            if (dbl)
+                fma_peak_kernel<double><<<blocks, 256, 0, st>>>(iters, 0.999999, 1e-7, static_cast<double *>(sink));
+            else
+                fma_peak_kernel<float><<<blocks, 256, 0, st>>>(iters, 0.9999f, 1e-4f, static_cast<float *>(sink));
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return false;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < best) best = ms;
+        }
+        const double flops = 2.0 * PEAK_CHAINS * (double)iters * 256.0 * blocks;
+        *out = flops / (best * 1e-3) / 1e12;
+        return true;
+    };
+    const bool ok = best_rate(false, 4096, blocks_f, fp32_tflops) && best_rate(true, 64, blocks_d, fp64_tflops);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ok && cudaGetLastError() == cudaSuccess ? MG_OK : MG_ERR_CUDA;
 }
 
 mg_status_t mg_profile_enable(mg_context_t ctx, int32_t on) {

@@ -327,6 +327,18 @@ def stage_times(which: str, device=None) -> dict:
     return {} if n < 0 else {names[q].decode(): float(ms[q]) for q in range(n)}
 
 
+def measure_fp_peaks(device=None) -> dict:
+    """FP32 and FP64 fused multiply-add rates of the device in TFLOP/s, from the library's
+    own kernel (independent FMA chains on a full-occupancy grid, CUDA events; no clock or
+    power setting touched).  Synchronises."""
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    sink = torch.zeros(2, dtype=torch.float64, device=dev)
+    f32, f64 = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _capi.check(_capi.load().mg_measure_fp_peaks(context(dev), sink.data_ptr(), ctypes.byref(f32), ctypes.byref(f64),
+                                                 _stream(dev)), "mg_measure_fp_peaks")
+    return {"fp32_tflops": f32.value, "fp64_tflops": f64.value}
+
+
 def last_launch_count(device=None) -> int:
     return int(_capi.load().mg_last_launch_count(context(device)))
 
@@ -438,6 +450,65 @@ def graph_to_host(g: Graph, out: dict, num_edges: Optional[int] = None) -> dict:
                                        ctypes.byref(h), _stream(dev))
     _capi.check(rc, "mg_graph_to_host")
     return out
+
+
+class Step:
+    """One step of a generative loop through a single library call (mg_graph_step): new
+    geometry copied in from pinned host tensors, graphs[0] (and graphs[1], on its own
+    stream) rebuilt, each graph's rows copied to its host buffers, edge vectors and the
+    backward of grad_vec / grad_len on graphs[0], results copied out.  The argument
+    block is built once here; run() only enqueues (synchronise streams[0] to read).
+
+    graphs: one or two built Graphs on the same batch; streams: torch streams (the first
+    is the step's); host: per graph a dict from host_buffers (or None); inputs: dict of
+    pinned host tensors 'frac', 'lattice', 'atom_ptr' (any subset); outputs: dict of
+    pinned host tensors 'vec', 'len', 'grad_frac', 'grad_lattice' (any subset); capture:
+    record the step as one CUDA graph at the first run and replay it (one launch)."""
+
+    def __init__(self, graphs, streams, host=(None, None), inputs=None, grad_vec=None, grad_len=None, vec=None,
+                 ln=None, grad_frac=None, grad_lattice=None, outputs=None, host_edges=None, capture=True):
+        g0 = graphs[0]
+        g1 = graphs[1] if len(graphs) > 1 else None
+        batch = g0.batch
+        inputs = inputs or {}
+        outputs = outputs or {}
+        self._keep = [graphs, streams, host, inputs, outputs, grad_vec, grad_len, vec, ln, grad_frac, grad_lattice]
+        st = _capi.MgStep()
+        st.batch = ctypes.addressof(batch.c)
+        st.frac_host = _ptr(inputs.get("frac"))
+        st.lattice_host = _ptr(inputs.get("lattice"))
+        st.atom_ptr_host = _ptr(inputs.get("atom_ptr"))
+        self._hosts = []
+        for q, g in enumerate((g0, g1)):
+            if g is None:
+                continue
+            st.graph[q] = ctypes.addressof(g.c)
+            st.ws[q] = g.ws.data_ptr()
+            st.ws_bytes[q] = g.ws.numel()
+            h = host[q] if q < len(host) else None
+            if h is not None:
+                hh = _capi.MgGraphHost(*[_ptr(h.get(f)) for f in HOST_FIELDS])
+                self._hosts.append(hh)
+                st.graph_host[q] = ctypes.addressof(hh)
+            edges = host_edges[q] if host_edges is not None else g.num_edges
+            st.host_edges[q] = int(edges)
+        for q, s_ in enumerate(streams[:3]):
+            st.stream[q] = s_.cuda_stream if s_ is not None else None
+        st.grad_vec, st.grad_len = _ptr(grad_vec), _ptr(grad_len)
+        st.vec, st.len = _ptr(vec), _ptr(ln)
+        st.grad_frac, st.grad_lattice = _ptr(grad_frac), _ptr(grad_lattice)
+        st.vec_host, st.len_host = _ptr(outputs.get("vec")), _ptr(outputs.get("len"))
+        st.grad_frac_host, st.grad_lattice_host = _ptr(outputs.get("grad_frac")), _ptr(outputs.get("grad_lattice"))
+        st.capture = int(bool(capture))  # record the step once as a CUDA graph, replay it after
+        self._st = st
+        self._ref = ctypes.byref(st)
+        self._lib = _capi.load()
+        self._ctx = context(batch.device)
+
+    def run(self) -> None:
+        rc = self._lib.mg_graph_step(self._ctx, self._ref)
+        if rc:
+            _capi.check(rc, "mg_graph_step")
 
 
 # ---------------------------------------------------------------------------- edge vectors

@@ -39,11 +39,11 @@ def test_candidates_per_edge_model_against_a_brute_force_count():
 
 
 def test_fp32_term_arithmetic():
-    t = bench.fp32_term(1_000_000, 1e-3, 80.0)
+    t = bench.fp32_term(1_000_000, 1e-3, 80.0, "measured")
     per_edge = 11.0 * 6.0 / math.pi
     assert math.isclose(t["achieved"], per_edge * 1e6 / 1e-3 / 1e12)
     assert math.isclose(t["frac"], t["achieved"] / 80.0)
-    assert t["unit"] == "TFLOP/s"
+    assert t["unit"] == "TFLOP/s" and t["peak_source"] == "measured"
 
 
 def test_recorded_traffic_only_for_the_sources_it_was_captured_on(monkeypatch):

@@ -67,6 +67,22 @@ def test_output_struct_layouts_match_header(tmp_path):
                     ctypes.sizeof(MgGraphHost), MgGraphHost.vec.offset, MgGraphHost.src_ptr.offset], vals
 
 
+def test_step_struct_layout_matches_header(tmp_path):
+    """mg_step_t, field by field, as the C compiler lays it out."""
+    import ctypes
+    import subprocess
+    from paper_2307_05380_gb300._capi import MgStep
+    names = [f[0] for f in MgStep._fields_]
+    src = tmp_path / "step.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "matgraph.h"\n'
+                   'int main(void){printf("%zu", sizeof(mg_step_t));' +
+                   "".join(f'printf(" %zu", offsetof(mg_step_t, {n}));' for n in names) + 'return 0;}\n')
+    exe = tmp_path / "step"
+    subprocess.check_call(["gcc", "-I" + os.path.dirname(HEADER), str(src), "-o", str(exe)])
+    vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert vals == [ctypes.sizeof(MgStep)] + [getattr(MgStep, n).offset for n in names], vals
+
+
 def test_status_strings(lib):
     for code in range(11):
         s = lib.mg_status_string(code).decode()

@@ -520,3 +520,72 @@ def test_plans_recorded_again_when_profiling_changes():
     mg.profile_enable(False)
     mg.update_graph(g)
     assert_same_edges(graph_arrays(g), want, "replay without events")
+
+
+def test_measured_fp_peaks_are_plausible():
+    """The library's FMA issue-rate kernel: FP32 within a factor of two of the nominal
+    152 SM x 128 lanes x 2 flops x clock (80.5 TFLOP/s at 2070 MHz), FP64 at a small
+    fraction of it (this GPU's FP64 pipe is narrow), both positive and finite."""
+    p = mg.measure_fp_peaks(torch.device("cuda:0"))
+    assert 40.0 < p["fp32_tflops"] < 160.0, p
+    assert 0.0 < p["fp64_tflops"] < 0.25 * p["fp32_tflops"], p
+
+
+def test_graph_step_one_call_matches_the_oracle_and_separate_calls():
+    """mg_graph_step: new coordinates copied in from pinned host memory, the cutoff graph
+    and the KNN graph (on a second stream) rebuilt and copied out, edge vectors and the
+    backward of a length gradient, results copied out, all from one call.  The host
+    copies of both graphs equal the oracle's graphs of the new geometry; the gradients
+    equal those of separate library calls, bit for bit."""
+    b = synth.make_batch(2)
+    batch = to_device(b)
+    s0, s1, s2 = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    with torch.cuda.stream(s0):
+        g_cut = mg.cutoff_graph(batch, 6.0, with_perm=False)
+        g_knn = mg.knn_graph(batch, 16, with_perm=False)
+    cur = synth.perturb(b, seed=3, step=1)
+    inputs = {"frac": torch.from_numpy(cur.frac).pin_memory(), "lattice": torch.from_numpy(cur.lattice).pin_memory()}
+    cap = g_cut.capacity
+    host_cut = mg.host_buffers(g_cut, cap, ("status", "src", "dst", "offset", "src_ptr"))
+    host_knn = mg.host_buffers(g_knn, g_knn.capacity, ("status", "src", "dst", "offset", "vec", "len"))
+    gl = torch.from_numpy(synth.normal(6, 1, cap)).cuda()
+    vec = torch.empty(cap, 3, device="cuda")
+    ln = torch.empty(cap, device="cuda")
+    gf = torch.empty(b.total_atoms, 3, device="cuda")
+    gL = torch.empty(b.num_structures, 3, 3, device="cuda")
+    out = {"grad_frac": torch.empty(b.total_atoms, 3).pin_memory(),
+           "grad_lattice": torch.empty(b.num_structures, 3, 3).pin_memory(),
+           "len": torch.empty(cap).pin_memory()}
+    step = mg.Step([g_cut, g_knn], [s0, s1, s2], host=(host_cut, host_knn), inputs=inputs, grad_len=gl, vec=vec, ln=ln,
+                   grad_frac=gf, grad_lattice=gL, outputs=out, host_edges=(cap, g_knn.capacity))
+    for _ in range(2):  # twice: the argument block is reused
+        step.run()
+        s0.synchronize()
+    st = host_cut["status"]
+    assert int(st[0]) & 0xFFFFFFFF == 0
+    E = int(st[1])
+    want = oracle.cutoff(cur.lattice, cur.frac, cur.atom_ptr, 6.0)
+    got = {"src": host_cut["src"][:E].numpy(), "dst": host_cut["dst"][:E].numpy(), "offset": host_cut["offset"][:E].numpy()}
+    assert_same_edges(got, want, "step: cutoff graph of the new geometry")
+    kst = host_knn["status"]
+    Ek = int(kst[1])
+    kgot = {"src": host_knn["src"][:Ek].numpy(), "dst": host_knn["dst"][:Ek].numpy(),
+            "offset": host_knn["offset"][:Ek].numpy(), "vec": host_knn["vec"][:Ek].numpy(),
+            "len": host_knn["len"][:Ek].numpy()}
+    assert_same_edges(kgot, oracle.knn(cur.lattice, cur.frac, cur.atom_ptr, 16), "step: knn graph")
+    assert_vectors(cur, kgot)
+    with torch.cuda.stream(s0):
+        g_cut.num_edges = E
+        f2, L2 = mg.edge_vectors_bwd(g_cut, batch, None, gl, vec, ln)
+    s0.synchronize()
+    assert torch.equal(out["grad_frac"], f2.cpu()) and torch.equal(out["grad_lattice"], L2.cpu())
+    assert torch.equal(out["len"][:E], ln[:E].cpu())
+    # the same step enqueued call by call (not recorded): the same results
+    out2 = {key: torch.empty_like(v).pin_memory() for key, v in out.items()}
+    step2 = mg.Step([g_cut, g_knn], [s0, s1, s2], host=(host_cut, host_knn), inputs=inputs, grad_len=gl, vec=vec,
+                    ln=ln, grad_frac=gf, grad_lattice=gL, outputs=out2, host_edges=(cap, g_knn.capacity),
+                    capture=False)
+    step2.run()
+    s0.synchronize()
+    for key in out:
+        assert torch.equal(out[key], out2[key]), key
