@@ -404,6 +404,10 @@ def run_mine(args, rank, world, local_rank):
     b = synth.make_batch(args.config, seed=replica_seed(args.config, rank))
     batch = mg.Batch(torch.from_numpy(b.frac).to(dev), torch.from_numpy(b.lattice).to(dev),
                      torch.from_numpy(b.atom_ptr).to(dev), max_atoms=b.max_atoms)
+    # schedules per size class from the per-device autotune cache (measured here, outside
+    # every timed region, when the device or the library's sources are new to it)
+    tune = {"cutoff": mg.autotune_cached(batch, "cutoff", cutoff=wl["cutoff"]),
+            "knn": mg.autotune_cached(batch, "knn", k=wl["k"])}
     # the cutoff graph is symmetric: its backward needs no destination order, so the
     # optional perm_dst output is not requested; the step differentiates through the
     # cutoff graph only, so the KNN graph's destination order is not requested either
@@ -645,6 +649,8 @@ def run_mine(args, rank, world, local_rank):
                            "step": "cutoff build + KNN build (CUDA-graph plans) + edge-vector fwd + bwd on the "
                                    "cutoff graph; destination orders not requested (unused by the step)"},
                 "roofline": roof, "cpu_baseline": cpu, "float_error": ferr, "fp_peaks_measured": fp_peaks,
+                "autotune": {kd: {"schedule": v["schedule"], "size_class": v["size_class"], "tuned_now": v["tuned_now"]}
+                             for kd, v in tune.items()},
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": gpu_launches, "clocks": clocks, "per_structure": per_structure,
                 "stage_ms_per_step": stages, "wall_s_timed_region": t_wall}

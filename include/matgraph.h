@@ -260,6 +260,12 @@ mg_status_t mg_autotune(mg_context_t ctx, const mg_batch_t *batch, int32_t kind,
                         int32_t k, mg_graph_t *graph, void *workspace, size_t workspace_bytes,
                         void *stream);
 
+/* The context's tuned schedules, table[kind - 1][size class] (4 size classes as in
+ * mg_autotune; 0 = not tuned, else the schedule mg_autotune chose), read into table
+ * (set = 0) or replaced from it (set = 1; values outside 0..5 are rejected), so that a
+ * caller can keep them across processes (e.g. in a per-device cache file). */
+mg_status_t mg_tuned_table(mg_context_t ctx, int32_t table[2][4], int32_t set);
+
 /* Host buffers for mg_graph_to_host, all owned by the caller; any may be NULL (not
  * copied).  Page-locked (pinned) memory lets the copies run asynchronously. */
 typedef struct {

@@ -92,6 +92,7 @@ SIGNATURES = [
     ("mg_graph_to_host", c_int32, [c_void_p, ctypes.POINTER(MgBatch), ctypes.POINTER(MgGraph), c_int64,
                                    ctypes.POINTER(MgGraphHost), c_void_p]),
     ("mg_graph_step", c_int32, [c_void_p, ctypes.POINTER(MgStep)]),
+    ("mg_tuned_table", c_int32, [c_void_p, ctypes.POINTER(c_int32 * 8), c_int32]),
     ("mg_measure_fp_peaks", c_int32, [c_void_p, c_void_p, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double), c_void_p]),
     ("mg_profile_enable", c_int32, [c_void_p, c_int32]),

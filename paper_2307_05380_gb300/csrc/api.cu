@@ -1274,6 +1274,21 @@ mg_status_t mg_measure_fp_peaks(mg_context_t ctx, void *sink, double *fp32_tflop
     return ok && cudaGetLastError() == cudaSuccess ? MG_OK : MG_ERR_CUDA;
 }
 
+mg_status_t mg_tuned_table(mg_context_t ctx, int32_t table[2][4], int32_t set) {
+    if (!ctx || !table || (set != 0 && set != 1)) return MG_ERR_INVALID_ARGUMENT;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    for (int k = 0; k < 2; ++k)
+        for (int c = 0; c < 4; ++c) {
+            if (set && (table[k][c] < 0 || table[k][c] > 5)) return MG_ERR_INVALID_ARGUMENT;
+        }
+    for (int k = 0; k < 2; ++k)
+        for (int c = 0; c < 4; ++c) {
+            if (set) ctx->tuned[k][c] = table[k][c];
+            else table[k][c] = ctx->tuned[k][c];
+        }
+    return MG_OK;
+}
+
 mg_status_t mg_profile_enable(mg_context_t ctx, int32_t on) {
     if (!ctx) return MG_ERR_INVALID_ARGUMENT;
     std::lock_guard<std::mutex> lk(ctx->mu);

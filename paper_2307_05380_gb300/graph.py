@@ -352,6 +352,72 @@ def autotune(batch: Batch, kind: str, cutoff: float = 0.0, k: int = 0, capacity=
     _capi.check(rc, "mg_autotune")
 
 
+def tuned_table(device=None) -> list:
+    """The context's tuned schedules: [kind - 1][size class] (0 = not tuned)."""
+    t = (ctypes.c_int32 * 8)()
+    _capi.check(_capi.load().mg_tuned_table(context(device), ctypes.byref(t), 0), "mg_tuned_table")
+    return [list(t[0:4]), list(t[4:8])]
+
+
+def set_tuned_table(table, device=None) -> None:
+    t = (ctypes.c_int32 * 8)(*[int(v) for row in table for v in row])
+    _capi.check(_capi.load().mg_tuned_table(context(device), ctypes.byref(t), 1), "mg_tuned_table")
+
+
+def size_class(max_atoms: int) -> int:
+    """The size class of a batch by its largest structure (as the library's)."""
+    m = int(max_atoms)
+    if m <= 0:
+        return 1
+    return 0 if m <= 32 else 1 if m <= 128 else 2 if m <= 512 else 3
+
+
+def _tune_path(device) -> str:
+    import hashlib
+    import os
+    from . import _build
+    h = hashlib.sha256()
+    for f in sorted(_build._sources()):
+        h.update(open(f, "rb").read())
+    idx = _dev_index(torch.device(device))
+    props = torch.cuda.get_device_properties(idx)
+    name = "".join(c if c.isalnum() else "_" for c in props.name)
+    d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tune")
+    return os.path.join(d, f"{name}_sm{props.multi_processor_count}_{h.hexdigest()[:12]}.json")
+
+
+def autotune_cached(batch: Batch, kind: str, cutoff: float = 0.0, k: int = 0, path=None) -> dict:
+    """The schedule of this batch's size class from a per-device cache file (keyed by the
+    device, its SM count and the library's sources); when the entry is missing,
+    mg_autotune measures it on this batch and the file is written again.  Returns
+    {"schedule", "size_class", "tuned_now", "path"}."""
+    import json
+    import os
+    path = path or _tune_path(batch.device)
+    cache = {}
+    if os.path.exists(path):
+        try:
+            cache = json.load(open(path))
+        except (OSError, ValueError):
+            cache = {}
+    ki = 0 if kind == "cutoff" else 1
+    sc = size_class(batch.max_atoms)
+    table = tuned_table(batch.device)
+    for key, sched in cache.items():  # "kind:class" -> schedule
+        kk, cc = key.split(":")
+        table[0 if kk == "cutoff" else 1][int(cc)] = int(sched)
+    set_tuned_table(table, batch.device)
+    tuned_now = f"{kind}:{sc}" not in cache
+    if tuned_now:
+        autotune(batch, kind, cutoff=cutoff, k=k)
+        cache[f"{kind}:{sc}"] = tuned_table(batch.device)[ki][sc]
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = f"{path}.{os.getpid()}.tmp"
+        json.dump(cache, open(tmp, "w"), indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    return {"schedule": int(cache[f"{kind}:{sc}"]), "size_class": sc, "tuned_now": tuned_now, "path": path}
+
+
 # ---------------------------------------------------------------------------- graph operations
 
 @dataclass

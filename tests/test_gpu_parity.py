@@ -463,6 +463,41 @@ def test_pair_lane_knn_identical_to_warp_knn(cfg, k):
     assert_same_edges(got, oracle_sources("knn", b, k, srcs), f"knn k={k}, 512 sources")
 
 
+def test_autotuned_schedules_identical_on_8192_structures(tmp_path):
+    """mg_autotune on the 8192-structure mixture (cutoff 6 A, k = 16) through the per-device
+    cache file: the tuned builds give the same arrays, bit for bit, as every fixed
+    schedule, and sampled structures match the oracle; a second call reads the cache
+    instead of tuning again."""
+    b = synth.make_batch(3)
+    batch = to_device(b)
+    path = str(tmp_path / "tune.json")
+    saved = mg.tuned_table(batch.device)
+    try:
+        t1 = mg.autotune_cached(batch, "cutoff", cutoff=6.0, path=path)
+        t2 = mg.autotune_cached(batch, "knn", k=16, path=path)
+        assert t1["tuned_now"] and t2["tuned_now"]
+        assert not mg.autotune_cached(batch, "cutoff", cutoff=6.0, path=path)["tuned_now"]
+        tuned = graph_arrays(mg.cutoff_graph(batch, 6.0, with_perm=False))
+        for sched in (3, 4, 5):
+            other = graph_arrays(mg.cutoff_graph(batch, 6.0, with_perm=False, opts=mg.make_opts(schedule=sched)))
+            for key in tuned:
+                np.testing.assert_array_equal(tuned[key], other[key], err_msg=f"cutoff schedule {sched} {key}")
+        ktuned = graph_arrays(mg.knn_graph(batch, 16, with_perm=False))
+        for sched in (1, 2, 5):
+            other = graph_arrays(mg.knn_graph(batch, 16, with_perm=False, opts=mg.make_opts(schedule=sched)))
+            for key in ktuned:
+                np.testing.assert_array_equal(ktuned[key], other[key], err_msg=f"knn schedule {sched} {key}")
+        rng = np.random.default_rng(31)
+        for s in sorted(rng.choice(b.num_structures, 12, replace=False).tolist()):
+            lo, hi = tuned["edge_ptr"][s], tuned["edge_ptr"][s + 1]
+            sub = b.subset([s])
+            part = {key: tuned[key][lo:hi] - (b.atom_ptr[s] if key in ("src", "dst") else 0)
+                    for key in ("src", "dst", "offset")}
+            assert_same_edges(part, oracle.cutoff(sub.lattice, sub.frac, sub.atom_ptr, 6.0), f"structure {s}")
+    finally:
+        mg.set_tuned_table(saved, batch.device)
+
+
 # ------------------------------------------------------------------ schedules, per-structure, update
 
 def test_schedules_and_per_structure_identical():
