@@ -251,20 +251,24 @@ mg_status_t mg_symmetrize(mg_context_t ctx, const mg_batch_t *batch, const mg_gr
                           mg_graph_t *out, void *workspace, size_t workspace_bytes, void *stream);
 
 /* Time the available schedules for this batch shape on the caller's buffers and keep
- * the fastest per size class (largest structure: <= 32, <= 128, <= 512 atoms, larger)
- * in the context: KNN schedules 1, 2 and 5; cutoff graphs the one-pass build, and the
- * staged and pair-lane builds when the workspace covers graph->capacity.
+ * the fastest per size class (largest structure: <= 32, <= 128, <= 512 atoms, larger;
+ * times batches below 8192 atoms and from there: class = 0..3 + 4 for the latter) in
+ * the context: KNN schedules 1, 2 and 5; cutoff graphs the one-pass build, and the
+ * staged and pair-lane builds when the workspace covers graph->capacity.  Each schedule
+ * is timed as a loop rebuilds: a build that records it, then mg_update_graph replays
+ * (CUDA events around three replays after a first one).
  * Synchronises; results are identical for every schedule.  kind/cutoff/k as in
  * mg_build_per_structure. */
 mg_status_t mg_autotune(mg_context_t ctx, const mg_batch_t *batch, int32_t kind, float cutoff,
                         int32_t k, mg_graph_t *graph, void *workspace, size_t workspace_bytes,
                         void *stream);
 
-/* The context's tuned schedules, table[kind - 1][size class] (4 size classes as in
+/* The context's tuned schedules, table[kind - 1][size class] (the size classes of
  * mg_autotune; 0 = not tuned, else the schedule mg_autotune chose), read into table
  * (set = 0) or replaced from it (set = 1; values outside 0..5 are rejected), so that a
  * caller can keep them across processes (e.g. in a per-device cache file). */
-mg_status_t mg_tuned_table(mg_context_t ctx, int32_t table[2][4], int32_t set);
+#define MG_SIZE_CLASSES 8
+mg_status_t mg_tuned_table(mg_context_t ctx, int32_t table[2][MG_SIZE_CLASSES], int32_t set);
 
 /* Host buffers for mg_graph_to_host, all owned by the caller; any may be NULL (not
  * copied).  Page-locked (pinned) memory lets the copies run asynchronously. */

@@ -44,6 +44,9 @@ class MgGraphHost(ctypes.Structure):
                 ("vec", c_void_p), ("len", c_void_p), ("edge_ptr", c_void_p), ("src_ptr", c_void_p)]
 
 
+MG_SIZE_CLASSES = 8
+
+
 class MgStep(ctypes.Structure):
     _fields_ = [("batch", c_void_p), ("frac_host", c_void_p), ("lattice_host", c_void_p),
                 ("atom_ptr_host", c_void_p), ("graph", c_void_p * 2), ("ws", c_void_p * 2), ("ws_bytes", c_size_t * 2),
@@ -92,7 +95,7 @@ SIGNATURES = [
     ("mg_graph_to_host", c_int32, [c_void_p, ctypes.POINTER(MgBatch), ctypes.POINTER(MgGraph), c_int64,
                                    ctypes.POINTER(MgGraphHost), c_void_p]),
     ("mg_graph_step", c_int32, [c_void_p, ctypes.POINTER(MgStep)]),
-    ("mg_tuned_table", c_int32, [c_void_p, ctypes.POINTER(c_int32 * 8), c_int32]),
+    ("mg_tuned_table", c_int32, [c_void_p, ctypes.POINTER(c_int32 * (2 * MG_SIZE_CLASSES)), c_int32]),
     ("mg_measure_fp_peaks", c_int32, [c_void_p, c_void_p, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double), c_void_p]),
     ("mg_profile_enable", c_int32, [c_void_p, c_int32]),

@@ -72,7 +72,7 @@ struct mg_context {
     std::map<const void *, Plan> plans;      // keyed by graph->src
     std::map<const void *, mg_graph_t> sym;  // symmetric closures written here, keyed by src
     std::map<const void *, const void *> pair_owner;  // workspace -> graph (src) whose pair table it holds
-    int tuned[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};  // [kind-1][size class] -> schedule
+    int tuned[2][MG_SIZE_CLASSES] = {};  // [kind-1][size class] -> schedule (0: not tuned)
     int64_t last_launches = 0;
     cudaEvent_t step_ev[3] = {};  // mg_graph_step's fork and join events (no timing)
     struct StepRec {              // the step mg_graph_step recorded as a CUDA graph
@@ -211,6 +211,7 @@ Work carve(void *ws, int B, int N, int64_t max_edges) {
     w.stage_off = reinterpret_cast<long long *>(b + L.stage_off);
     w.stage_ctr = reinterpret_cast<unsigned long long *>(w.queue + 4);
     w.items = reinterpret_cast<int2 *>(b + L.items);
+    w.spill_list = w.cursor;  // the scatter cursors are not in use during a cutoff build
     w.plan_items = reinterpret_cast<int32_t *>(b + L.plan_items);
     w.plan_class = reinterpret_cast<int32_t *>(b + L.plan_class);
     w.item_base = reinterpret_cast<int32_t *>(b + L.item_base);
@@ -252,13 +253,13 @@ mg_status_t check_graph(const mg_graph_t *g, const mg_batch_t *b) {
     return MG_OK;
 }
 
+// Size class of a batch: its largest structure (<= 32, <= 128, <= 512 atoms, larger or
+// unknown as <= 128), plus 4 from 8192 atoms in the batch (where the staged and
+// pair-lane forms start to pay for their extra launches).
 int size_class(const mg_batch_t *b) {
     const int m = b->max_atoms;
-    if (m <= 0) return 1;
-    if (m <= 32) return 0;
-    if (m <= 128) return 1;
-    if (m <= 512) return 2;
-    return 3;
+    const int c = m <= 0 ? 1 : m <= 32 ? 0 : m <= 128 ? 1 : m <= 512 ? 2 : 3;
+    return c + (b->total_atoms >= STAGED_MIN_ATOMS ? 4 : 0);
 }
 
 // KNN schedule: 1 / 2 the warp-enumeration KNN on a flat or persistent grid, 5 the
@@ -1065,13 +1066,20 @@ mg_status_t mg_autotune(mg_context_t ctx, const mg_batch_t *b, int32_t kind, flo
         mg_opts_t o = defaults(nullptr);
         o.schedule = sched;
         float tot = 0.f;
+        // the build once with this schedule (which records it), then replays of the
+        // recorded plan, as a rebuild inside a loop runs (mg_update_graph); the first
+        // replay records the CUDA graph and is not counted
+        mg_status_t r0 = kind == MG_KIND_CUTOFF ? mg_cutoff_graph(ctx, b, cutoff, nullptr, &o, g, ws, ws_bytes, stream)
+                                                : mg_knn_graph(ctx, b, k, &o, g, ws, ws_bytes, stream);
+        if (r0) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return r0;
+        }
         for (int rep = 0; rep < 4; ++rep) {
             mg_status_t r;
             cudaEventRecord(e0, st);
-            if (kind == MG_KIND_CUTOFF)
-                r = mg_cutoff_graph(ctx, b, cutoff, nullptr, &o, g, ws, ws_bytes, stream);
-            else
-                r = mg_knn_graph(ctx, b, k, &o, g, ws, ws_bytes, stream);
+            r = mg_update_graph(ctx, b, g, ws, ws_bytes, stream);
             cudaEventRecord(e1, st);
             if (r) {
                 cudaEventDestroy(e0);
@@ -1274,15 +1282,15 @@ mg_status_t mg_measure_fp_peaks(mg_context_t ctx, void *sink, double *fp32_tflop
     return ok && cudaGetLastError() == cudaSuccess ? MG_OK : MG_ERR_CUDA;
 }
 
-mg_status_t mg_tuned_table(mg_context_t ctx, int32_t table[2][4], int32_t set) {
+mg_status_t mg_tuned_table(mg_context_t ctx, int32_t table[2][MG_SIZE_CLASSES], int32_t set) {
     if (!ctx || !table || (set != 0 && set != 1)) return MG_ERR_INVALID_ARGUMENT;
     std::lock_guard<std::mutex> lk(ctx->mu);
     for (int k = 0; k < 2; ++k)
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < MG_SIZE_CLASSES; ++c) {
             if (set && (table[k][c] < 0 || table[k][c] > 5)) return MG_ERR_INVALID_ARGUMENT;
         }
     for (int k = 0; k < 2; ++k)
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < MG_SIZE_CLASSES; ++c) {
             if (set) ctx->tuned[k][c] = table[k][c];
             else table[k][c] = ctx->tuned[k][c];
         }

@@ -51,6 +51,8 @@ __global__ void __launch_bounds__(GROUP == 32 ? 128 : GROUP) prep_kernel(PrepArg
     if (blockIdx.x == 0 && threadIdx.x == 0) {  // queue[10], queue[11]: the KNN fallback list and its cursor
         queue[10] = 0;
         queue[11] = 0;
+        queue[12] = 0;  // queue[12], queue[13]: the staged builds' spill list and its cursor
+        queue[13] = 0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && (a.init_status || (a.knn_k > 0 && a.edge_ptr))) {
         // nothing else writes the status word before the kernels that follow prep
@@ -885,6 +887,7 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_stage_kernel(Build
     if (lane == 0) {
         w.cnt[i] = m;
         w.stage_off[i] = spill ? -1 : off;
+        if (spill && m > 0) note_spill(w.spill_list, w.queue, i);
     }
 }
 
@@ -955,20 +958,26 @@ __global__ void __launch_bounds__(256) cutoff_emit_kernel(BuildArgs a, Work w) {
 }
 
 // Staged build, spilled sources (more edges than the shared staging holds, an offset
-// outside the packed key, or a full staging area): a warp each enumerates its source
-// again in canonical all-pairs order, writing at src_ptr[i].
+// outside the packed key, or a full staging area): a small persistent grid takes the
+// spill list, a warp per source enumerating it again in canonical all-pairs order and
+// writing at src_ptr[i].
 template <bool PERSRC>
 __global__ void __launch_bounds__(BUILD_WARPS * 32, 6) cutoff_spill_kernel(BuildArgs a, Work w) {
-    const int i = a.atom_lo + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (i >= a.atom_hi) return;
-    if (w.stage_off[i] >= 0) return;
     if (a.src_ptr[a.atom_hi] > a.g.capacity) return;  // reported by the finalize kernel
-    const int64_t base = a.src_ptr[i];
-    const int m = (int)(a.src_ptr[i + 1] - base);
-    if (m == 0) return;
-    SrcScan c;
-    if (!source_setup<PERSRC>(a, w, i, c)) return;
-    emit_source<PERSRC>(a, w, c, i, base, m, nullptr, nullptr, true);
+    const unsigned total = w.queue[12];
+    for (;;) {
+        unsigned v = 0;
+        if (lane_id() == 0) v = atomicAdd(&w.queue[13], 1u);
+        v = __shfl_sync(FULL, v, 0);
+        if (v >= total) return;
+        const int i = w.spill_list[v];
+        const int64_t base = a.src_ptr[i];
+        const int m = (int)(a.src_ptr[i + 1] - base);
+        if (m == 0) continue;
+        SrcScan c;
+        if (!source_setup<PERSRC>(a, w, i, c)) continue;
+        emit_source<PERSRC>(a, w, c, i, base, m, nullptr, nullptr, true);
+    }
 }
 
 cudaError_t launch_cutoff_build(const BuildArgs &a, const Work &w, cudaStream_t s) {
@@ -1006,7 +1015,7 @@ cudaError_t launch_cutoff_emit(const BuildArgs &a, const Work &w, cudaStream_t s
     // 16 blocks per SM (longer ranges per warp beyond)
     const int64_t want = (a.g.capacity + 255) / 256;
     const int blocks = (int)(want < 16 * num_sms() ? (want > 0 ? want : 1) : 16 * num_sms());
-    const int sblocks = (atoms + BUILD_WARPS - 1) / BUILD_WARPS;
+    const int sblocks = max(1, min((atoms + BUILD_WARPS - 1) / BUILD_WARPS, 2 * num_sms()));  // spill list: usually empty
     if (a.cut_atom || a.rr_atom) {
         cutoff_emit_kernel<true><<<blocks, 256, 0, s>>>(a, w);
         cutoff_spill_kernel<true><<<sblocks, BUILD_WARPS * 32, 0, s>>>(a, w);

@@ -290,6 +290,7 @@ __device__ __forceinline__ void warp_source_stage(const BuildArgs &a, const Work
     if (lane == 0) {
         w.cnt[i] = m;
         w.stage_off[i] = spill ? -1 : off;
+        if (spill && m > 0) note_spill(w.spill_list, w.queue, i);
     }
     __syncwarp();
 }
@@ -395,6 +396,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 6) pair_stage_kernel(const __
         if (jg == 0 && src_ok) {
             w.cnt[ir] = src_count;
             w.stage_off[ir] = spill ? -1ll : off + src_first;
+            if (spill && src_count > 0) note_spill(w.spill_list, w.queue, (int)ir);
         }
         if (spill) {
             if (a.write_pairs && lane == 0 && T > 0) w.pair_ok[item.x] = 0;

@@ -68,6 +68,12 @@ __device__ __forceinline__ void set_error(mg_device_status_t *st, int code, int 
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
+// A source whose keys a staged build could not stage: appended to the spill list, which
+// the spill kernel enumerates again (list [N], count queue[12]).
+__device__ __forceinline__ void note_spill(int32_t *list, unsigned int *queue, int i) {
+    list[atomicAdd(&queue[12], 1u)] = i;
+}
+
 // Programmatic dependent launch: a kernel launched with programmatic stream
 // serialization may start while the kernel before it in the stream is still running;
 // pdl_wait() returns once that kernel has completed and its writes are visible (at once

@@ -40,6 +40,8 @@ struct Work {
     int32_t *pair_ok;         // [B] 1: the pair table of the structure is complete
     int32_t *lat_cnt;         // [B] atoms of the structure whose lattice partial is stored
     int2 *items;              // [N] pair-lane build: work items (structure, item within it)
+    int32_t *spill_list;      // [N] staged builds: sources whose keys were not staged
+                              // (queue[12] of them, taken through cursor queue[13]); aliases cursor
     int32_t *plan_items;      // [B] work items of each structure
     int32_t *plan_class;      // [B] cost class of each structure's items
     int32_t *item_base;       // [B] first slot of each structure's items in `items`

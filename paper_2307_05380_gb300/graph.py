@@ -354,22 +354,23 @@ def autotune(batch: Batch, kind: str, cutoff: float = 0.0, k: int = 0, capacity=
 
 def tuned_table(device=None) -> list:
     """The context's tuned schedules: [kind - 1][size class] (0 = not tuned)."""
-    t = (ctypes.c_int32 * 8)()
+    n = _capi.MG_SIZE_CLASSES
+    t = (ctypes.c_int32 * (2 * n))()
     _capi.check(_capi.load().mg_tuned_table(context(device), ctypes.byref(t), 0), "mg_tuned_table")
-    return [list(t[0:4]), list(t[4:8])]
+    return [list(t[0:n]), list(t[n:2 * n])]
 
 
 def set_tuned_table(table, device=None) -> None:
-    t = (ctypes.c_int32 * 8)(*[int(v) for row in table for v in row])
+    t = (ctypes.c_int32 * (2 * _capi.MG_SIZE_CLASSES))(*[int(v) for row in table for v in row])
     _capi.check(_capi.load().mg_tuned_table(context(device), ctypes.byref(t), 1), "mg_tuned_table")
 
 
-def size_class(max_atoms: int) -> int:
-    """The size class of a batch by its largest structure (as the library's)."""
+def size_class(max_atoms: int, total_atoms: int) -> int:
+    """The size class of a batch (as the library's): its largest structure, plus 4 from
+    8192 atoms in the batch."""
     m = int(max_atoms)
-    if m <= 0:
-        return 1
-    return 0 if m <= 32 else 1 if m <= 128 else 2 if m <= 512 else 3
+    c = 1 if m <= 0 else 0 if m <= 32 else 1 if m <= 128 else 2 if m <= 512 else 3
+    return c + (4 if int(total_atoms) >= 8192 else 0)
 
 
 def _tune_path(device) -> str:
@@ -401,7 +402,7 @@ def autotune_cached(batch: Batch, kind: str, cutoff: float = 0.0, k: int = 0, pa
         except (OSError, ValueError):
             cache = {}
     ki = 0 if kind == "cutoff" else 1
-    sc = size_class(batch.max_atoms)
+    sc = size_class(batch.max_atoms, batch.N)
     table = tuned_table(batch.device)
     for key, sched in cache.items():  # "kind:class" -> schedule
         kk, cc = key.split(":")
