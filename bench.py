@@ -2,11 +2,12 @@
 """Benchmark of the batched periodic-graph hot path on GB300.
 
 One step = the whole path over one batch: the cutoff multigraph build (prep,
-interplanar-box FP32 scan with FP64 re-test, one-pass write with a decoupled look-back),
-the KNN build (adaptive radius, register top-k, FP64 re-rank, destination order) and the
-edge-vector forward and backward passes on the cutoff graph.  Both builds replay their
-captured CUDA-graph plans (mg_update_graph).  Units are edges built per step (cutoff +
-KNN).
+interplanar-box FP32 scan with FP64 re-test in the band; at this size the pair-lane
+build over a cost-sorted work list, keys staged and written by a thread per edge), the
+KNN build (a lane per target, candidates sorted in shared memory, adaptive radius,
+FP64 ranking of the band; on a second stream) and the edge-vector forward and backward
+passes on the cutoff graph.  Both builds replay their captured CUDA-graph plans
+(mg_update_graph).  Units are edges built per step (cutoff + KNN).
 
 Default workload: 8192 synthetic structures with a 70/25/5% mixture of 1-32, 33-128
 and 129-400 atoms, 10% highly skewed cells; cutoff 6 A, k = 16 (--config 2: 256
