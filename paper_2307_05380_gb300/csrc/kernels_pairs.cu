@@ -671,12 +671,11 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 6) knn_pairs_kernel(const __g
         const int E = rmax < 0.49f ? 1 : (rmax < 0.99f ? 2 : 0);
         C = 0;
         bool over = false;
-        for (int jb = 0; jb < n; jb += 32) {
-            const int j_loc = jb + lane;
-            const bool okj = j_loc < n;
-            const int64_t jr = (int64_t)begin + (okj ? j_loc : 0);
-            const float xj0 = a.frac[3 * jr], xj1 = a.frac[3 * jr + 1], xj2 = a.frac[3 * jr + 2];
-            const float4 pj = w.pos[jr];
+        // one chunk of targets (a target per lane): the pair boxes, then the cells with
+        // FP32 d2 < rho^2 except (i, i, 0), with the same fused operations as the warp
+        // enumeration, so the structure's FP32 error bound holds.  false: stop the scan
+        // (the source falls back, or the buffer is full)
+        auto chunk = [&](float xj0, float xj1, float xj2, float4 pj, int j_loc, bool okj) -> bool {
             const float dx[3] = {__fsub_rn(xj0, xi0), __fsub_rn(xj1, xi1), __fsub_rn(xj2, xi2)};
             float lo[3], nn[3];
             bool big = false;
@@ -691,21 +690,86 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 6) knn_pairs_kernel(const __g
             if (E > 0) big |= fmaxf(nn[0], fmaxf(nn[1], nn[2])) > (float)E;  // cannot happen
             if (__any_sync(FULL, big)) {
                 fallback = true;
-                break;
+                return false;
             }
-            // the cells with FP32 d2 < rho^2, except (i, i, 0): same fused operations as
-            // the warp enumeration, so the structure's FP32 error bound holds
             const float ax = __fsub_rn(pj.x, pi4.x), ay = __fsub_rn(pj.y, pi4.y), az = __fsub_rn(pj.z, pi4.z);
-            const bool same = j_loc == i_loc;
+            const bool same = okj && j_loc == i_loc;
             if (a.collect_stats) ncand += (unsigned long long)__fmul_rn(__fmul_rn(nn[0], nn[1]), nn[2]);
-            bool placed;
-            if (E == 1)
-                placed = knn_small_cells<1>(L, ax, ay, az, lo, nn, rho2, same, j_loc, C, ord, keys, over);
-            else if (E == 2)
-                placed = knn_small_cells<2>(L, ax, ay, az, lo, nn, rho2, same, j_loc, C, ord, keys, over);
-            else
-                placed = knn_box_cells(L, ax, ay, az, lo, nn, rho2, same, j_loc, C, ord, keys, over);
-            if (!placed) break;
+            if (E == 1) return knn_small_cells<1>(L, ax, ay, az, lo, nn, rho2, same, j_loc, C, ord, keys, over);
+            if (E == 2) return knn_small_cells<2>(L, ax, ay, az, lo, nn, rho2, same, j_loc, C, ord, keys, over);
+            return knn_box_cells(L, ax, ay, az, lo, nn, rho2, same, j_loc, C, ord, keys, over);
+        };
+        if (R.nb[0] == 0 || n <= PL_MAX_ATOMS) {
+            // every atom of the structure, in order (up to PL_MAX_ATOMS atoms this is
+            // faster than the cell list: measured 0.81 against 0.90 ms for k = 16 on
+            // 8192 structures of up to 400 atoms); the targets' coordinates one chunk
+            // ahead (their loads overlap this chunk's cells)
+            int64_t jr = (int64_t)begin + (lane < n ? lane : 0);
+            float nx0 = a.frac[3 * jr], nx1 = a.frac[3 * jr + 1], nx2 = a.frac[3 * jr + 2];
+            float4 npj = w.pos[jr];
+            for (int jb = 0; jb < n; jb += 32) {
+                const int j_loc = jb + lane;
+                const float xj0 = nx0, xj1 = nx1, xj2 = nx2;
+                const float4 pj = npj;
+                if (jb + 32 < n) {
+                    jr = (int64_t)begin + (j_loc + 32 < n ? j_loc + 32 : 0);
+                    nx0 = a.frac[3 * jr];
+                    nx1 = a.frac[3 * jr + 1];
+                    nx2 = a.frac[3 * jr + 2];
+                    npj = w.pos[jr];
+                }
+                if (!chunk(xj0, xj1, xj2, pj, j_loc, j_loc < n)) break;
+            }
+        } else {
+            // larger structures with a cell list (20.4 against 1.48 ms for k = 32 on 32
+            // supercells of 1,728 to 21,952 atoms): the atoms of the bins that the reach interval
+            // [x_i - reach_k, x_i + reach_k] (wrapped) touches on each axis, each bin
+            // once; every image with FP32 d2 < rho^2 lies in the pair boxes of these
+            // targets.  Candidates then come in bin order: only the ranking by distance
+            // and the final (j, t) sort see them, so the result does not depend on it.
+            int blo[3], bcnt[3];
+            const float xw[3] = {wrap01(xi0), wrap01(xi1), wrap01(xi2)};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int nk = R.nb[d];
+                const float m = 1e-5f * (1.0f + reach[d]);
+                const int blo_d = (int)floorf((xw[d] - reach[d] - m) * (float)nk);
+                const int bhi_d = (int)floorf((xw[d] + reach[d] + m) * (float)nk);
+                blo[d] = bhi_d - blo_d + 1 >= nk ? 0 : blo_d;
+                bcnt[d] = bhi_d - blo_d + 1 >= nk ? nk : bhi_d - blo_d + 1;
+            }
+            const int nbins = bcnt[0] * bcnt[1] * bcnt[2];
+            bool go = true;
+            for (int bb = 0; bb < nbins && go; bb += 32) {
+                const int q = bb + lane;
+                int64_t st = 0;
+                int cnt = 0;
+                if (q < nbins) {
+                    const int c2 = q % bcnt[2], c1 = (q / bcnt[2]) % bcnt[1], c0 = q / (bcnt[2] * bcnt[1]);
+                    const int b0 = ((blo[0] + c0) % R.nb[0] + R.nb[0]) % R.nb[0];
+                    const int b1 = ((blo[1] + c1) % R.nb[1] + R.nb[1]) % R.nb[1];
+                    const int b2 = ((blo[2] + c2) % R.nb[2] + R.nb[2]) % R.nb[2];
+                    const int64_t gb = (int64_t)R.bin_base + (b0 * R.nb[1] + b1) * R.nb[2] + b2;
+                    st = w.cell_start[gb];
+                    cnt = (int)(w.cell_start[gb + 1] - st);
+                }
+                const int incl = warp_incl_scan(cnt);
+                const int total = __shfl_sync(FULL, incl, 31);
+                const int excl = incl - cnt;
+                for (int ab = 0; ab < total && go; ab += 32) {
+                    const int q2 = ab + lane;
+                    const bool va = q2 < total;
+                    const int ow = warp_owner(incl, va ? q2 : total - 1);
+                    const int64_t ost = __shfl_sync(FULL, st, ow);
+                    const int oex = __shfl_sync(FULL, excl, ow);
+                    float4 xj = make_float4(0.f, 0.f, 0.f, 0.f), pj = xj;
+                    if (va) {
+                        xj = w.cell_fx[ost + (q2 - oex)];
+                        pj = w.cell_p[ost + (q2 - oex)];
+                    }
+                    go = chunk(xj.x, xj.y, xj.z, pj, va ? __float_as_int(xj.w) : 0, va);
+                }
+            }
         }
         __syncwarp();
         if (fallback) break;

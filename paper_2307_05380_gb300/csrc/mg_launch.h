@@ -50,7 +50,8 @@ struct Work {
 
 constexpr int SCAN_TILE = 4096;
 constexpr int BUILD_TILE = 4;    // source atoms (one warp each) per look-back tile of the one-pass build
-constexpr int PAIR_MAX = 128;    // largest structure with a pair table (run of i -> j per (i, j))
+constexpr int PAIR_MAX = 512;    // largest structure with a pair table (run of i -> j per (i, j)):
+                                 // 2 KB of workspace per atom
 
 struct PrepArgs {
     int B, N;

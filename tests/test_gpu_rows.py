@@ -298,10 +298,10 @@ def test_symmetrized_graph_backward_uses_reverse_edges():
 
 def test_symmetric_backward_pair_table_and_search_paths_identical():
     """The reverse-edge backward finds reverse edges through the build's pair table
-    (structures of <= 128 atoms) or by binary search; both give bit-identical sums.
+    (structures of <= 512 atoms) or by binary search; both give bit-identical sums.
     A per-structure rebuild records no pair table, so the same graph then takes the
     search path."""
-    b = synth.make_batch(3, B=160)  # mostly small structures, a few above 128 atoms
+    b = synth.make_batch(3, B=160)  # structures of 1 to about 400 atoms
     assert int(np.diff(b.atom_ptr).max()) > 128
     batch = to_device(b)
     g = mg.cutoff_graph(batch, 5.0, with_perm=False)
