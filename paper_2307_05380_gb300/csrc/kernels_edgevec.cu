@@ -227,16 +227,16 @@ __device__ __forceinline__ void store_atom_sums(float *__restrict__ grad_frac, f
     if (!(lane & 1) && lane >= 6 && lane < 24) lpart[9 * j + (lane / 2 - 3)] = r;
 }
 
-// Lattice partial of one edge: M[k][c] += df_k g_c with df = x_j - x_i + t carried
-// exactly, then rounded once.
+// Lattice partial of one edge: M[k][c] += df_k g_c with df = x_j - x_i + t within about
+// one rounding of its value: x_j - x_i exactly as s1 + e1 (TwoSum); s1 + t is exact when
+// the two nearly cancel (Sterbenz) and otherwise rounds once relative to df itself.
 __device__ __forceinline__ void add_lattice_term(float M[9], const float xs[3], const float xd[3], const int t[3],
                                                  float3 g) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        float s1, e1, s2, e2;
+        float s1, e1;
         two_sum(xd[k], -xs[k], s1, e1);
-        two_sum(s1, (float)t[k], s2, e2);
-        const float df = __fadd_rn(s2, __fadd_rn(e2, e1));
+        const float df = __fadd_rn(__fadd_rn(s1, (float)t[k]), e1);
         M[3 * k + 0] = __fmaf_rn(df, g.x, M[3 * k + 0]);
         M[3 * k + 1] = __fmaf_rn(df, g.y, M[3 * k + 1]);
         M[3 * k + 2] = __fmaf_rn(df, g.z, M[3 * k + 2]);
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(256, 4) bwd_sym_kernel(EdgeVecArgs a, float2 *
         const int i = i_next;
         i_next = (p + 32 < hi) ? a.g.dst[p + 32] : -1;
         float3 g = make_float3(0.f, 0.f, 0.f);
-        float f = 0.f, vx = 0.f, vy = 0.f, vz = 0.f, l = 0.f;
+        float f = 0.f, il = 0.f, vx = 0.f, vy = 0.f, vz = 0.f, l = 0.f;
         int t[3] = {0, 0, 0};
         float xi[3] = {0.f, 0.f, 0.f};
         int64_t ilo = 0, ihi = 0;
@@ -440,7 +440,10 @@ __global__ void __launch_bounds__(256, 4) bwd_sym_kernel(EdgeVecArgs a, float2 *
                 vx = a.vec[3 * p];
                 vy = a.vec[3 * p + 1];
                 vz = a.vec[3 * p + 2];
-                if (l > 0.f) f = __fdiv_rn(a.grad_len[p], l);
+                if (l > 0.f) {
+                    il = __frcp_rn(l);
+                    f = __fmul_rn(a.grad_len[p], il);
+                }
             }
             t[0] = a.g.offset[3 * p];
             t[1] = a.g.offset[3 * p + 1];
@@ -481,7 +484,7 @@ __global__ void __launch_bounds__(256, 4) bwd_sym_kernel(EdgeVecArgs a, float2 *
         float3 gr = make_float3(0.f, 0.f, 0.f);
         if (a.grad_vec) gr = make_float3(a.grad_vec[3 * rev], a.grad_vec[3 * rev + 1], a.grad_vec[3 * rev + 2]);
         if (a.grad_len && l > 0.f) {
-            const float fr = __fdiv_rn(a.grad_len[rev], l);
+            const float fr = __fmul_rn(a.grad_len[rev], il);
             g.x = __fmaf_rn(f, vx, g.x);
             g.y = __fmaf_rn(f, vy, g.y);
             g.z = __fmaf_rn(f, vz, g.z);
