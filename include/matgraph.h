@@ -345,8 +345,9 @@ mg_status_t mg_cutoff_graph_noalloc(mg_context_t ctx, const mg_batch_t *batch, f
  *      stream[0] when stream[2] is NULL), beside the rest of the step;
  *   4. mg_edge_vectors_fwd into vec / len and mg_edge_vectors_bwd of grad_vec / grad_len
  *      into grad_frac / grad_lattice on graph[0] (ws[0] as the backward's workspace), each
- *      skipped when its outputs are NULL; vec_host, len_host (host_edges[0] rows),
- *      grad_frac_host and grad_lattice_host are copied out behind them;
+ *      skipped when its outputs are NULL; vec_host and len_host (host_edges[0] rows) are
+ *      copied out behind the forward on stream[2] (after graph[0]'s copy) while the
+ *      backward runs, grad_frac_host and grad_lattice_host behind the backward;
  *   5. stream[0] waits for streams 1 and 2: synchronise stream[0] to read the results.
  * Each graph must have been built before on this context (mg_update_graph's
  * conditions); errors are those of the calls named.  Does not synchronise.

@@ -74,7 +74,7 @@ struct mg_context {
     std::map<const void *, const void *> pair_owner;  // workspace -> graph (src) whose pair table it holds
     int tuned[2][MG_SIZE_CLASSES] = {};  // [kind-1][size class] -> schedule (0: not tuned)
     int64_t last_launches = 0;
-    cudaEvent_t step_ev[3] = {};  // mg_graph_step's fork and join events (no timing)
+    cudaEvent_t step_ev[4] = {};  // mg_graph_step's fork and join events (no timing)
     struct StepRec {              // the step mg_graph_step recorded as a CUDA graph
         mg_step_t st{};
         mg_batch_t batch{};
@@ -1131,7 +1131,7 @@ mg_status_t enqueue_step(mg_context_t ctx, const mg_step_t *p) {
     cudaStream_t s0 = static_cast<cudaStream_t>(p->stream[0]);
     cudaStream_t s1 = p->stream[1] ? static_cast<cudaStream_t>(p->stream[1]) : s0;
     cudaStream_t s2 = p->stream[2] ? static_cast<cudaStream_t>(p->stream[2]) : s0;
-    cudaEvent_t ev_in = ctx->step_ev[0], ev_g0 = ctx->step_ev[1], ev_done = ctx->step_ev[2];
+    cudaEvent_t ev_in = ctx->step_ev[0], ev_g0 = ctx->step_ev[1], ev_done = ctx->step_ev[2], ev_fwd = ctx->step_ev[3];
     // 1. inputs
     const size_t N = (size_t)b->total_atoms, B = (size_t)b->num_structures;
     if (p->frac_host && N &&
@@ -1173,6 +1173,17 @@ mg_status_t enqueue_step(mg_context_t ctx, const mg_step_t *p) {
         r = mg_edge_vectors_fwd(ctx, b, p->graph[0], p->vec, p->len, s0);
         if (r) return r;
     }
+    // the vectors and lengths go out behind the forward, on the copy stream (after the
+    // graph's rows), while the backward runs: the host link stays busy through the step
+    cudaStream_t sv = s2 != s0 ? s2 : s0;
+    if (sv != s0 && (p->vec_host || p->len_host)) {
+        if (cudaEventRecord(ev_fwd, s0) != cudaSuccess || cudaStreamWaitEvent(sv, ev_fwd, 0) != cudaSuccess)
+            return MG_ERR_CUDA;
+    }
+    if (p->vec_host && p->vec && E && cudaMemcpyAsync(p->vec_host, p->vec, 12 * E, cudaMemcpyDeviceToHost, sv) != cudaSuccess)
+        return MG_ERR_CUDA;
+    if (p->len_host && p->len && E && cudaMemcpyAsync(p->len_host, p->len, 4 * E, cudaMemcpyDeviceToHost, sv) != cudaSuccess)
+        return MG_ERR_CUDA;
     if (p->grad_frac && p->grad_lattice) {
         r = mg_edge_vectors_bwd(ctx, b, p->graph[0], p->grad_vec, p->grad_len, p->vec, p->len, p->grad_frac,
                                 p->grad_lattice, p->ws[0], p->ws_bytes[0], s0);
@@ -1183,9 +1194,7 @@ mg_status_t enqueue_step(mg_context_t ctx, const mg_step_t *p) {
         const void *src;
         size_t bytes;
     };
-    const Out outs[] = {{p->vec_host, p->vec, 12 * E},
-                        {p->len_host, p->len, 4 * E},
-                        {p->grad_frac_host, p->grad_frac, 12 * N},
+    const Out outs[] = {{p->grad_frac_host, p->grad_frac, 12 * N},
                         {p->grad_lattice_host, p->grad_lattice, 36 * B}};
     for (const Out &o : outs)
         if (o.dst && o.src && o.bytes && cudaMemcpyAsync(o.dst, o.src, o.bytes, cudaMemcpyDeviceToHost, s0) != cudaSuccess)
