@@ -114,7 +114,8 @@ typedef struct {
                               KNN graphs (exact k): auto / 5 the pair-lane KNN (a warp per
                               source, a lane per target evaluating that pair's offset box,
                               candidates sorted in shared memory; sources whose boxes are too
-                              large go to the warp-enumeration KNN), 1 the warp-enumeration
+                              large go to the warp-enumeration KNN; k <= 64, larger k
+                              takes schedule 1), 1 the warp-enumeration
                               KNN on a flat grid for every source, 2 on a persistent work
                               queue.  Cutoff builds: auto picks the one-pass build (decoupled
                               look-back) below 8192 atoms; from there the pair-lane build

@@ -389,7 +389,8 @@ mg_status_t enqueue_build(mg_context *ctx, int kind, const mg_batch_t *b, float 
         ba.rr_atom = w.rr_atom;
         ba.inclusive = 1;
         if (!cutoff_build(ba)) return MG_ERR_CUDA;
-    } else if (ba.schedule == 1 || ba.schedule == 2) {  // the warp-enumeration KNN for every source
+    } else if (ba.schedule == 1 || ba.schedule == 2 || k > PL_KNN_MAX_K) {  // the warp-enumeration KNN
+        if (ba.schedule != 1 && ba.schedule != 2) ba.schedule = 1;  // k beyond the pair-lane buffer
         if (launch_knn(ba, w, st)) return MG_ERR_CUDA;
         n += 1 + (ba.schedule == 2);
         mk.mark("knn");

@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 6) pair_stage_kernel(const __
 
 // ============================================================================ pair-lane KNN
 
-constexpr int KNN_CAP = 256;  // candidates one warp collects for its source
+constexpr int KNN_CAP = 2 * PL_KNN_MAX_K;  // candidates one warp collects for its source
 
 // Canonical FP64 squared distance of one candidate, out of line (see band_is_edge).
 __device__ __noinline__ double canon_pair_d2(const StructRec *__restrict__ rec, float xi0, float xi1, float xi2,
@@ -471,11 +471,36 @@ __device__ __forceinline__ unsigned long long warp_sort_u64(unsigned long long v
     return v;
 }
 
-// Sort n (<= KNN_CAP) 64-bit keys in shared memory with one warp: in registers up to 32,
-// by the shared-memory network beyond (padded to a power of two >= 64).
+// 64 keys, two per lane (element r 32 + lane in register r), sorted ascending by the
+// same bitonic network over 64 elements: strides below 32 across lanes, stride 32 within
+// the lane.
+__device__ __forceinline__ void warp_sort_u64x2(unsigned long long &a, unsigned long long &b) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int size = 2; size <= 64; size <<= 1) {
+        const bool d0 = (lane & size) != 0, d1 = ((lane + 32) & size) != 0;
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride == 32) {  // size 64, ascending: element lane against lane + 32
+                const unsigned long long lo = a < b ? a : b, hi = a < b ? b : a;
+                a = lo;
+                b = hi;
+            } else {
+                const bool lower = (lane & stride) == 0;
+                unsigned long long y = __shfl_xor_sync(FULL, a, stride);
+                a = (lower != d0) ? (a < y ? a : y) : (a < y ? y : a);
+                y = __shfl_xor_sync(FULL, b, stride);
+                b = (lower != d1) ? (b < y ? b : y) : (b < y ? y : b);
+            }
+        }
+    }
+}
+
+// Sort n (<= KNN_CAP) 64-bit keys in shared memory with one warp: in registers up to 64,
+// by the shared-memory network beyond (padded to a power of two >= 128).
 __device__ __forceinline__ void warp_sort_n(unsigned long long *b, int n) {
+    const int lane = lane_id();
     if (n <= 32) {
-        const int lane = lane_id();
         unsigned long long v = lane < n ? b[lane] : ~0ull;
         v = warp_sort_u64(v);
         __syncwarp();
@@ -483,7 +508,16 @@ __device__ __forceinline__ void warp_sort_n(unsigned long long *b, int n) {
         __syncwarp();
         return;
     }
-    int P = 64;
+    if (n <= 64) {
+        unsigned long long v0 = b[lane], v1 = lane + 32 < n ? b[lane + 32] : ~0ull;
+        warp_sort_u64x2(v0, v1);
+        __syncwarp();
+        b[lane] = v0;
+        if (lane + 32 < n) b[lane + 32] = v1;
+        __syncwarp();
+        return;
+    }
+    int P = 128;
     while (P < n) P <<= 1;
     warp_smem_sort_u64(b, n, P);
 }
@@ -627,7 +661,7 @@ __device__ __forceinline__ bool knn_box_cells(const float L[9], float ax, float 
 // selection of the warp-enumeration KNN: certain members below tau - 2 delta, the band
 // ranked by (canonical FP64 d2, j, t) when it holds more candidates than the slots left,
 // the k winners sorted by (j, t) and written at rows i k .. i k + k - 1.
-__global__ void __launch_bounds__(PAIR_WARPS * 32, 6) knn_pairs_kernel(const __grid_constant__ BuildArgs a,
+__global__ void __launch_bounds__(PAIR_WARPS * 32, 7) knn_pairs_kernel(const __grid_constant__ BuildArgs a,
                                                                         const __grid_constant__ Work w) {
     __shared__ unsigned long long ord_all[PAIR_WARPS][KNN_CAP];  // (FP32 d2 bits << 32 | slot)
     __shared__ unsigned long long key_all[PAIR_WARPS][KNN_CAP];  // (j << 32 | packed t) by slot

@@ -138,6 +138,7 @@ cudaError_t launch_cutoff_count(const BuildArgs &a, const Work &w, cudaStream_t 
 cudaError_t launch_cutoff_finalize(const BuildArgs &a, const Work &w, cudaStream_t s);
 cudaError_t launch_cutoff_write(const BuildArgs &a, const Work &w, cudaStream_t s);
 cudaError_t launch_knn(const BuildArgs &a, const Work &w, cudaStream_t s);
+constexpr int PL_KNN_MAX_K = 64;  // largest k of the pair-lane KNN (its buffer holds 2k candidates)
 // Pair-lane KNN (exact k, batched): a warp per source, lanes over targets evaluating
 // their pairs' offset boxes at a growing search radius; sources it cannot take go to a
 // list that launch_knn (with knn_list = 1) builds afterwards.
