@@ -396,10 +396,11 @@ __device__ __forceinline__ int64_t key_bound(const int32_t *__restrict__ keys, i
 // grad_frac[j] = sum_p (g_rev(p) - g_p) L^T; the lattice partial sums (x_i - x_j + t)^T g_p.
 // Fixed per-lane order and a fixed warp reduction (the 12 sums of an atom in one
 // reduce-scatter): deterministic, no destination order.  A warp per source atom; its
-// chunks of 32 out-edges are software-pipelined (see the loop).  64 registers, 4 blocks
-// of 8 warps per SM: the measured best against deeper pipelining or more blocks.
+// chunks of 32 out-edges are software-pipelined (see the loop).  48 registers, 5 blocks
+// of 8 warps per SM (a few spilled values): at 8192 structures 0.722 ms against 0.747 at
+// 64 registers and 4 blocks, and 0.857 at 40 registers and 6 blocks.
 template <int PAIRS>
-__global__ void __launch_bounds__(256, 4) bwd_sym_kernel(EdgeVecArgs a, float2 *__restrict__ lpart) {
+__global__ void __launch_bounds__(256, 5) bwd_sym_kernel(EdgeVecArgs a, float2 *__restrict__ lpart) {
     pdl_wait();  // launched early behind the forward: its vectors must be complete
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = lane_id();
