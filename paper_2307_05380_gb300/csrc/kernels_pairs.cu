@@ -573,8 +573,15 @@ __device__ __forceinline__ bool knn_small_cells(const float L[9], float ax, floa
             mask &= ~(1u << ((fint(z0) * E + fint(z1)) * E + fint(z2)));
     }
     const int m = __popc(mask);
-    const int incl = warp_incl_scan(m);
-    const int tot = __shfl_sync(FULL, incl, 31);
+    int incl, tot;
+    if (E == 1) {  // at most one candidate per lane: a ballot is the scan
+        const unsigned bal = __ballot_sync(FULL, m != 0);
+        incl = __popc(bal & (0xffffffffu >> (31 - lane_id())));
+        tot = __popc(bal);
+    } else {
+        incl = warp_incl_scan(m);
+        tot = __shfl_sync(FULL, incl, 31);
+    }
     if (C + tot > KNN_CAP) {
         over = true;
         return false;
