@@ -396,11 +396,12 @@ __device__ __forceinline__ int64_t key_bound(const int32_t *__restrict__ keys, i
 // grad_frac[j] = sum_p (g_rev(p) - g_p) L^T; the lattice partial sums (x_i - x_j + t)^T g_p.
 // Fixed per-lane order and a fixed warp reduction (the 12 sums of an atom in one
 // reduce-scatter): deterministic, no destination order.  A warp per source atom; its
-// chunks of 32 out-edges are software-pipelined (see the loop).  48 registers, 5 blocks
-// of 8 warps per SM (a few spilled values): at 8192 structures 0.722 ms against 0.747 at
-// 64 registers and 4 blocks, and 0.857 at 40 registers and 6 blocks.
-template <int PAIRS>
-__global__ void __launch_bounds__(256, 5) bwd_sym_kernel(EdgeVecArgs a, float2 *__restrict__ lpart) {
+// chunks of 32 out-edges are software-pipelined (see the loop).  BLOCKS blocks of 8 warps
+// per SM: 5 (48 registers, a few spilled values) for large batches, at 8192 structures
+// 0.722 ms against 0.747 at 4 blocks and 64 registers and 0.857 at 6 blocks and 40
+// registers; 4 for batches in one partial wave (256 structures: 20.1 against 21.9 us).
+template <int PAIRS, int BLOCKS>
+__global__ void __launch_bounds__(256, BLOCKS) bwd_sym_kernel(EdgeVecArgs a, float2 *__restrict__ lpart) {
     pdl_wait();  // launched early behind the forward: its vectors must be complete
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = lane_id();
@@ -527,8 +528,12 @@ cudaError_t launch_bwd_sym(const EdgeVecArgs &a, const Work &w, cudaStream_t s) 
     if (a.N <= 0) return cudaSuccess;
     const int blocks = (a.N + 7) / 8;
     float2 *lpart = w.lpart;
-    if (!a.pair_lo) return launch_pdl(bwd_sym_kernel<0>, dim3(blocks), dim3(256), s, a, lpart);
-    return launch_pdl(bwd_sym_kernel<1>, dim3(blocks), dim3(256), s, a, lpart);
+    if (a.N < 8192) {  // one partial wave: the 64-register form
+        if (!a.pair_lo) return launch_pdl(bwd_sym_kernel<0, 4>, dim3(blocks), dim3(256), s, a, lpart);
+        return launch_pdl(bwd_sym_kernel<1, 4>, dim3(blocks), dim3(256), s, a, lpart);
+    }
+    if (!a.pair_lo) return launch_pdl(bwd_sym_kernel<0, 5>, dim3(blocks), dim3(256), s, a, lpart);
+    return launch_pdl(bwd_sym_kernel<1, 5>, dim3(blocks), dim3(256), s, a, lpart);
 }
 
 cudaError_t launch_bwd_src(const EdgeVecArgs &a, const Work &w, cudaStream_t s) {
