@@ -722,12 +722,24 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 7) knn_pairs_kernel(const __g
             const float dx[3] = {__fsub_rn(xj0, xi0), __fsub_rn(xj1, xi1), __fsub_rn(xj2, xi2)};
             float lo[3], nn[3];
             bool big = false;
+            if (E == 1) {
+                // reach below half a cell: the only integer that can lie within reach of
+                // -dx is the nearest one (a cell at the interval's edge lies beyond rho
+                // by the reach's margin, so either test keeps every image closer than rho)
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                lo[d] = fceil(__fsub_rn(-reach[d], dx[d]));
-                const float hi = ffloor(__fsub_rn(reach[d], dx[d]));
-                nn[d] = okj ? fmaxf(0.0f, __fadd_rn(__fsub_rn(hi, lo[d]), 1.0f)) : 0.0f;
-                big |= okj && (lo[d] < -(float)OFFSET_KEY_LIM || hi > (float)OFFSET_KEY_LIM);
+                for (int d = 0; d < 3; ++d) {
+                    lo[d] = frnd(-dx[d]);
+                    nn[d] = (okj && fabsf(__fadd_rn(dx[d], lo[d])) <= reach[d]) ? 1.0f : 0.0f;
+                    big |= okj && fabsf(lo[d]) > (float)OFFSET_KEY_LIM;
+                }
+            } else {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    lo[d] = fceil(__fsub_rn(-reach[d], dx[d]));
+                    const float hi = ffloor(__fsub_rn(reach[d], dx[d]));
+                    nn[d] = okj ? fmaxf(0.0f, __fadd_rn(__fsub_rn(hi, lo[d]), 1.0f)) : 0.0f;
+                    big |= okj && (lo[d] < -(float)OFFSET_KEY_LIM || hi > (float)OFFSET_KEY_LIM);
+                }
             }
             big |= __fmul_rn(__fmul_rn(nn[0], nn[1]), nn[2]) > (float)PL_BOX_MAX;
             if (E > 0) big |= fmaxf(nn[0], fmaxf(nn[1], nn[2])) > (float)E;  // cannot happen
