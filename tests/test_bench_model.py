@@ -49,16 +49,16 @@ def test_fp32_term_arithmetic():
 def test_recorded_traffic_only_for_the_sources_it_was_captured_on(monkeypatch):
     """DRAM traffic from a committed ncu capture is reported only while the kernel
     sources hash to the value stored with it; any other source gives null."""
-    entry = bench.recorded_traffic(2, ("cutoff", "build"))
+    entry = bench.recorded_traffic(3, ("cutoff", "build"))
     current = bench.kernel_source_hash()
     import json
     import os
     d = json.load(open(os.path.join(os.path.dirname(bench.__file__), "profiles", "traffic.json")))
-    stored = d["config2"]["cutoff.build"]
+    stored = d["config3"]["cutoff.build"]
     if stored["source_hash"] == current:
         assert entry == stored["bytes_per_launch"]
     else:
         assert entry is None
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
-    assert bench.recorded_traffic(2, ("cutoff", "build")) is None
+    assert bench.recorded_traffic(3, ("cutoff", "build")) is None
     assert bench.recorded_traffic(9, ("cutoff", "build")) is None
