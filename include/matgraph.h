@@ -111,7 +111,8 @@ typedef struct {
                               distance all kept, so >= k edges per atom; the capacity then
                               works as for a cutoff graph).  Other values: invalid argument */
     int32_t schedule;      /* 0 auto (tuned where mg_autotune ran for the size class).
-                              KNN graphs (exact k): auto / 5 the pair-lane KNN (a warp per
+                              KNN graphs (exact k): 5 (auto from 8192 atoms; 1 below) the
+                              pair-lane KNN (a warp per
                               source, a lane per target evaluating that pair's offset box,
                               candidates sorted in shared memory; sources whose boxes are too
                               large go to the warp-enumeration KNN; k <= 64, larger k

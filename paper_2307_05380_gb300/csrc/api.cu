@@ -263,11 +263,13 @@ int size_class(const mg_batch_t *b) {
 }
 
 // KNN schedule: 1 / 2 the warp-enumeration KNN on a flat or persistent grid, 5 the
-// pair-lane KNN (the default), as requested or as mg_autotune measured for the size class.
+// pair-lane KNN, as requested or as mg_autotune measured for the size class; untuned,
+// the pair-lane KNN from 8192 atoms and the warp enumeration below (batches of 32-512
+// small structures: 0.034-0.063 against 0.040-0.081 ms for k = 32).
 int pick_schedule(mg_context *ctx, int kind, const mg_batch_t *b, const mg_opts_t &o) {
     if (o.schedule == 1 || o.schedule == 2 || (kind == MG_KIND_KNN && o.schedule == 5)) return o.schedule;
     const int t = ctx->tuned[kind == MG_KIND_KNN ? 1 : 0][size_class(b)];
-    if (kind == MG_KIND_KNN) return t ? t : 5;
+    if (kind == MG_KIND_KNN) return t ? t : (b->total_atoms >= STAGED_MIN_ATOMS ? 5 : 1);
     return t == 1 || t == 2 ? t : 1;
 }
 

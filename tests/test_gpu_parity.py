@@ -247,6 +247,29 @@ def test_edge_cases_knn():
         knn_parity(b, k)
 
 
+def test_pair_lane_knn_small_batches_and_edge_cases():
+    """The pair-lane KNN forced (schedule 5; batches below 8192 atoms take the warp
+    enumeration by default) on the 16- and 256-structure workloads, the edge cases (one
+    atom, a 25 degree skew, unwrapped coordinates, a long cell, an empty structure; k up
+    to 64, and k = 100 handed to the warp enumeration), the needle cells and the
+    cell-list structures, against the oracle."""
+    opts = mg.make_opts(schedule=5)
+    knn_parity(synth.make_batch(1), 12, opts=opts)
+    knn_parity(synth.make_batch(2), 16, opts=opts)
+    knn_parity(synth.make_batch(2), 32, opts=opts)
+    b = edge_case_batch()
+    for k in (1, 5, 27, 33, 64, 100):
+        knn_parity(b, k, opts=opts)
+    knn_parity(cell_list_batch(), 16, opts=opts)
+    c, s_ = np.cos(0.7), np.sin(0.7)  # the needle cells: the radius grows along L_0
+    R = np.array([[c, -s_, 0.0], [s_, c, 0.0], [0.0, 0.0, 1.0]]) @ np.array([[1.0, 0.0, 0.0], [0.0, c, -s_], [0.0, s_, c]])
+    lat = np.stack([np.diag([1.0, 10.0, 10.0]), np.diag([1.0, 10.0, 10.0]) @ R.T,
+                    np.array([[1.0, 0.0, 0.0], [5.0, 10.0, 0.0], [3.0, 4.0, 10.0]])])
+    needles = synth.Batch(lat, np.array([[0.3, 0.6, 0.2]] * 3), np.array([0, 1, 2, 3], np.int32))
+    for k in (5, 18):
+        knn_parity(needles, k, opts=opts)
+
+
 def cell_list_batch():
     """Structures large enough for the cell list: a skewed 2-atom cell tiled 6x6x6 with
     some atoms moved by whole cells (unwrapped coordinates), and a noisy 5x5x5 tiling of
