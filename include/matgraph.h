@@ -124,9 +124,13 @@ typedef struct {
                               pass, scan of the counts, write pass) for a constant radius
                               when max_atoms is known and at most 1024, else the staged
                               build (scan and stage keys, scan the counts, write) when the
-                              workspace covers the capacity; 3 forces the one-pass build,
-                              4 the staged one (if the workspace covers the capacity), 5
-                              the pair-lane one (constant radius; other builds ignore it) */
+                              workspace covers the capacity (when it does not, the
+                              one-pass pair-lane build for a constant radius); 3 forces
+                              the one-pass build, 4 the staged one (if the workspace covers
+                              the capacity), 5 the pair-lane one, 6 the one-pass pair-lane
+                              one (items of the pair-lane scan in canonical order, a
+                              decoupled look-back, no staging; 5 and 6: constant radius,
+                              other builds ignore them) */
     int32_t collect_stats; /* 1: count FP32 candidates and FP64 re-tests into status */
     int32_t fault_tile;    /* -1.  Testing only: the one-pass cutoff build's tile with this
                               index never publishes its offset, so the bounded waits of the
@@ -257,8 +261,8 @@ mg_status_t mg_symmetrize(mg_context_t ctx, const mg_batch_t *batch, const mg_gr
 /* Time the available schedules for this batch shape on the caller's buffers and keep
  * the fastest per size class (largest structure: <= 32, <= 128, <= 512 atoms, larger;
  * times batches below 8192 atoms and from there: class = 0..3 + 4 for the latter) in
- * the context: KNN schedules 1, 2 and 5; cutoff graphs the one-pass build, and the
- * staged and pair-lane builds when the workspace covers graph->capacity.  Each schedule
+ * the context: KNN schedules 1, 2 and 5; cutoff graphs the one-pass builds (3, 6), and
+ * the staged and pair-lane builds when the workspace covers graph->capacity.  Each schedule
  * is timed as a loop rebuilds: a build that records it, then mg_update_graph replays
  * (CUDA events around three replays after a first one).
  * Synchronises; results are identical for every schedule.  kind/cutoff/k as in

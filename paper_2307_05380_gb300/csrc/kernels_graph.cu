@@ -725,57 +725,6 @@ cudaError_t launch_cutoff_write(const BuildArgs &a, const Work &w, cudaStream_t 
 
 // ============================================================================ single-pass build
 
-// Tile status words of the decoupled look-back: value in the low 62 bits, flag on top.
-constexpr unsigned long long TILE_AGG = 1ull << 62;      // tile total published
-constexpr unsigned long long TILE_PREFIX = 2ull << 62;   // inclusive prefix published
-constexpr unsigned long long TILE_VALUE = (1ull << 62) - 1;
-constexpr int LOOKBACK_SPIN_LIMIT = 1 << 22;             // bounded wait per predecessor
-
-__device__ __forceinline__ unsigned long long load_flag(const unsigned long long *p) {
-    return *reinterpret_cast<const volatile unsigned long long *>(p);
-}
-
-// Exclusive prefix of tile `tile` from its predecessors' published words.  Every wait is
-// bounded: a predecessor that publishes nothing within the limit makes the build report
-// MG_ERR_TIMEOUT (and the prefix is then wrong) instead of hanging.
-// The warp reads the flags of the 32 nearest predecessors not yet accounted for and
-// consumes them once every flag up to the nearest published prefix is set; a window with
-// an unpublished flag is read again (nothing is skipped), so a tile never waits on a
-// predecessor beyond its nearest prefix.  Called by a whole warp; every lane returns the
-// prefix.
-__device__ long long tile_lookback_warp(const unsigned long long *flags, int tile, mg_device_status_t *status) {
-    const int lane = lane_id();
-    long long excl = 0;
-    int top = tile - 1, spins = 0;
-    while (top >= 0) {
-        const int q = top - lane;
-        const unsigned long long v = q >= 0 ? load_flag(&flags[q]) : TILE_PREFIX;  // before tile 0: prefix 0
-        const unsigned long long f = v & ~TILE_VALUE;
-        const unsigned pre = __ballot_sync(FULL, f == TILE_PREFIX);
-        const unsigned none = __ballot_sync(FULL, f == 0);
-        const int kp = pre ? __ffs(pre) - 1 : 31;  // nearest prefix in the window
-        const unsigned need = kp == 31 ? FULL : ((2u << kp) - 1u);
-        if (none & need) {
-            if (++spins > LOOKBACK_SPIN_LIMIT) {
-                // give up at the first unpublished predecessor, keeping what precedes it:
-                // every tile stopped by the same silent predecessor then gets the same
-                // shifted prefix, so the offsets stay monotone (the build still fails)
-                const int kz = __ffs(none & need) - 1;
-                excl += warp_sum(lane < kz ? (long long)(v & TILE_VALUE) : 0ll);
-                if (lane == 0) set_error(status, MG_ERR_TIMEOUT, -1);
-                break;
-            }
-            __nanosleep(32);
-            continue;
-        }
-        excl += warp_sum(lane <= kp ? (long long)(v & TILE_VALUE) : 0ll);
-        if (pre) break;
-        top -= 32;
-        spins = 0;
-    }
-    return excl;
-}
-
 // Cutoff graph in one pass.  Tiles of BUILD_WARPS consecutive source atoms are taken in
 // order (a ticket per block, so every tile a block waits on is already running); each
 // warp scans its source once and stages the edges' (j, t) keys in shared memory

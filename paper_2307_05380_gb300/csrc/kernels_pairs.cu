@@ -447,6 +447,253 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 8) pair_stage_kernel(const __
     }
 }
 
+// ============================================================================ one-pass pair-lane build
+
+// The one-pass form's items in canonical order (structure by structure): item_base[s] is
+// the first item of structure s, queue[8] the number of items.  One block: each thread
+// sums a contiguous range of structures, a block scan gives the ranges' starts.
+__global__ void __launch_bounds__(PLAN_THREADS) pair_item_scan_kernel(int B, const int32_t *__restrict__ plan_items,
+                                                                    int32_t *__restrict__ item_base,
+                                                                    unsigned int *__restrict__ queue) {
+    __shared__ int part[PLAN_THREADS];
+    const int t = threadIdx.x;
+    const int per = (B + PLAN_THREADS - 1) / PLAN_THREADS;
+    const int s0 = min(B, t * per), s1 = min(B, s0 + per);
+    int sum = 0;
+    for (int s = s0; s < s1; ++s) sum += plan_items[s];
+    part[t] = sum;
+    __syncthreads();
+    for (int off = 1; off < PLAN_THREADS; off <<= 1) {  // inclusive scan of the ranges' sums
+        const int v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int run = part[t] - sum;
+    for (int s = s0; s < s1; ++s) {
+        item_base[s] = run;
+        run += plan_items[s];
+    }
+    if (t == PLAN_THREADS - 1) queue[8] = (unsigned)part[t];
+}
+
+// The pair-lane build in one pass (small batches, where the count scan and the staging
+// of the other forms cost more than they save): blocks take tiles of PAIR_WARPS
+// consecutive items in canonical order (a ticket per block, so a tile only waits on tiles
+// already running).  A warp computes its item's pair masks into shared memory (or, for a
+// structure outside the pair-lane scan, scans its one source by the warp enumeration,
+// keys in shared memory); the tile's total is published and its offset found by the
+// decoupled look-back; then every lane writes its pairs' edges at their canonical
+// positions (or the warp emits its source).  Writes src_ptr, edge_ptr, the pair table of
+// symmetric graphs, and (the last tile) the edge count and the capacity check.  4 blocks
+// of 4 warps per SM at up to 128 registers (at 80 both scans spill; the batches this form
+// serves fill less than a wave of blocks anyway).
+__global__ void __launch_bounds__(PAIR_WARPS * 32, 4) pair_onepass_kernel(const __grid_constant__ BuildArgs a,
+                                                                           const __grid_constant__ Work w) {
+    __shared__ unsigned long long buf_all[PAIR_WARPS][BUILD_CAP];  // source keys, or masks and boxes
+    static_assert(32 * MASK_CHUNKS + 16 * MASK_CHUNKS <= BUILD_CAP, "mask buffer");
+    __shared__ int s_tile;
+    __shared__ long long s_cnt[PAIR_WARPS];
+    __shared__ long long s_prefix;
+    const int wid = threadIdx.x >> 5, lane = lane_id();
+    unsigned long long *buf = buf_all[wid];
+    unsigned *boxes = reinterpret_cast<unsigned *>(buf + 32 * MASK_CHUNKS);
+    const mg_graph_t &g = a.g;
+    pdl_wait();  // prep's records, positions, items and zeroed look-back words
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(&w.queue[3], 1u);
+    __syncthreads();
+    const int tile = s_tile;
+    const int total = (int)w.queue[8];
+    const int last_tile = (total + PAIR_WARPS - 1) / PAIR_WARPS - 1;
+    if (tile > last_tile) return;  // the whole block: more blocks than tiles
+    const int it = tile * PAIR_WARPS + wid;
+    const bool have = it < total;
+    // the item's structure: the last s with item_base[s] <= it (structures without items
+    // share their base with the next one and precede it)
+    int s = 0;
+    if (have) {
+        int lo = 0, hi = a.B;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (w.item_base[mid] <= it) lo = mid;
+            else hi = mid;
+        }
+        s = lo;
+    }
+    const StructRec &R = w.recs[s];
+    const int q_item = have ? it - w.item_base[s] : 0;
+    const bool pairs = have && R.pl != 0;
+    unsigned long long nre = 0, ncand = 0;
+    // ---- pass 1: masks and counts (pair-lane) or the source's keys (warp enumeration)
+    PairStruct P;
+    int G = 32, jg = 0, lead = 0, nchunks = 0, src_first = 0, i_loc = 0;
+    bool src_ok = false;
+    int64_t ir = 0;
+    float xi0 = 0.f, xi1 = 0.f, xi2 = 0.f;
+    long long item_total = 0;
+    SrcScan c;
+    c.s = 0;
+    int m_src = 0;
+    bool spill = false;
+    if (pairs) {
+        load_pair_struct(P, R);
+        G = P.G;
+        const int grp = lane / G;
+        jg = lane % G;
+        lead = grp * G;
+        i_loc = q_item * P.spw + grp;
+        src_ok = i_loc < P.n;
+        ir = (int64_t)P.begin + (src_ok ? i_loc : 0);
+        xi0 = a.frac[3 * ir];
+        xi1 = a.frac[3 * ir + 1];
+        xi2 = a.frac[3 * ir + 2];
+        const float4 pi4 = w.pos[ir];
+        const float3 pi = make_float3(pi4.x, pi4.y, pi4.z);
+        int cnt = 0;
+#define MG_PAIR_MASKS1(U_)                                                                                   \
+    cnt = pair_masks<U_>(P, &R, a, w, jg, i_loc, src_ok, xi0, xi1, xi2, pi, buf, boxes, nchunks, nre, ncand)
+        switch (R.pl & 255) {
+        case 1: MG_PAIR_MASKS1(1); break;
+        case 2: MG_PAIR_MASKS1(2); break;
+        case 3: MG_PAIR_MASKS1(3); break;
+        case 4: MG_PAIR_MASKS1(4); break;
+        case 5: MG_PAIR_MASKS1(5); break;
+        case 6: MG_PAIR_MASKS1(6); break;
+        case 7: MG_PAIR_MASKS1(7); break;
+        case 8: MG_PAIR_MASKS1(8); break;
+        default: MG_PAIR_MASKS1(0); break;
+        }
+#undef MG_PAIR_MASKS1
+        const int incl = warp_incl_scan(cnt);
+        item_total = __shfl_sync(FULL, incl, 31);
+        src_first = __shfl_sync(FULL, incl - cnt, lead);
+    } else if (have) {
+        const int i = R.atom_begin + q_item;
+        if (source_setup<false>(a, w, i, c)) m_src = scan_source<false>(a, w, c, buf, nullptr, spill);
+        item_total = m_src;
+    }
+    if (lane == 0) s_cnt[wid] = item_total;
+    __syncthreads();
+    if (wid == 0) {  // the tile's total and prefix: one warp looks back
+        long long agg = 0;
+        for (int q = 0; q < PAIR_WARPS; ++q) agg += s_cnt[q];
+        long long prefix = 0;
+        unsigned long long *flags = w.tile_flags;
+        if (tile == 0) {
+            if (lane == 0) atomicExch(&flags[0], TILE_PREFIX | (unsigned long long)agg);
+        } else {
+            if (lane == 0) atomicExch(&flags[tile], TILE_AGG | (unsigned long long)agg);
+            __syncwarp();
+            prefix = tile_lookback_warp(flags, tile, g.status);
+            if (lane == 0) atomicExch(&flags[tile], TILE_PREFIX | (unsigned long long)(prefix + agg));
+        }
+        if (lane == 0) s_prefix = prefix;
+        if (lane == 0 && tile == last_tile) {  // the last tile knows the edge count
+            const long long tot = prefix + agg;
+            Status *st = reinterpret_cast<Status *>(g.status);
+            st->num_edges = (unsigned long long)tot;
+            st->required_capacity = (unsigned long long)tot;
+            if (tot > g.capacity) set_error(g.status, MG_ERR_CAPACITY, -1);
+            a.src_ptr[a.N] = tot;
+            g.edge_ptr[a.B] = tot;
+            for (int q = a.B - 1; q >= 0 && a.atom_ptr[q] == a.N; --q) g.edge_ptr[q] = tot;
+        }
+    }
+    __syncthreads();
+    if (!have) return;
+    long long base = s_prefix;
+    for (int q = 0; q < wid; ++q) base += s_cnt[q];
+    const bool fits = base + item_total <= g.capacity;
+    if (!pairs) {  // ---- a source of the warp enumeration
+        const int i = R.atom_begin + q_item;
+        if (lane == 0) {
+            a.src_ptr[i] = base;
+            for (int q = s; q >= 0 && a.atom_ptr[q] == i; --q) g.edge_ptr[q] = base;  // structures starting at i
+        }
+        if (m_src > 0 && fits) emit_source<false>(a, w, c, i, base, m_src, buf, nullptr, spill);
+        return;
+    }
+    // ---- the pair-lane item: every lane writes its pairs' edges, chunk by chunk
+    const long long seg = base + src_first;  // this lane's source: its first row
+    if (jg == 0 && src_ok) {
+        a.src_ptr[ir] = seg;
+        if (i_loc == 0)
+            for (int q = s; q >= 0 && a.atom_ptr[q] == (int)ir; --q) g.edge_ptr[q] = seg;
+    }
+    if (fits) {
+        const bool ptab = a.write_pairs && P.n <= PAIR_MAX;
+        const unsigned mB2 = (65536u + P.B2 - 1) / P.B2, mB1 = (65536u + P.B1 - 1) / P.B1;
+        long long pos_src = seg;
+        for (int cc = 0; cc < nchunks; ++cc) {
+            unsigned long long mask = buf[32 * cc + lane];
+            const int m = __popcll(mask);
+            const int ci = warp_incl_scan(m);
+            const int cfirst = __shfl_sync(FULL, ci - m, lead);
+            const int ccount = __shfl_sync(FULL, ci, lead + G - 1) - cfirst;
+            long long p = pos_src + (ci - m - cfirst);
+            if (m) {
+                const int jl = cc * G + jg;
+                const int64_t jr = (int64_t)P.begin + jl;
+                if (ptab) {
+                    w.pair_lo[ir * PAIR_MAX + jl] = (uint16_t)(p - seg);
+                    w.pair_hi[ir * PAIR_MAX + jl] = (uint16_t)(p - seg + m);
+                }
+                int t0, t1, t2;
+                unpack_t(boxes[32 * cc + lane], t0, t1, t2);
+                while (mask) {  // bit b is offset lo + (r / B1, r % B1, b % B2), r = b / B2
+                    const unsigned b = (unsigned)(__ffsll((long long)mask) - 1);
+                    mask &= mask - 1;
+                    const unsigned r = (b * mB2) >> 16;
+                    const unsigned q0 = (r * mB1) >> 16;
+                    const int q2 = (int)(b - r * (unsigned)P.B2), q1 = (int)(r - q0 * (unsigned)P.B1);
+                    g.src[p] = (int32_t)ir;
+                    g.dst[p] = (int32_t)jr;
+                    g.offset[3 * p + 0] = t0 + (int)q0;
+                    g.offset[3 * p + 1] = t1 + q1;
+                    g.offset[3 * p + 2] = t2 + q2;
+                    ++p;
+                }
+            }
+            pos_src += ccount;
+        }
+        // the vectors of the item's rows, a lane per row (the rows' lanes vary in their
+        // edge counts; this part does not): read back what the warp just wrote
+        __syncwarp();
+        if (g.vec || g.len) {
+            for (long long e = base + lane; e < base + item_total; e += 32) {
+                const int64_t si = g.src[e], sj = g.dst[e];
+                const float3 v =
+                    edge_vec_ff(P.L, a.frac[3 * si], a.frac[3 * si + 1], a.frac[3 * si + 2], a.frac[3 * sj],
+                                a.frac[3 * sj + 1], a.frac[3 * sj + 2], g.offset[3 * e], g.offset[3 * e + 1],
+                                g.offset[3 * e + 2]);
+                if (g.vec) {
+                    g.vec[3 * e + 0] = v.x;
+                    g.vec[3 * e + 1] = v.y;
+                    g.vec[3 * e + 2] = v.z;
+                }
+                if (g.len) g.len[e] = vec_len(v);
+            }
+        }
+    }
+    if (a.collect_stats) {
+        nre = warp_sum(nre);
+        ncand = warp_sum(ncand);
+        if (lane == 0 && ncand) {
+            Status *st = reinterpret_cast<Status *>(g.status);
+            atomicAdd(&st->rechecked, nre);
+            atomicAdd(&st->candidates, ncand);
+        }
+    }
+}
+
+cudaError_t launch_pair_onepass(const BuildArgs &a, const Work &w, cudaStream_t s) {
+    if (a.N <= 0) return cudaSuccess;
+    pair_item_scan_kernel<<<1, PLAN_THREADS, 0, s>>>(a.B, w.plan_items, w.item_base, w.queue);
+    const int blocks = (a.N + PAIR_WARPS - 1) / PAIR_WARPS;  // at most one item per atom
+    pair_onepass_kernel<<<blocks, PAIR_WARPS * 32, 0, s>>>(a, w);
+    return cudaGetLastError();
+}
+
 // ============================================================================ pair-lane KNN
 
 constexpr int KNN_CAP = 2 * PL_KNN_MAX_K;  // candidates one warp collects for its source

@@ -124,6 +124,10 @@ struct BuildArgs {
 // large or that use a cell list are scanned by the warp enumeration inside the pass.
 cudaError_t launch_pair_plan(const BuildArgs &a, const Work &w, cudaStream_t s);
 cudaError_t launch_pair_stage(const BuildArgs &a, const Work &w, cudaStream_t s);
+// One-pass pair-lane build (constant radius, small batches): items of the pair-lane
+// scan in canonical order (1 launch), then masks, a decoupled look-back over tiles of
+// items and the edges written from the masks (1 launch).
+cudaError_t launch_pair_onepass(const BuildArgs &a, const Work &w, cudaStream_t s);
 // One-pass cutoff build (batched): scan once, stage keys, look-back offsets, write.
 cudaError_t launch_cutoff_build(const BuildArgs &a, const Work &w, cudaStream_t s);
 // Staged cutoff build: scan and stage keys globally (stage), scan the counts and write

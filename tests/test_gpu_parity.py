@@ -458,6 +458,83 @@ def test_pair_lane_build_capacity_bad_inputs_and_gradient():
         assert ep[s + 1] - ep[s] == int(np.sum((want["src"] >= b.atom_ptr[s]) & (want["src"] < b.atom_ptr[s + 1])))
 
 
+def onepass_opts(**kw):
+    return mg.make_opts(schedule=6, **kw)
+
+
+def test_pair_lane_one_pass_build_against_the_oracle():
+    """The one-pass pair-lane build (schedule 6: items in canonical order, masks, a
+    decoupled look-back, edges written from the masks) on the 16- and 256-structure
+    workloads, the edge cases, warp-enumerated structures (cell lists, large boxes, a
+    source re-enumerated past the shared staging) beside pair-lane ones, and across many
+    tiles: edges, pointers, vectors and destination order against the oracle."""
+    for b, r in ((synth.make_batch(1), 5.0), (synth.make_batch(2), 6.0), (edge_case_batch(), 3.0),
+                 (edge_case_batch(), 5.5)):
+        cutoff_parity(b, r, opts=onepass_opts())
+    b = synth.concat([cell_list_batch(), synth.crystal(np.eye(3), [[0.1, 0.2, 0.3]]), synth.make_batch(2, B=16)])
+    for r in (2.5, 4.0, 7.3):
+        cutoff_parity(b, r, opts=onepass_opts())
+
+
+def test_pair_lane_one_pass_build_identical_to_one_pass_build():
+    """Schedule 6 against the one-pass build of the warp enumeration (schedule 3), bit for
+    bit with destination order, on the 256- and 1024-structure workloads and on 160
+    structures of the 8192-structure mixture (up to 400 atoms, skewed cells); capacity
+    error with the exact requirement; the backward through its pair table."""
+    for b, r in ((synth.make_batch(2), 6.0), (synth.make_batch(4), 5.0), (synth.make_batch(3, B=160), 6.0)):
+        batch = to_device(b)
+        one = graph_arrays(mg.cutoff_graph(batch, r, opts=onepass_opts()))
+        ref = graph_arrays(mg.cutoff_graph(batch, r, opts=mg.make_opts(schedule=3)))
+        assert one.keys() == ref.keys()
+        for key in ref:
+            np.testing.assert_array_equal(one[key], ref[key], err_msg=key)
+    b = synth.make_batch(2)
+    batch = to_device(b)
+    want = oracle.cutoff(b.lattice, b.frac, b.atom_ptr, 6.0)
+    g = mg.cutoff_graph(batch, 6.0, capacity=1000, opts=onepass_opts(), sync=False)
+    st = g.read_status()
+    assert st["code"] == 4 and st["required_capacity"] == len(want["src"]), st
+    g = mg.cutoff_graph(batch, 6.0, opts=onepass_opts(), with_perm=False)
+    grad_check(b, g, synth.normal(9, 1, g.num_edges), c=synth.normal(9, 2, 3 * g.num_edges).reshape(-1, 3))
+    g3 = mg.cutoff_graph(batch, 6.0, opts=mg.make_opts(schedule=3), with_perm=False)
+    gl = torch.from_numpy(synth.normal(9, 3, g.num_edges)).cuda()
+    v, ln = mg.edge_vectors_fwd(g)
+    f1, L1 = mg.edge_vectors_bwd(g, batch, None, gl, v, ln)
+    v3, ln3 = mg.edge_vectors_fwd(g3)
+    f3, L3 = mg.edge_vectors_bwd(g3, batch, None, gl, v3, ln3)
+    assert torch.equal(f1, f3) and torch.equal(L1, L3)
+
+
+def test_pair_lane_one_pass_build_without_staging_space():
+    """A large batch whose workspace does not cover the capacity cannot stage keys: the
+    automatic choice is then the one-pass pair-lane build (stage events name one 'build'
+    stage), with the same arrays as the pair-lane build of a full workspace."""
+    import ctypes
+    from paper_2307_05380_gb300 import _capi
+    from paper_2307_05380_gb300 import graph as G
+    b = synth.make_batch(3, B=1024)
+    batch = to_device(b)
+    ref = graph_arrays(mg.cutoff_graph(batch, 6.0, with_perm=False))
+    g = mg.cutoff_graph(batch, 6.0, with_perm=False)
+    nbytes = ctypes.c_size_t(0)
+    _capi.check(_capi.load().mg_workspace_size(G.context(batch.device), ctypes.byref(batch.c), 0,
+                                               ctypes.byref(nbytes)), "mg_workspace_size")
+    g.ws = g.ws[:int(nbytes.value)]  # the per-atom regions only: no room to stage edges
+    mg.profile_enable(True, batch.device)
+    try:
+        mg.rebuild(g)
+        n_auto = mg.last_launch_count(batch.device)
+        stages = mg.stage_times("cutoff", batch.device)
+    finally:
+        mg.profile_enable(False, batch.device)
+    assert "build" in stages and "stage" not in stages, stages
+    mg.cutoff_graph(batch, 6.0, with_perm=False, opts=mg.make_opts(schedule=3))
+    assert n_auto == mg.last_launch_count(batch.device) + 1  # the item scan, then the one pass
+    got = graph_arrays(g)
+    for key in ref:
+        np.testing.assert_array_equal(got[key], ref[key], err_msg=key)
+
+
 def test_pair_lane_build_stats():
     b = synth.make_batch(3, B=512)
     g = mg.cutoff_graph(to_device(b), 6.0, opts=pair_opts(collect_stats=True))
