@@ -62,3 +62,24 @@ def test_recorded_traffic_only_for_the_sources_it_was_captured_on(monkeypatch):
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
     assert bench.recorded_traffic(3, ("cutoff", "build")) is None
     assert bench.recorded_traffic(9, ("cutoff", "build")) is None
+
+
+def test_oracle_sample_is_bounded():
+    """The host-side oracle legs time a bounded sample: the whole batch for the small
+    workloads, the first 32 structures of the 8192-structure mixture, and for the
+    supercells the smallest ones within 1.2e7 atom pairs (one pass of the brute force
+    in seconds, not the hour the whole batch takes)."""
+    import numpy as np
+
+    import synth
+    b2 = synth.make_batch(2)
+    sub, _ = bench.oracle_sample(2, b2)
+    assert sub.num_structures == b2.num_structures
+    sub, what = bench.oracle_sample(3, synth.make_batch(3, B=64))
+    assert sub.num_structures == 32 and "first 32" in what
+    b5 = synth.make_batch(5)
+    sub, what = bench.oracle_sample(5, b5)
+    n = np.diff(sub.atom_ptr).astype(np.float64)
+    assert 1 <= sub.num_structures < b5.num_structures
+    assert (n ** 2).sum() <= 1.2e7 or sub.num_structures == 1
+    assert n.max() <= np.diff(b5.atom_ptr).min() * 2  # the smallest supercells
