@@ -88,6 +88,8 @@ def parse_args():
                    help="cutoff r = 4, 6, 8 and KNN k = 8, 16, 32 on --config, batched vs per structure")
     p.add_argument("--md", action="store_true",
                    help="the 20-step perturbation loop of the 1024-structure workload")
+    p.add_argument("--link", action="store_true",
+                   help="pinned host<->device copy bandwidth (the bound of the e2e numbers)")
     return p.parse_args()
 
 
@@ -990,6 +992,51 @@ def run_md(args, local_rank):
     return 0
 
 
+def run_link(args, local_rank):
+    """Pinned host memory <-> device copy bandwidth by the copy engines (what the e2e
+    step's copies run at): one line per size and direction, the best of the
+    repetitions, CUDA events around each copy; also several copies on separate streams
+    at once."""
+    import torch
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    reps = max(5, min(args.steps, 50))
+    for mb in (2, 16, 256, 1024):
+        n = (mb << 20) // 4
+        d = torch.empty(n, dtype=torch.float32, device=dev).fill_(1.0)
+        h = torch.empty(n, dtype=torch.float32, pin_memory=True)
+        for name, dst, src in (("D2H", h, d), ("H2D", d, h)):
+            best = 1e30
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                dst.copy_(src, non_blocking=True)
+                e1.record()
+                torch.cuda.synchronize(dev)
+                best = min(best, e0.elapsed_time(e1))
+            print(json.dumps({"link": name, "MB": mb, "ms": best, "GB_per_s": (mb << 20) / best / 1e6,
+                              "how": "one pinned copy, best of %d, CUDA events" % reps}), flush=True)
+    # four D2H copies of 256 MB on four streams at once
+    streams = [torch.cuda.Stream(dev) for _ in range(4)]
+    n = (256 << 20) // 4
+    ds = [torch.empty(n, dtype=torch.float32, device=dev).fill_(1.0) for _ in streams]
+    hs = [torch.empty(n, dtype=torch.float32, pin_memory=True) for _ in streams]
+    best = 1e30
+    for _ in range(reps):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for st, d_, h_ in zip(streams, ds, hs):
+            with torch.cuda.stream(st):
+                h_.copy_(d_, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        best = min(best, time.perf_counter() - t0)
+    print(json.dumps({"link": "D2H x4 streams", "MB": 4 * 256, "ms": best * 1e3,
+                      "GB_per_s": 4 * (256 << 20) / best / 1e9,
+                      "how": "four pinned copies on four streams, host clock around all four"}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     rank, world, local_rank = dist_env()
@@ -1003,6 +1050,8 @@ def main():
         return run_runs(args, local_rank) if rank == 0 else 0
     if args.md:
         return run_md(args, local_rank) if rank == 0 else 0
+    if args.link:
+        return run_link(args, local_rank) if rank == 0 else 0
     return run_mine(args, rank, world, local_rank)
 
 
